@@ -1,0 +1,121 @@
+"""Loop contraction, exact loops and the TSM combine (oracle; test infrastructure).
+
+Loop of one source (Sec. 2.3: (1/N) sum_r <eta_r^dag X s_r> ~ Tr(M^-1 X); all
+timeslices come out at once, Sec. 4):
+
+    L_j(Gamma, t, q) = sum_{x : x_4 = t} exp(i q.x) eta_j(x)^dag Gamma s_j(x),
+    q = 2 pi (n_x / Lx, n_y / Ly, n_z / Lz),  x in [0, L).
+
+Exact loop from a dense inverse (what the estimator converges to, Eq. 2.2):
+
+    L(Gamma, t, q) = sum_{x : x_4 = t} exp(i q.x) tr_{spin,colour}[Gamma D^-1(x, x)].
+
+TSM estimator (Sec. 2.2, Eq. 2.4).  Reading of the index sets: the HP set is
+j = 0..N_HP-1 and the LP set j = N_HP..N_HP+N_LP-1, disjoint (the printed LP
+sum runs over N_LP + 1 terms, read as an off-by-one; the text after Eq. 2.4
+counts N_HP + N_LP low-precision inversions).
+
+    L_TSM = (1/N_HP) sum_{j in HP} [L_j(s_HP) - L_j(s_LP)] + (1/N_LP) sum_{j in LP} L_j(s_LP)
+
+Error (reading; the paper gives none): sigma^2 = Var_corr / N_HP + Var_LP / N_LP
+with Var the unbiased sample variance of the complex per-source values,
+Var = sum |X_j - mean|^2 / (N - 1).
+"""
+import numpy as np
+
+from .gamma import gamma_list
+from . import dirac, philox, solver
+
+
+def phases(dims, moms):
+    """exp(i q.x) on the full lattice for each momentum n in moms: [n_q, T, Z, Y, X]."""
+    lx, ly, lz, lt = dims
+    t, z, y, x = np.meshgrid(np.arange(lt), np.arange(lz), np.arange(ly),
+                             np.arange(lx), indexing='ij')
+    out = []
+    for n in moms:
+        arg = 2 * np.pi * (n[0] * x / lx + n[1] * y / ly + n[2] * z / lz)
+        out.append(np.exp(1j * arg))
+    return np.array(out)
+
+
+def local_loops(eta, s, dims, gammas, moms):
+    """L(Gamma, t, q) for one source: [n_gamma, n_q, T] complex."""
+    G = gamma_list()[list(gammas)]
+    # eta^dag Gamma s at each site, colour summed
+    dens = np.einsum('tzyxac,gab,tzyxbc->gtzyx', np.conj(eta), G, s)
+    ph = phases(dims, moms)
+    return np.einsum('qtzyx,gtzyx->gqt', ph, dens)
+
+
+def exact_loops(Dinv, dims, gammas, moms):
+    """L(Gamma, t, q) from a dense inverse (index 12*site + 3*spin + colour)."""
+    lx, ly, lz, lt = dims
+    vol = lx * ly * lz * lt
+    blocks = Dinv.reshape(vol, 4, 3, vol, 4, 3)
+    diag = blocks[np.arange(vol), :, :, np.arange(vol), :, :]  # [V, 4, 3, 4, 3]
+    diag_spin = np.einsum('vacbc->vab', diag)                   # colour trace
+    G = gamma_list()[list(gammas)]
+    tr = np.einsum('gba,vab->gv', G, diag_spin).reshape(len(gammas), lt, lz, ly, lx)
+    ph = phases(dims, moms)
+    return np.einsum('qtzyx,gtzyx->gqt', ph, tr)
+
+
+def tsm_combine(corr, lp):
+    """Eq. 2.4 from per-source loops.
+
+    corr: [N_HP, ...] values L_j(s_HP) - L_j(s_LP) over the HP set
+    lp:   [N_LP, ...] values L_j(s_LP) over the LP set
+    Returns (estimate, sigma).
+    """
+    corr = np.asarray(corr)
+    lp = np.asarray(lp)
+    n_hp, n_lp = corr.shape[0], lp.shape[0]
+    est = np.zeros(lp.shape[1:], dtype=np.complex128)
+    var = np.zeros(lp.shape[1:], dtype=np.float64)
+    if n_hp > 0:
+        m = corr.mean(axis=0)
+        est += m
+        if n_hp > 1:
+            var += (np.abs(corr - m) ** 2).sum(axis=0) / (n_hp - 1) / n_hp
+    if n_lp > 0:
+        m = lp.mean(axis=0)
+        est += m
+        if n_lp > 1:
+            var += (np.abs(lp - m) ** 2).sum(axis=0) / (n_lp - 1) / n_lp
+    return est, np.sqrt(var)
+
+
+def tsm_loops(U, dims, kappa, mu, seed, noise_kind, n_hp, n_lp, hp_stop, lp_stop,
+              gammas, moms, antiperiodic_t=True):
+    """The whole TSM estimate, source by source, in the order of Eq. 2.4.
+
+    hp_stop / lp_stop = (rel_tol, max_iter).  Source j uses eta_j from
+    oracle.philox.noise(seed, j, ...).  Returns a dict with the estimate, its
+    error, the LP-only mean over the LP set, the mean correction, the per-source
+    loops and iteration counts.
+    """
+    corr, lp_vals, hp_iters, lp_iters = [], [], [], []
+    for j in range(n_hp + n_lp):
+        eta = philox.noise(seed, j, dims, noise_kind)
+        s_lp, it_lp, _, _ = solver.solve_full(U, eta, dims, kappa, mu, lp_stop[0], lp_stop[1],
+                                              antiperiodic_t)
+        lp_iters.append(it_lp)
+        l_lp = local_loops(eta, s_lp, dims, gammas, moms)
+        if j < n_hp:
+            s_hp, it_hp, _, _ = solver.solve_full(U, eta, dims, kappa, mu, hp_stop[0], hp_stop[1],
+                                                  antiperiodic_t)
+            hp_iters.append(it_hp)
+            corr.append(local_loops(eta, s_hp, dims, gammas, moms) - l_lp)
+        else:
+            lp_vals.append(l_lp)
+    shape = (len(gammas), len(moms), dims[3])
+    corr = np.array(corr).reshape((n_hp,) + shape)
+    lp_vals = np.array(lp_vals).reshape((n_lp,) + shape)
+    est, err = tsm_combine(corr, lp_vals)
+    return {
+        'loops': est, 'err': err,
+        'lp_mean': lp_vals.mean(axis=0) if n_lp else np.zeros(shape, np.complex128),
+        'corr_mean': corr.mean(axis=0) if n_hp else np.zeros(shape, np.complex128),
+        'corr': corr, 'lp': lp_vals, 'hp_iters': hp_iters, 'lp_iters': lp_iters,
+    }
