@@ -1,0 +1,437 @@
+"""Benchmark of the TSM loop path on GB300 (one JSON line on rank 0).
+
+Workload (N = 1): 24^3 x 48 lattice, near-unit SU(3) links exp(0.25 i H)
+(seed 3), kappa = 0.1245, mu = 0.005, antiperiodic t, Z4 noise; N_HP = 8 HP
+solves (FP32 iterations with FP64 reliable updates, rel. residual 1e-10) and
+N_LP = 256 LP solves (FP16 storage, FP32 arithmetic, truncated at 5e-3 or 60
+iterations); loops for 16 insertions at 7 momenta; TSM combine.  One step =
+one complete TSM estimate (264 sources) with fresh noise (seed per step).
+
+metric: TSM sources/s.  Alongside: the equal-loop-error comparison with the
+plain FP64 path (every source solved to 1e-10 in FP64, standard estimator),
+the hop-kernel roofline (CUDA events on the library's stream inside the timed
+region), standalone Dslash GB/s per tier, the end-to-end number through the C
+ABI with host buffers, the oracle's CPU throughput on a bounded sample, the
+clocks seen during the timed region and the kernel-launch count.
+
+--impl reference runs the CPU oracle (the only other implementation of this
+method here) on the same workload: each step is a bounded sample (one CG
+iteration of the oracle at 24^3 x 48), scaled to sources/s.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (24, 24, 24, 48)
+EPS, KAPPA, MU, GAUGE_SEED = 0.25, 0.1245, 0.005, 3
+N_HP, N_LP = 8, 256
+HP_TOL, LP_TOL, LP_MAXIT, HP_MAXIT = 1e-10, 5e-3, 60, 20000
+N_GAMMA, N_Q = 16, 7
+METRIC = "TSM sources/sec at 24^3x48 and Dslash HBM GB/s, vs plain FP64 at equal loop error"
+WORKLOAD = "tsm-24^3x48-eps0.25-k0.1245-mu0.005-Z4-hp8(f32+f64rel,1e-10)-lp256(f16,5e-3|60)-16G-7q"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e / equal-error / cpu-baseline legs")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle sample
+def oracle_sample(U, t_src_too=True):
+    """Time the CPU oracle on a bounded sample of the workload: one CG iteration
+    (Dhat then Dhat^dag plus the vector updates) at 24^3 x 48 and, optionally,
+    the per-source work outside the iterations (Schur source, odd-site
+    reconstruction, contraction)."""
+    from oracle import dirac, loops, philox
+    eta = philox.noise(1000, 0, DIMS, 4)
+    e = dirac.even_mask(DIMS)
+    p = e * eta
+    t0 = time.perf_counter()
+    q = dirac.schur(U, p, DIMS, KAPPA, MU)
+    alpha = np.vdot(p, p).real / np.vdot(q, q).real
+    x = alpha * p
+    r = p - alpha * dirac.schur_dag(U, q, DIMS, KAPPA, MU)
+    beta = np.vdot(r, r).real / np.vdot(p, p).real
+    p = r + beta * p
+    t_it = time.perf_counter() - t0
+    t_src = None
+    if t_src_too:
+        t0 = time.perf_counter()
+        bh = dirac.schur_source(U, eta, DIMS, KAPPA, MU)
+        s = dirac.schur_reconstruct(U, x, eta, DIMS, KAPPA, MU)
+        loops.local_loops(eta, s, DIMS, list(range(N_GAMMA)), default_moms())
+        # Dhat^dag bhat that starts every solve
+        dirac.schur_dag(U, bh, DIMS, KAPPA, MU)
+        t_src = time.perf_counter() - t0
+    return t_it, t_src
+
+
+def default_moms():
+    from paper_1211_0126_gb300 import synthetic as S
+    return S.default_momenta(N_Q)
+
+
+def oracle_rate(t_it, t_src, lp_iters_per_src, hp_iters_per_src):
+    """sources/s of the oracle for the workload: every LP solve costs its
+    iterations plus the per-source work; every HP-set source adds its HP solve."""
+    t_lp = lp_iters_per_src * t_it + t_src
+    t_hp = hp_iters_per_src * t_it + t_src
+    total = (N_HP + N_LP) * t_lp + N_HP * t_hp
+    return (N_HP + N_LP) / total
+
+
+# nominal iteration counts of the workload for the CPU-only arm, which cannot
+# run a 24^3 x 48 solve to completion: LP solves stop at their 60-iteration
+# cap; the HP count is the CG count of the FP64 1e-10 solve of this workload
+NOMINAL_LP_ITERS, NOMINAL_HP_ITERS = 60, 1500
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1211_0126_gb300 import synthetic as S
+    U = S.gauge_field(DIMS, EPS, GAUGE_SEED)
+    t_src = None
+    times = []
+    for k in range(args.warmup + args.steps):
+        t_it, ts = oracle_sample(U, t_src_too=(k == 0))
+        if ts is not None:
+            t_src = ts
+        if k >= args.warmup:
+            times.append(t_it)
+    t_it = float(np.mean(times))
+    value = oracle_rate(t_it, t_src, NOMINAL_LP_ITERS, NOMINAL_HP_ITERS)
+    ms_step = (N_HP + N_LP) / value * 1e3
+    sample = ("one oracle CG iteration at 24^3x48 per step (%.2f s) + per-source work once (%.2f s), "
+              "scaled with %d LP and %d HP iterations per source (extrapolated)"
+              % (t_it, t_src, NOMINAL_LP_ITERS, NOMINAL_HP_ITERS))
+    line = {"metric": METRIC, "value": value, "unit": "sources/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "sources/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "sources/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("dslash.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1211_0126_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per hop launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "hop_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1211_0126_gb300 import build, replicas, tsm
+    from paper_1211_0126_gb300 import synthetic as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if not os.path.exists(tsm.LIB_PATH):
+        if rank == 0:
+            build.build()
+        if world > 1:
+            dist.barrier()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    U = S.gauge_field(DIMS, EPS, GAUGE_SEED)
+    U_pinned = torch.from_numpy(U.view(np.float64).reshape(-1)).pin_memory()
+    ctx = tsm.Context(local, stream.cuda_stream)
+    ctx.load_gauge(U, DIMS, KAPPA, MU)
+    gam, moms = list(range(N_GAMMA)), S.default_momenta(N_Q)
+    hp_stop = tsm.stop(HP_TOL, HP_MAXIT, tsm.TSM_F32, reliable=True)
+    lp_stop = tsm.stop(LP_TOL, LP_MAXIT, tsm.TSM_F16)
+    hp_range, lp_range = replicas.source_ranges(N_HP, N_LP, rank, world)
+    E = N_GAMMA * N_Q * DIMS[3]
+    shape = (N_GAMMA, N_Q, DIMS[3])
+    d_loops = torch.zeros(shape, dtype=torch.complex128, device=dev)
+    d_err = torch.zeros(shape, dtype=torch.float64, device=dev)
+    d_pc = torch.zeros((N_HP,) + shape, dtype=torch.complex128, device=dev)
+    d_pl = torch.zeros((N_LP,) + shape, dtype=torch.complex128, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def step(seed):
+        p = tsm.params(seed, 4, hp_range, lp_range, hp_stop, lp_stop, gam, moms)
+        return tsm.tsm_loops(ctx.h, p, d_loops, d_err, None, None, d_pc, d_pl)
+
+    for k in range(args.warmup):
+        step(10_000 + k)
+    # ---------------- timed region
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    tsm.tsm_profile(ctx.h, True)
+    launches0 = ctx.launch_count()
+    times, stats = [], []
+    for k in range(args.steps):
+        flush.zero_()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record(stream)
+        stats.append(step(20_000 + k))
+        ev1.record(stream)
+        barrier()
+        times.append(ev0.elapsed_time(ev1))
+    launches = ctx.launch_count() - launches0
+    prof_ms, prof_cnt, prof_bytes = ctx.profile_read()
+    tsm.tsm_profile(ctx.h, False)
+    clk = clocks.stop()
+    # ---------------- end of timed region
+    step_ms = float(sum(times)) / len(times)
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = world * (N_HP + N_LP) / (step_ms * 1e-3)
+
+    peak, peak_kind = measured_peaks()
+    tot_ms, tot_bytes = float(prof_ms.sum()), float(prof_bytes.sum())
+    achieved = tot_bytes / (tot_ms * 1e-3) / 1e9 if tot_ms > 0 else None
+    traffic = ncu_traffic()
+    per_kind = {}
+    for kname, i in (("K1_hop", 0), ("K2_hop_xpay_norm", 1), ("K3_hop_dag", 2), ("K4_hop_dag_cg_update", 3)):
+        if prof_cnt[i]:
+            per_kind[kname] = {"launches_timed": int(prof_cnt[i]), "us_per_launch": 1e3 * prof_ms[i] / prof_cnt[i],
+                               "gbs": prof_bytes[i] / (prof_ms[i] * 1e-3) / 1e9}
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": (traffic["dram_bytes_per_launch"] if traffic else None),
+                "kernel": "half-Dslash hop family K1-K4 (FP16 LP + FP32 HP solves)",
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "per_kernel": per_kind}
+
+    st = stats[-1]
+    line = {"metric": METRIC, "value": value, "unit": "sources/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": list(DIMS), "n_hp_per_gpu": N_HP, "n_lp_per_gpu": N_LP,
+                       "l2": "flushed between steps (256 MB write)",
+                       "lp_iters_per_source": st.lp_iters / float(N_HP + N_LP),
+                       "hp_iters_per_source": st.hp_iters / float(N_HP),
+                       "hp_max_true_res": st.hp_max_true_res},
+            "roofline": roofline, "clocks": clk, "gpu_launches": int(launches)}
+
+    if rank == 0 and not args.no_extras:
+        line["dslash"] = dslash_gbs(ctx, S, tsm, flush, peak)
+        line["e2e"] = e2e_leg(ctx, tsm, U_pinned, lp_stop, hp_stop, gam, moms, stream, hp_range, lp_range)
+        line["equal_error"] = equal_error(ctx, tsm, S, d_pc, d_pl, step_ms, stream)
+        t_it, t_src = oracle_sample(U)
+        cpu_val = oracle_rate(t_it, t_src, st.lp_iters / float(N_HP + N_LP), st.hp_iters / float(N_HP))
+        line["cpu_baseline"] = {"value": cpu_val, "unit": "sources/s", "cores": 1, "kind": "oracle",
+                                "sample": "one oracle CG iteration at 24^3x48 (%.2f s) + per-source work (%.2f s), "
+                                          "scaled with this run's LP/HP iteration counts (extrapolated)"
+                                          % (t_it, t_src)}
+    if world > 1:
+        # one exchange at the end: per-source loops to every rank, combined in rank order
+        g = dist.new_group(backend="gloo")
+        pc, pl = replicas.gather_per_source(d_pc.cpu().numpy(), d_pl.cpu().numpy(), g)
+        comb = ctx.combine(pc, pl)
+        line["combined_sources"] = int(pc.shape[0] + pl.shape[0])
+        line["combined_finite"] = bool(np.isfinite(comb["loops"]).all())
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def dslash_gbs(ctx, S, tsm, flush, peak):
+    """Standalone H_eo launches per tier at 24^3 x 48, L2 flushed before each
+    call; kernel time from CUDA events around the hop launch."""
+    psi = S.random_spinor(DIMS, 99)
+    out = np.zeros_like(psi)
+    res = {}
+    for name, prec in (("f64", tsm.TSM_F64), ("f32", tsm.TSM_F32), ("f16", tsm.TSM_F16), ("bf16", tsm.TSM_BF16)):
+        for _ in range(2):
+            tsm.tm_dslash(ctx.h, prec, tsm.TM_OP_HOP_EO, 0, psi, out)
+        tsm.tsm_profile(ctx.h, True)
+        for _ in range(10):
+            flush.zero_()
+            tsm.tm_dslash(ctx.h, prec, tsm.TM_OP_HOP_EO, 0, psi, out)
+        ms, cnt, by = ctx.profile_read()
+        tsm.tsm_profile(ctx.h, False)
+        gbs = by.sum() / (ms.sum() * 1e-3) / 1e9
+        res[name] = {"us_per_launch": 1e3 * ms.sum() / cnt.sum(), "algorithmic_gbs": gbs, "frac": gbs / peak,
+                     "bytes_per_site": by.sum() / cnt.sum() / (np.prod(DIMS) // 2)}
+    return res
+
+
+def e2e_leg(ctx, tsm, U_pinned, lp_stop, hp_stop, gam, moms, stream, hp_range, lp_range, steps=2):
+    """The same TSM step through the public API with host buffers: gauge field
+    uploaded from pinned host memory, loops and errors read back to host."""
+    import torch
+    shape = (N_GAMMA, N_Q, DIMS[3])
+    loops = np.zeros(shape, dtype=np.complex128)
+    err = np.zeros(shape, dtype=np.float64)
+    ms = []
+    for k in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tsm.tsm_load_gauge(ctx.h, ctx.lat, U_pinned)
+        p = tsm.params(30_000 + k, 4, hp_range, lp_range, hp_stop, lp_stop, gam, moms)
+        tsm.tsm_loops(ctx.h, p, loops, err)
+        ms.append((time.perf_counter() - t0) * 1e3)
+    t = float(np.mean(ms))
+    return {"value": (N_HP + N_LP) / (t * 1e-3), "unit": "sources/s",
+            "h2d_bytes_per_step": int(U_pinned.numel() * 8), "d2h_bytes_per_step": int(loops.nbytes + err.nbytes),
+            "ms_per_step": t}
+
+
+def equal_error(ctx, tsm, S, d_pc, d_pl, step_ms, stream):
+    """Plain FP64 path vs TSM at equal loop error.  Plain: every source solved
+    to 1e-10 in FP64 (standard estimator), cost t_P per source (one solve
+    timed here); its per-source variance is that of the LP-set loops (the LP
+    solution differs from the exact one by the truncation only).  TSM error^2
+    = Var_corr/N_HP + Var_LP/N_LP from this run's per-source loops."""
+    import torch
+    pc = d_pc.cpu().numpy()
+    pl = d_pl.cpu().numpy()
+    out = {}
+    # plain FP64 solve of one source, timed with events
+    b = np.zeros((DIMS[3], DIMS[2], DIMS[1], DIMS[0], 4, 3), dtype=np.complex128)
+    tsm.tsm_noise(ctx.h, 777, 4, 0, b)
+    s = np.zeros_like(b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, iters, tres = tsm.tm_solve_batch(ctx.h, b, s, tsm.stop(HP_TOL, HP_MAXIT, tsm.TSM_F64))
+    t_p = time.perf_counter() - t0
+    out["plain_fp64"] = {"s_per_source": t_p, "iters": int(iters[0]), "true_res": float(tres[0])}
+    sel = {"Gamma=1,q=0,sum_t": (0, 0), "Gamma=gamma3gamma5,q=0,sum_t": (8, 0)}
+    for name, (g, q) in sel.items():
+        c = pc[:, g, q, :].sum(-1)
+        lv = pl[:, g, q, :].sum(-1)
+        var_c = np.var(c.real, ddof=1) + np.var(c.imag, ddof=1)
+        var_l = np.var(lv.real, ddof=1) + np.var(lv.imag, ddof=1)
+        eps2 = var_c / len(c) + var_l / len(lv)
+        n_eq = var_l / eps2
+        eff = n_eq / (step_ms * 1e-3)
+        out[name] = {"tsm_err": float(np.sqrt(eps2)), "plain_sources_for_equal_error": float(n_eq),
+                     "tsm_effective_sources_per_s": float(eff), "plain_sources_per_s": 1.0 / t_p,
+                     "ratio_vs_plain_fp64": float(eff * t_p)}
+    # median over all entries
+    var_c = np.var(pc.real, axis=0, ddof=1) + np.var(pc.imag, axis=0, ddof=1)
+    var_l = np.var(pl.real, axis=0, ddof=1) + np.var(pl.imag, axis=0, ddof=1)
+    ok = var_l > 0
+    ratio = (var_l[ok] / (var_c[ok] / pc.shape[0] + var_l[ok] / pl.shape[0])) / (step_ms * 1e-3) * t_p
+    out["median_all_entries_ratio_vs_plain_fp64"] = float(np.median(ratio))
+    return out
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * tsm.h -- C ABI of the GB300 truncated-solver-method (TSM) loop library.
+ *
+ * The library computes disconnected fermion loops with the truncated solver
+ * method of Alexandrou et al., "Evaluation of disconnected contributions using
+ * GPUs" (LATTICE 2012):
+ *
+ *   - Z4 / Z2 noise sources with the moments of Sec. 2.1, Eq. (2.1), generated
+ *     on the fly from a counter-based generator (Sec. 3: no propagators stored);
+ *   - inversions of the twisted-mass operator
+ *         D_tm = 1 - kappa H + 2 i kappa mu gamma_5,
+ *         (H psi)(x) = sum_mu [(1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                             + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu)]
+ *     (the twisted-mass regularisation of Sec. 2.2), by CG on the normal
+ *     equations of the even/odd Schur complement, truncated (LP) or run to high
+ *     precision (HP) (Sec. 2.2);
+ *   - loops L_j(Gamma, t, q) = sum_{x: x_4 = t} e^{i q.x} eta_j(x)^dag Gamma s_j(x)
+ *     (Sec. 2.3, first estimator; all insertion times at once, Sec. 4);
+ *   - the TSM estimate of Sec. 2.2, Eq. (2.4): LP mean over the LP set plus the
+ *     HP - LP correction over the HP set.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice: L = {Lx, Ly, Lz, T}, every extent even and >= 2.  Site index
+ *   i = x + Lx*(y + Ly*(z + Lz*t)); parity (x+y+z+t) mod 2, even = 0.
+ * Gamma basis: Euclidean chiral, gamma_k = [[0, -i sigma_k], [i sigma_k, 0]],
+ *   gamma_4 = [[0, 1], [1, 0]], gamma_5 = diag(1, 1, -1, -1).
+ * Insertion list: 0: 1, 1-4: gamma_1..gamma_4, 5: gamma_5, 6-9: gamma_mu gamma_5,
+ *   10-15: sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu] for
+ *   (mu nu) = 12, 13, 14, 23, 24, 34.
+ * Canonical host formats (complex = two doubles, re then im):
+ *   gauge  U[T][Z][Y][X][mu][a][b]    mu = 0:x, 1:y, 2:z, 3:t; every link SU(3)
+ *   spinor psi[T][Z][Y][X][spin][colour]   (24 doubles per site)
+ *   loops  L[n_gamma][n_q][T] complex
+ * Momenta: integer triples n, q = 2 pi (n_x / Lx, n_y / Ly, n_z / Lz).
+ * Noise: source j, seed s -> Philox4x32-10 (Salmon et al., SC'11), key
+ *   (s mod 2^32, s >> 32), counter (i, j, 0, 0); word 0 bit 2a (2a+1) set makes
+ *   the real (imaginary) part of component a = 3*spin + colour negative.
+ *   Z4 entries (+-1 +- i)/sqrt 2, Z2 entries +-1 (bit 2a).  The noise of
+ *   source j does not depend on batching or on how sources are split.
+ * Memory: the caller owns every pointer it passes.  With on_device = 0 the
+ *   pointers are host memory and the library copies in and out; with
+ *   on_device = 1 they are device pointers on the context's device.  The
+ *   context owns its own device workspace (allocated on first use, freed by
+ *   tsm_destroy).
+ * Streams: every call is ordered on the stream given to tsm_create and has
+ *   completed when the call returns.
+ * Errors: every call returns a tsm_status; none throws across the ABI.
+ *   tsm_last_error() gives a one-line message for the last failure on the
+ *   calling thread.
+ */
+#ifndef TSM_H
+#define TSM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tsm_ctx tsm_ctx;
+
+typedef enum {
+  TSM_OK = 0,
+  TSM_ERR_ARG = -1,            /* null pointer, bad enum, bad count */
+  TSM_ERR_DIMS = -2,           /* an extent odd or < 2, or lattice too large */
+  TSM_ERR_CUDA = -3,           /* a CUDA runtime call failed */
+  TSM_ERR_NOT_CONVERGED = -4,  /* a solve hit max_iter above its tolerance (outputs still written) */
+  TSM_ERR_NONFINITE = -5,      /* NaN/Inf met in a reduction */
+  TSM_ERR_TIMEOUT = -6,        /* a bounded device wait ran out */
+  TSM_ERR_NOT_UNITARY = -7,    /* gauge links not SU(3) to 1e-8 (2-row storage needs SU(3)) */
+  TSM_ERR_NO_GAUGE = -8,       /* no gauge field loaded */
+  TSM_ERR_TOO_LARGE = -9       /* request above a fixed internal capacity */
+} tsm_status;
+
+/* Storage / arithmetic tier.
+ *   TSM_F64  FP64 storage and arithmetic (the plain FP64 path).
+ *   TSM_F32  FP32 storage and arithmetic; in solves optionally with FP64
+ *            reliable updates (tm_stop.reliable).
+ *   TSM_BF16, TSM_F16  16-bit storage of links and Krylov/operator vectors,
+ *            FP32 arithmetic; residual and solution kept in FP32. */
+typedef enum { TSM_F64 = 0, TSM_F32 = 1, TSM_BF16 = 2, TSM_F16 = 3 } tsm_prec;
+
+typedef struct {
+  int L[4];            /* Lx, Ly, Lz, T */
+  double kappa;        /* hopping parameter */
+  double mu;           /* twisted mass (sign selects the flavour: +mu = u) */
+  int t_antiperiodic;  /* 1: fermion field antiperiodic in t (hops across t = T-1 <-> 0 get -1) */
+} tm_lattice;
+
+/* Stopping rule of one solve (Sec. 2.2: "a large residual or equivalently a
+ * fixed number of iterations").  The solve is CG on
+ * Dhat^dag Dhat x = Dhat^dag bhat with zero start; it stops after the first
+ * iteration k with ||r_k|| / ||Dhat^dag bhat|| < rel_tol (not squared), or
+ * after max_iter iterations.  rel_tol = 0 gives a fixed iteration count. */
+typedef struct {
+  double rel_tol;
+  int max_iter;
+  int prec;            /* tsm_prec */
+  int reliable;        /* TSM_F32 only: FP64 solution and FP64 residual recomputation
+                          whenever ||r|| fell by reliable_delta since the last one */
+  double reliable_delta; /* 0 -> 0.1 */
+} tm_stop;
+
+/* Per-call statistics of tsm_loops. */
+typedef struct {
+  int n_sources;            /* HP + LP sources processed */
+  long long lp_iters;       /* summed CG iterations of LP solves (HP set + LP set) */
+  long long hp_iters;       /* summed CG iterations of HP solves */
+  int hp_not_converged;     /* HP solves that hit max_iter */
+  double hp_max_true_res;   /* max over HP solves of ||eta - D s|| / ||eta|| */
+  double lp_max_true_res;   /* max over LP solves of the same */
+} tsm_loop_stats;
+
+/* Operators of tm_dslash. */
+enum {
+  TM_OP_FULL = 0,      /* out = D_tm in  (dagger: D_tm^dag in); full lattice */
+  TM_OP_HOP_EO = 1,    /* out_e = H_eo in_o, out_o = 0  (dagger: (H^dag)_eo) */
+  TM_OP_HOP_OE = 2,    /* out_o = H_oe in_e, out_e = 0  (dagger: (H^dag)_oe) */
+  TM_OP_SCHUR = 3,     /* out_e = Dhat in_e, out_o = 0  (dagger: Dhat^dag);
+                          Dhat = 1 - kappa^2 A_ee^-1 H_eo A_oo^-1 H_oe,
+                          A = 1 + 2 i kappa mu gamma_5 */
+  TM_OP_NORMAL = 4     /* out_e = Dhat^dag Dhat in_e, out_o = 0 */
+};
+
+/* Create a context on CUDA device `device`, ordering all work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the handle. */
+int tsm_create(int device, void* cuda_stream, tsm_ctx** out);
+
+/* Free the context and all device memory it owns.  NULL is accepted. */
+int tsm_destroy(tsm_ctx* ctx);
+
+/* Load the gauge field: canonical FP64 links (host or device), converted to the
+ * library's even/odd two-row (12 real) storage in FP64, FP32, FP16 and BF16.
+ * Checks every link for SU(3) (unitary rows, row 3 = conj(row1 x row2)) to
+ * 1e-8 and returns TSM_ERR_NOT_UNITARY otherwise; extents must be even >= 2.
+ * The boundary sign is applied inside the operator, never folded into links. */
+int tsm_load_gauge(tsm_ctx* ctx, const tm_lattice* lat, const double* U, int on_device);
+
+/* Apply an operator (TM_OP_*) to one canonical spinor, with links and vectors
+ * stored in tier `prec` (input rounded to that tier on entry, output written
+ * in FP64).  Sites the operator does not produce are written as zero. */
+int tm_dslash(tsm_ctx* ctx, int prec, int op, int dagger,
+              const double* in, double* out, int on_device);
+
+/* Solve D_tm s_r = b_r for nrhs canonical right-hand sides (b and s each
+ * nrhs * 24 * V doubles, source r at offset r * 24 * V) by even/odd reduction,
+ * CG on the Schur complement normal equations (tier stop->prec) and odd-site
+ * reconstruction.  iters[r] (may be NULL) receives the CG iteration count and
+ * true_res[r] (may be NULL) ||b_r - D_tm s_r|| / ||b_r|| computed in FP64.
+ * Returns TSM_ERR_NOT_CONVERGED if any solve hit max_iter above rel_tol (the
+ * solutions are still written). */
+int tm_solve_batch(tsm_ctx* ctx, int nrhs, const double* b, double* s,
+                   const tm_stop* stop, int on_device, int* iters, double* true_res);
+
+/* Write the canonical noise source eta_j (24 * V doubles) for seed, kind
+ * (4 = Z4, 2 = Z2) and source index j, exactly as the solvers see it. */
+int tsm_noise(tsm_ctx* ctx, uint64_t seed, int kind, uint32_t source,
+              double* out, int on_device);
+
+/* Contract one canonical solution with its regenerated noise source:
+ * out[g][q][t] = sum_{x: x_4 = t} e^{i q.x} eta_j(x)^dag Gamma_g (s_a - s_b)(x),
+ * s_b may be NULL (treated as zero).  gammas: n_gamma indices in [0, 16);
+ * moms: n_q integer triples.  prec TSM_F64 contracts in FP64, TSM_F32 in FP32
+ * per site with FP64 sums over blocks and sites. */
+int tsm_contract(tsm_ctx* ctx, int prec, uint64_t seed, int kind, uint32_t source,
+                 const double* s_a, const double* s_b,
+                 const int* gammas, int n_gamma, const int* moms, int n_q,
+                 double* out, int on_device);
+
+/* TSM parameters (Sec. 2.2, Eq. 2.4).  Sources hp_begin .. hp_end-1 form this
+ * call's part of the HP set and lp_begin .. lp_end-1 its part of the LP set;
+ * a single process passes hp = [0, N_HP) and lp = [N_HP, N_HP + N_LP). */
+typedef struct {
+  uint64_t seed;
+  int noise;                /* 4 = Z4, 2 = Z2 */
+  uint32_t hp_begin, hp_end;
+  uint32_t lp_begin, lp_end;
+  tm_stop hp;               /* stopping rule / tier of the HP solves */
+  tm_stop lp;               /* stopping rule / tier of the LP solves (same map for both sets) */
+  int batch;                /* sources solved together (>= 1; 1 = single-RHS kernels) */
+  const int* gammas; int n_gamma;
+  const int* moms; int n_q; /* host pointers */
+} tsm_params;
+
+/* Run the TSM over this call's source ranges.  Outputs (host or device per
+ * on_device; any may be NULL):
+ *   loops     [n_gamma][n_q][T] complex   the estimate of Eq. 2.4
+ *   err       [n_gamma][n_q][T] double    sigma = sqrt(Var_corr / N_HP + Var_LP / N_LP)
+ *   lp_mean   [n_gamma][n_q][T] complex   LP-only mean over the LP set (biased)
+ *   corr_mean [n_gamma][n_q][T] complex   mean HP - LP correction over the HP set
+ *   per_corr  [hp_end-hp_begin][n_gamma][n_q][T] complex  per-source L(s_HP - s_LP)
+ *   per_lp    [lp_end-lp_begin][n_gamma][n_q][T] complex  per-source L(s_LP)
+ * stats (host, may be NULL) receives iteration counts and residuals.
+ * Var is the unbiased complex sample variance sum |X_j - mean|^2 / (N - 1),
+ * evaluated in two passes in source order (bit-reproducible). */
+int tsm_loops(tsm_ctx* ctx, const tsm_params* p,
+              double* loops, double* err, double* lp_mean, double* corr_mean,
+              double* per_corr, double* per_lp, int on_device, tsm_loop_stats* stats);
+
+/* Combine per-source loops gathered from several processes into the estimate
+ * of Eq. 2.4.  Runs the same device kernel, in the same summation order, as
+ * the final step of tsm_loops, so any split of the source ranges gives
+ * bit-identical results.  per_corr: n_hp x n_entries complex, per_lp:
+ * n_lp x n_entries complex (host or device per on_device); outputs as in
+ * tsm_loops, each n_entries long, any may be NULL. */
+int tsm_combine(tsm_ctx* ctx, const double* per_corr, int n_hp, const double* per_lp, int n_lp,
+                int n_entries, double* loops, double* err, double* lp_mean, double* corr_mean,
+                int on_device);
+
+/* Instrumentation.  tsm_profile(ctx, 1) starts recording CUDA-event times of
+ * hop-kernel launches on the context's stream (in CG solves: the hop kernels
+ * of the first iteration of every chunk); tsm_profile_read returns, per hop
+ * kind k = 0..3 (plain hop, hop + xpay/norm, adjoint hop, adjoint hop + CG
+ * update), the summed milliseconds, launch count and algorithmic bytes.
+ * tsm_launch_count returns the number of library kernels launched so far. */
+int tsm_profile(tsm_ctx* ctx, int enable);
+int tsm_profile_read(tsm_ctx* ctx, double ms[4], long long count[4], double bytes[4]);
+long long tsm_launch_count(tsm_ctx* ctx);
+
+/* One-line message for the last failed call on this thread ("" if none). */
+const char* tsm_last_error(void);
+/* Name of a status code. */
+const char* tsm_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSM_H */

@@ -1,0 +1,568 @@
+// api.cu -- the C ABI (include/tsm.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "contract.h"
+#include "fields.cuh"
+#include "solver.h"
+
+using namespace tsm;
+
+namespace tsm {
+const char* last_error();
+}
+
+namespace {
+
+int bad(int code, const char* msg) {
+  set_error("%s", msg);
+  return code;
+}
+
+int select_device(Ctx& c) {
+  TSM_CUDA(cudaSetDevice(c.device));
+  return TSM_OK;
+}
+
+// device pointer for a caller buffer: the caller's own (on_device) or a
+// workspace staging buffer, optionally filled from host memory
+int stage_in(Ctx& c, const char* name, const double* user, size_t bytes, int on_device, const double** dev) {
+  if (on_device) {
+    *dev = user;
+    return TSM_OK;
+  }
+  void* p = nullptr;
+  TSM_TRY(c.buffer(name, bytes, &p));
+  TSM_CUDA(cudaMemcpyAsync(p, user, bytes, cudaMemcpyHostToDevice, c.stream));
+  *dev = static_cast<const double*>(p);
+  return TSM_OK;
+}
+
+int stage_out_ptr(Ctx& c, const char* name, double* user, size_t bytes, int on_device, double** dev) {
+  if (on_device) {
+    *dev = user;
+    return TSM_OK;
+  }
+  void* p = nullptr;
+  TSM_TRY(c.buffer(name, bytes, &p));
+  *dev = static_cast<double*>(p);
+  return TSM_OK;
+}
+
+int stage_out_finish(Ctx& c, double* user, const double* dev, size_t bytes, int on_device) {
+  if (!on_device && user != nullptr) TSM_CUDA(cudaMemcpyAsync(user, dev, bytes, cudaMemcpyDeviceToHost, c.stream));
+  return TSM_OK;
+}
+
+size_t spinor_bytes(const Ctx& c) { return (size_t)c.g.V * 24 * sizeof(double); }
+
+int pack_eo(Ctx& c, int prec, const double* canon, EOField f) {
+  return dispatch_prec(prec, [&](auto tag) {
+    using S = decltype(tag);
+    TSM_TRY(launch_pack<S>(c, 0, canon, f.e));
+    return launch_pack<S>(c, 1, canon, f.o);
+  });
+}
+
+int unpack_eo(Ctx& c, int prec, EOField f, double* canon) {
+  return dispatch_prec(prec, [&](auto tag) {
+    using S = decltype(tag);
+    TSM_TRY(launch_unpack<S>(c, 0, f.e, canon));
+    return launch_unpack<S>(c, 1, f.o, canon);
+  });
+}
+
+int eo_fields(Ctx& c, const std::string& name, int prec, EOField* f) {
+  TSM_TRY(c.field(name + "_e", prec, &f->e));
+  return c.field(name + "_o", prec, &f->o);
+}
+
+int check_stop(const tm_stop* s) {
+  if (s == nullptr) return bad(TSM_ERR_ARG, "null tm_stop");
+  if (s->prec < TSM_F64 || s->prec > TSM_F16) return bad(TSM_ERR_ARG, "tm_stop.prec out of range");
+  if (s->max_iter < 0 || !(s->rel_tol >= 0.0)) return bad(TSM_ERR_ARG, "tm_stop: max_iter < 0 or rel_tol < 0");
+  return TSM_OK;
+}
+
+template <class S>
+int apply_operator(Ctx& c, int op, int dagger, EOField in, EOField out) {
+  const double k = c.lat.kappa, mu = c.lat.mu, k2 = k * k;
+  const double m = dagger ? -mu : mu;
+  const int zb = (c.g.Vh + SITE_NT - 1) / SITE_NT;
+  auto zero = [&](PField f) {
+    convert_kernel<S, S><<<zb, SITE_NT, 0, c.stream>>>(c.g.Vh, nullptr, f.as<S>(), c.sstride);
+    c.launches++;
+    return check_launch(c, "convert_kernel");
+  };
+  switch (op) {
+    case TM_OP_FULL:
+      for (int par = 0; par < 2; ++par) {
+        HopArgs<S> h = hop_args<S>(c, par);
+        h.in = (par ? in.e : in.o).as<S>();
+        h.center = (par ? in.o : in.e).as<S>();
+        h.tc = twist_A(k, m);
+        h.ac = 1.0;
+        h.ah = -k;
+        h.out = (par ? out.o : out.e).as<S>();
+        TSM_TRY(launch_hop<S>(c, h, dagger, HOP_CENTER, -1));
+      }
+      return TSM_OK;
+    case TM_OP_HOP_EO:
+    case TM_OP_HOP_OE: {
+      const int par = (op == TM_OP_HOP_EO) ? 0 : 1;
+      HopArgs<S> h = hop_args<S>(c, par);
+      h.in = (par ? in.e : in.o).as<S>();
+      h.out = (par ? out.o : out.e).as<S>();
+      TSM_TRY(launch_hop<S>(c, h, dagger, 0, -1));
+      return zero(par ? out.e : out.o);
+    }
+    case TM_OP_SCHUR:
+    case TM_OP_NORMAL: {
+      PField t, w;
+      TSM_TRY(c.field("op_t", S::id, &t));
+      TSM_TRY(c.field("op_w", S::id, &w));
+      PField src = in.e;
+      if (op == TM_OP_NORMAL || !dagger) {
+        // Dhat: t = A^-1 H_oe src ; out = A^-1 (A src - kappa^2 H_eo t)
+        HopArgs<S> h = hop_args<S>(c, 1);
+        h.in = src.as<S>();
+        h.out = t.as<S>();
+        h.to = twist_Ainv(k, mu);
+        TSM_TRY(launch_hop<S>(c, h, 0, 0, -1));
+        h = hop_args<S>(c, 0);
+        h.in = t.as<S>();
+        h.center = src.as<S>();
+        h.tc = twist_A(k, mu);
+        h.ac = 1.0;
+        h.ah = -k2;
+        h.to = twist_Ainv(k, mu);
+        h.out = (op == TM_OP_NORMAL ? w : out.e).as<S>();
+        TSM_TRY(launch_hop<S>(c, h, 0, HOP_CENTER, -1));
+        src = (op == TM_OP_NORMAL) ? w : out.e;
+      }
+      if (op == TM_OP_NORMAL || dagger) {
+        // Dhat^dag: u = A^-1(-mu) src ; t = A^-1(-mu) H^dag_oe u ; out = A(-mu) u - kappa^2 H^dag_eo t
+        PField u;
+        TSM_TRY(c.field("op_u", S::id, &u));
+        TSM_TRY(launch_twist<S>(c, twist_Ainv(k, -mu), src, u, nullptr));
+        HopArgs<S> h = hop_args<S>(c, 1);
+        h.in = u.as<S>();
+        h.out = t.as<S>();
+        h.to = twist_Ainv(k, -mu);
+        TSM_TRY(launch_hop<S>(c, h, 1, 0, -1));
+        h = hop_args<S>(c, 0);
+        h.in = t.as<S>();
+        h.center = u.as<S>();
+        h.tc = twist_A(k, -mu);
+        h.ac = 1.0;
+        h.ah = -k2;
+        h.out = out.e.as<S>();
+        TSM_TRY(launch_hop<S>(c, h, 1, HOP_CENTER, -1));
+      }
+      return zero(out.o);
+    }
+    default:
+      return bad(TSM_ERR_ARG, "unknown operator");
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tsm_last_error(void) { return tsm::last_error(); }
+
+const char* tsm_status_str(int s) {
+  switch (s) {
+    case TSM_OK: return "TSM_OK";
+    case TSM_ERR_ARG: return "TSM_ERR_ARG";
+    case TSM_ERR_DIMS: return "TSM_ERR_DIMS";
+    case TSM_ERR_CUDA: return "TSM_ERR_CUDA";
+    case TSM_ERR_NOT_CONVERGED: return "TSM_ERR_NOT_CONVERGED";
+    case TSM_ERR_NONFINITE: return "TSM_ERR_NONFINITE";
+    case TSM_ERR_TIMEOUT: return "TSM_ERR_TIMEOUT";
+    case TSM_ERR_NOT_UNITARY: return "TSM_ERR_NOT_UNITARY";
+    case TSM_ERR_NO_GAUGE: return "TSM_ERR_NO_GAUGE";
+    case TSM_ERR_TOO_LARGE: return "TSM_ERR_TOO_LARGE";
+    default: return "unknown status";
+  }
+}
+
+int tsm_create(int device, void* cuda_stream, tsm_ctx** out) {
+  if (out == nullptr) return bad(TSM_ERR_ARG, "null output handle");
+  *out = nullptr;
+  int n = 0;
+  TSM_CUDA(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return bad(TSM_ERR_ARG, "device index out of range");
+  tsm_ctx* h = new (std::nothrow) tsm_ctx();
+  if (h == nullptr) return bad(TSM_ERR_ARG, "out of host memory");
+  Ctx& c = h->c;
+  c.device = device;
+  c.stream = static_cast<cudaStream_t>(cuda_stream);
+  int rc = select_device(c);
+  if (rc == TSM_OK && cudaMalloc(&c.states, Ctx::kMaxStates * sizeof(CGState)) != cudaSuccess) rc = TSM_ERR_CUDA;
+  if (rc == TSM_OK && cudaMallocHost(&c.h_states, Ctx::kMaxStates * sizeof(CGState)) != cudaSuccess)
+    rc = TSM_ERR_CUDA;
+  if (rc == TSM_OK && cudaMalloc(&c.red.counter, sizeof(unsigned int)) != cudaSuccess) rc = TSM_ERR_CUDA;
+  if (rc == TSM_OK && cudaMemset(c.red.counter, 0, sizeof(unsigned int)) != cudaSuccess) rc = TSM_ERR_CUDA;
+  if (rc == TSM_OK && cudaMemset(c.states, 0, Ctx::kMaxStates * sizeof(CGState)) != cudaSuccess) rc = TSM_ERR_CUDA;
+  if (rc != TSM_OK) {
+    set_error("tsm_create: device allocation failed");
+    c.free_all();
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return TSM_OK;
+}
+
+int tsm_destroy(tsm_ctx* h) {
+  if (h == nullptr) return TSM_OK;
+  cudaSetDevice(h->c.device);
+  h->c.free_all();
+  delete h;
+  return TSM_OK;
+}
+
+int tsm_load_gauge(tsm_ctx* h, const tm_lattice* lat, const double* U, int on_device) {
+  if (h == nullptr || lat == nullptr || U == nullptr) return bad(TSM_ERR_ARG, "null argument");
+  Ctx& c = h->c;
+  TSM_TRY(select_device(c));
+  long long V = 1;
+  for (int k = 0; k < 4; ++k) {
+    if (lat->L[k] < 2 || (lat->L[k] & 1)) return bad(TSM_ERR_DIMS, "every extent must be even and >= 2");
+    V *= lat->L[k];
+  }
+  if (V * 4 >= (1ll << 31)) return bad(TSM_ERR_DIMS, "lattice too large for 32-bit site indexing");
+  if (!std::isfinite(lat->kappa) || !std::isfinite(lat->mu)) return bad(TSM_ERR_ARG, "kappa / mu not finite");
+  const bool resize = !c.has_gauge || (int)V != c.g.V;
+  c.has_gauge = false;
+  c.lat = *lat;
+  c.g.L[0] = lat->L[0];
+  c.g.L[1] = lat->L[1];
+  c.g.L[2] = lat->L[2];
+  c.g.L[3] = lat->L[3];
+  c.g.V = (int)V;
+  c.g.Vh = (int)(V / 2);
+  c.g.Lxh = lat->L[0] / 2;
+  c.g.apbc = lat->t_antiperiodic ? 1 : 0;
+  c.sstride = c.g.Vh;
+  c.lstride = c.g.Vh;
+  if (resize) {
+    TSM_CUDA(cudaStreamSynchronize(c.stream));
+    for (auto& kv : c.ws) cudaFree(kv.second.first);
+    c.ws.clear();
+    for (int k = 0; k < 4; ++k) {
+      if (c.links[k]) cudaFree(c.links[k]);
+      c.links[k] = nullptr;
+    }
+    const size_t vh = (size_t)c.g.Vh;
+    TSM_CUDA(cudaMalloc(&c.links[TSM_F64], 2 * 4 * F64::LN * vh * sizeof(double2)));
+    TSM_CUDA(cudaMalloc(&c.links[TSM_F32], 2 * 4 * F32::LN * vh * sizeof(float4)));
+    TSM_CUDA(cudaMalloc(&c.links[TSM_BF16], 2 * 4 * BF16::LN * vh * sizeof(uint2)));
+    TSM_CUDA(cudaMalloc(&c.links[TSM_F16], 2 * 4 * F16::LN * vh * sizeof(uint2)));
+    if (c.red.partials) cudaFree(c.red.partials);
+    c.red_cap = vh / 64 + 64;
+    TSM_CUDA(cudaMalloc(&c.red.partials, c.red_cap * sizeof(double)));
+  }
+  const double* dU = nullptr;
+  TSM_TRY(stage_in(c, "gauge_canon", U, (size_t)V * 4 * 9 * 2 * sizeof(double), on_device, &dU));
+  void* dev_max = nullptr;
+  TSM_TRY(c.buffer("gauge_maxdev", sizeof(unsigned int), &dev_max));
+  TSM_CUDA(cudaMemsetAsync(dev_max, 0, sizeof(unsigned int), c.stream));
+  const int nb = (int)((V * 4 + SITE_NT - 1) / SITE_NT);
+  pack_links_kernel<<<nb, SITE_NT, 0, c.stream>>>(
+      c.g, reinterpret_cast<const double2*>(dU), static_cast<double2*>(c.links[TSM_F64]),
+      static_cast<float4*>(c.links[TSM_F32]), static_cast<uint2*>(c.links[TSM_F16]),
+      static_cast<uint2*>(c.links[TSM_BF16]), c.lstride, static_cast<unsigned int*>(dev_max));
+  c.launches++;
+  TSM_TRY(check_launch(c, "pack_links_kernel"));
+  unsigned int bits = 0;
+  TSM_CUDA(cudaMemcpyAsync(&bits, dev_max, sizeof(bits), cudaMemcpyDeviceToHost, c.stream));
+  TSM_CUDA(cudaStreamSynchronize(c.stream));
+  float dev;
+  std::memcpy(&dev, &bits, sizeof(dev));
+  if (!(dev <= 1e-8f)) {
+    set_error("gauge links are not SU(3): max deviation %g", (double)dev);
+    return TSM_ERR_NOT_UNITARY;
+  }
+  c.has_gauge = true;
+  return TSM_OK;
+}
+
+int tm_dslash(tsm_ctx* h, int prec, int op, int dagger, const double* in, double* out, int on_device) {
+  if (h == nullptr || in == nullptr || out == nullptr) return bad(TSM_ERR_ARG, "null argument");
+  Ctx& c = h->c;
+  if (!c.has_gauge) return bad(TSM_ERR_NO_GAUGE, "no gauge field loaded");
+  if (op < TM_OP_FULL || op > TM_OP_NORMAL) return bad(TSM_ERR_ARG, "unknown operator");
+  TSM_TRY(select_device(c));
+  const size_t bytes = spinor_bytes(c);
+  const double* din = nullptr;
+  double* dout = nullptr;
+  TSM_TRY(stage_in(c, "io_in", in, bytes, on_device, &din));
+  TSM_TRY(stage_out_ptr(c, "io_out", out, bytes, on_device, &dout));
+  EOField fi, fo;
+  TSM_TRY(eo_fields(c, "ds_in", prec, &fi));
+  TSM_TRY(eo_fields(c, "ds_out", prec, &fo));
+  TSM_TRY(pack_eo(c, prec, din, fi));
+  c.prof_this_launch = c.profile;
+  int rc = dispatch_prec(prec, [&](auto tag) {
+    using S = decltype(tag);
+    return apply_operator<S>(c, op, dagger ? 1 : 0, fi, fo);
+  });
+  c.prof_this_launch = false;
+  TSM_TRY(rc);
+  TSM_TRY(unpack_eo(c, prec, fo, dout));
+  TSM_TRY(stage_out_finish(c, out, dout, bytes, on_device));
+  TSM_CUDA(cudaStreamSynchronize(c.stream));
+  return c.harvest_events();
+}
+
+int tm_solve_batch(tsm_ctx* h, int nrhs, const double* b, double* s, const tm_stop* stop, int on_device, int* iters,
+                   double* true_res) {
+  if (h == nullptr || b == nullptr || s == nullptr) return bad(TSM_ERR_ARG, "null argument");
+  if (nrhs < 0) return bad(TSM_ERR_ARG, "nrhs < 0");
+  TSM_TRY(check_stop(stop));
+  Ctx& c = h->c;
+  if (!c.has_gauge) return bad(TSM_ERR_NO_GAUGE, "no gauge field loaded");
+  TSM_TRY(select_device(c));
+  const size_t bytes = spinor_bytes(c);
+  const int sp = solution_prec(*stop);
+  EOField fb, fs;
+  TSM_TRY(eo_fields(c, "sv_b", sp, &fb));
+  TSM_TRY(eo_fields(c, "sv_s", sp, &fs));
+  int worst = TSM_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    const double* db = nullptr;
+    double* ds = nullptr;
+    TSM_TRY(stage_in(c, "io_in", b + (size_t)r * c.g.V * 24, bytes, on_device, &db));
+    TSM_TRY(stage_out_ptr(c, "io_out", s + (size_t)r * c.g.V * 24, bytes, on_device, &ds));
+    TSM_TRY(pack_eo(c, sp, db, fb));
+    SolveResult res;
+    TSM_TRY(solve_source(c, *stop, 0, fb, fs, &res));
+    if (iters) iters[r] = res.iters;
+    if (true_res) {
+      double tr = 0.0;
+      TSM_TRY(true_residual(c, sp, fb, fs, &tr));
+      true_res[r] = tr;
+    }
+    TSM_TRY(unpack_eo(c, sp, fs, ds));
+    TSM_TRY(stage_out_finish(c, s + (size_t)r * c.g.V * 24, ds, bytes, on_device));
+    TSM_CUDA(cudaStreamSynchronize(c.stream));
+    if (res.status != TSM_OK) worst = res.status;
+    else if (!res.converged && worst == TSM_OK) worst = TSM_ERR_NOT_CONVERGED;
+  }
+  TSM_TRY(c.harvest_events());
+  if (worst != TSM_OK) set_error("at least one solve %s", worst == TSM_ERR_NONFINITE ? "met NaN/Inf" : "did not converge");
+  return worst;
+}
+
+int tsm_noise(tsm_ctx* h, uint64_t seed, int kind, uint32_t source, double* out, int on_device) {
+  if (h == nullptr || out == nullptr) return bad(TSM_ERR_ARG, "null argument");
+  if (kind != 4 && kind != 2) return bad(TSM_ERR_ARG, "noise kind must be 4 or 2");
+  Ctx& c = h->c;
+  if (!c.has_gauge) return bad(TSM_ERR_NO_GAUGE, "no lattice loaded");
+  TSM_TRY(select_device(c));
+  const size_t bytes = spinor_bytes(c);
+  double* dout = nullptr;
+  TSM_TRY(stage_out_ptr(c, "io_out", out, bytes, on_device, &dout));
+  noise_canon_kernel<<<(c.g.V + SITE_NT - 1) / SITE_NT, SITE_NT, 0, c.stream>>>(c.g.V, make_noise(seed, kind), source,
+                                                                                reinterpret_cast<double2*>(dout));
+  c.launches++;
+  TSM_TRY(check_launch(c, "noise_canon_kernel"));
+  TSM_TRY(stage_out_finish(c, out, dout, bytes, on_device));
+  TSM_CUDA(cudaStreamSynchronize(c.stream));
+  return TSM_OK;
+}
+
+int tsm_contract(tsm_ctx* h, int prec, uint64_t seed, int kind, uint32_t source, const double* s_a,
+                 const double* s_b, const int* gammas, int n_gamma, const int* moms, int n_q, double* out,
+                 int on_device) {
+  if (h == nullptr || s_a == nullptr || out == nullptr) return bad(TSM_ERR_ARG, "null argument");
+  if (kind != 4 && kind != 2) return bad(TSM_ERR_ARG, "noise kind must be 4 or 2");
+  if (prec != TSM_F64 && prec != TSM_F32) return bad(TSM_ERR_ARG, "contraction tier must be TSM_F64 or TSM_F32");
+  Ctx& c = h->c;
+  if (!c.has_gauge) return bad(TSM_ERR_NO_GAUGE, "no lattice loaded");
+  TSM_TRY(select_device(c));
+  ContractPlan plan;
+  TSM_TRY(plan.prepare(c, gammas, n_gamma, moms, n_q));
+  const size_t bytes = spinor_bytes(c);
+  EOField fa, fb;
+  TSM_TRY(eo_fields(c, "ct_a", TSM_F64, &fa));
+  TSM_TRY(eo_fields(c, "ct_b", TSM_F64, &fb));
+  const double* da = nullptr;
+  TSM_TRY(stage_in(c, "io_in", s_a, bytes, on_device, &da));
+  TSM_TRY(pack_eo(c, TSM_F64, da, fa));
+  if (s_b) {
+    const double* db = nullptr;
+    TSM_TRY(stage_in(c, "io_in2", s_b, bytes, on_device, &db));
+    TSM_TRY(pack_eo(c, TSM_F64, db, fb));
+  }
+  const size_t obytes = (size_t)plan.entries(c.lat.L[3]) * sizeof(double2);
+  double* dout = nullptr;
+  TSM_TRY(stage_out_ptr(c, "io_loops", out, obytes, on_device, &dout));
+  const NoiseSpec ns = make_noise(seed, kind);
+  if (prec == TSM_F64)
+    TSM_TRY((launch_contract<double, F64, F64>(c, plan, ns, source, fa, s_b ? &fb : nullptr,
+                                               reinterpret_cast<double2*>(dout))));
+  else
+    TSM_TRY((launch_contract<float, F64, F64>(c, plan, ns, source, fa, s_b ? &fb : nullptr,
+                                              reinterpret_cast<double2*>(dout))));
+  TSM_TRY(stage_out_finish(c, out, dout, obytes, on_device));
+  TSM_CUDA(cudaStreamSynchronize(c.stream));
+  return TSM_OK;
+}
+
+int tsm_loops(tsm_ctx* h, const tsm_params* p, double* loops, double* err, double* lp_mean, double* corr_mean,
+              double* per_corr, double* per_lp, int on_device, tsm_loop_stats* stats) {
+  if (h == nullptr || p == nullptr) return bad(TSM_ERR_ARG, "null argument");
+  Ctx& c = h->c;
+  if (!c.has_gauge) return bad(TSM_ERR_NO_GAUGE, "no gauge field loaded");
+  if (p->noise != 4 && p->noise != 2) return bad(TSM_ERR_ARG, "noise kind must be 4 or 2");
+  if (p->hp_end < p->hp_begin || p->lp_end < p->lp_begin) return bad(TSM_ERR_ARG, "empty-reversed source range");
+  if (p->batch < 1) return bad(TSM_ERR_ARG, "batch must be >= 1");
+  TSM_TRY(check_stop(&p->hp));
+  TSM_TRY(check_stop(&p->lp));
+  TSM_TRY(select_device(c));
+  ContractPlan plan;
+  TSM_TRY(plan.prepare(c, p->gammas, p->n_gamma, p->moms, p->n_q));
+  const int T = c.lat.L[3];
+  const int E = plan.entries(T);
+  const int n_hp = (int)(p->hp_end - p->hp_begin), n_lp = (int)(p->lp_end - p->lp_begin);
+  const int sp_lp = solution_prec(p->lp), sp_hp = solution_prec(p->hp);
+  const bool fp64_path = (p->lp.prec == TSM_F64 && p->hp.prec == TSM_F64);
+  void* vc = nullptr;
+  void* vl = nullptr;
+  TSM_TRY(c.buffer("tsm_per_corr", (size_t)std::max(n_hp, 1) * E * sizeof(double2), &vc));
+  TSM_TRY(c.buffer("tsm_per_lp", (size_t)std::max(n_lp, 1) * E * sizeof(double2), &vl));
+  double2* d_corr = static_cast<double2*>(vc);
+  double2* d_lp = static_cast<double2*>(vl);
+  EOField b_lp, s_lp, b_hp, s_hp;
+  TSM_TRY(eo_fields(c, "tsm_b_lp", sp_lp, &b_lp));
+  TSM_TRY(eo_fields(c, "tsm_s_lp", sp_lp, &s_lp));
+  TSM_TRY(eo_fields(c, "tsm_b_hp", sp_hp, &b_hp));
+  TSM_TRY(eo_fields(c, "tsm_s_hp", sp_hp, &s_hp));
+  const NoiseSpec ns = make_noise(p->seed, p->noise);
+  tsm_loop_stats st{};
+  st.lp_max_true_res = -1.0;
+  auto gen = [&](int prec, uint32_t j, EOField f) {
+    return dispatch_prec(prec, [&](auto tag) {
+      using S = decltype(tag);
+      TSM_TRY(launch_noise<S>(c, 0, ns, j, f.e));
+      return launch_noise<S>(c, 1, ns, j, f.o);
+    });
+  };
+  auto contract = [&](uint32_t j, EOField a, int pa, const EOField* b, int pb, double2* out) {
+    if (fp64_path) return launch_contract<double, F64, F64>(c, plan, ns, j, a, b, out);
+    if (pa == TSM_F64 && (b == nullptr || pb == TSM_F64)) return launch_contract<float, F64, F64>(c, plan, ns, j, a, b, out);
+    if (pa == TSM_F64) return launch_contract<float, F64, F32>(c, plan, ns, j, a, b, out);
+    if (b == nullptr || pb == TSM_F32) return launch_contract<float, F32, F32>(c, plan, ns, j, a, b, out);
+    return launch_contract<float, F32, F64>(c, plan, ns, j, a, b, out);
+  };
+  for (uint32_t j = p->hp_begin; j < p->hp_end; ++j) {
+    SolveResult r_lp, r_hp;
+    TSM_TRY(gen(sp_lp, j, b_lp));
+    TSM_TRY(solve_source(c, p->lp, 0, b_lp, s_lp, &r_lp));
+    if (sp_hp != sp_lp) TSM_TRY(gen(sp_hp, j, b_hp));
+    EOField bh = (sp_hp != sp_lp) ? b_hp : b_lp;
+    TSM_TRY(solve_source(c, p->hp, 1, bh, s_hp, &r_hp));
+    if (r_lp.status != TSM_OK || r_hp.status != TSM_OK) return bad(TSM_ERR_NONFINITE, "NaN/Inf in a solve");
+    double tr = 0.0;
+    TSM_TRY(true_residual(c, sp_hp, bh, s_hp, &tr));
+    st.hp_max_true_res = std::max(st.hp_max_true_res, tr);
+    st.lp_iters += r_lp.iters;
+    st.hp_iters += r_hp.iters;
+    if (!r_hp.converged) st.hp_not_converged++;
+    TSM_TRY(contract(j, s_hp, sp_hp, &s_lp, sp_lp, d_corr + (size_t)(j - p->hp_begin) * E));
+  }
+  for (uint32_t j = p->lp_begin; j < p->lp_end; ++j) {
+    SolveResult r_lp;
+    TSM_TRY(gen(sp_lp, j, b_lp));
+    TSM_TRY(solve_source(c, p->lp, 0, b_lp, s_lp, &r_lp));
+    if (r_lp.status != TSM_OK) return bad(TSM_ERR_NONFINITE, "NaN/Inf in a solve");
+    st.lp_iters += r_lp.iters;
+    TSM_TRY(contract(j, s_lp, sp_lp, nullptr, sp_lp, d_lp + (size_t)(j - p->lp_begin) * E));
+  }
+  st.n_sources = n_hp + n_lp;
+  // Eq. 2.4 combine
+  double *d_est = nullptr, *d_err = nullptr, *d_lpm = nullptr, *d_cm = nullptr;
+  const size_t cb = (size_t)E * sizeof(double2), rb = (size_t)E * sizeof(double);
+  if (loops) TSM_TRY(stage_out_ptr(c, "out_est", loops, cb, on_device, &d_est));
+  if (err) TSM_TRY(stage_out_ptr(c, "out_err", err, rb, on_device, &d_err));
+  if (lp_mean) TSM_TRY(stage_out_ptr(c, "out_lpm", lp_mean, cb, on_device, &d_lpm));
+  if (corr_mean) TSM_TRY(stage_out_ptr(c, "out_cm", corr_mean, cb, on_device, &d_cm));
+  TSM_TRY(launch_combine(c, d_corr, n_hp, d_lp, n_lp, E, reinterpret_cast<double2*>(d_est), d_err,
+                         reinterpret_cast<double2*>(d_lpm), reinterpret_cast<double2*>(d_cm)));
+  if (loops) TSM_TRY(stage_out_finish(c, loops, d_est, cb, on_device));
+  if (err) TSM_TRY(stage_out_finish(c, err, d_err, rb, on_device));
+  if (lp_mean) TSM_TRY(stage_out_finish(c, lp_mean, d_lpm, cb, on_device));
+  if (corr_mean) TSM_TRY(stage_out_finish(c, corr_mean, d_cm, cb, on_device));
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (per_corr && n_hp > 0) TSM_CUDA(cudaMemcpyAsync(per_corr, d_corr, (size_t)n_hp * cb, k, c.stream));
+  if (per_lp && n_lp > 0) TSM_CUDA(cudaMemcpyAsync(per_lp, d_lp, (size_t)n_lp * cb, k, c.stream));
+  TSM_CUDA(cudaStreamSynchronize(c.stream));
+  TSM_TRY(c.harvest_events());
+  if (stats) *stats = st;
+  return TSM_OK;
+}
+
+int tsm_combine(tsm_ctx* h, const double* per_corr, int n_hp, const double* per_lp, int n_lp, int n_entries,
+                double* loops, double* err, double* lp_mean, double* corr_mean, int on_device) {
+  if (h == nullptr || n_hp < 0 || n_lp < 0 || n_entries < 0) return bad(TSM_ERR_ARG, "bad argument");
+  if ((n_hp > 0 && per_corr == nullptr) || (n_lp > 0 && per_lp == nullptr)) return bad(TSM_ERR_ARG, "null input");
+  Ctx& c = h->c;
+  TSM_TRY(select_device(c));
+  const size_t cb = (size_t)n_entries * sizeof(double2), rb = (size_t)n_entries * sizeof(double);
+  const double *dc = nullptr, *dl = nullptr;
+  if (n_hp > 0) TSM_TRY(stage_in(c, "cmb_corr", per_corr, (size_t)n_hp * cb, on_device, &dc));
+  if (n_lp > 0) TSM_TRY(stage_in(c, "cmb_lp", per_lp, (size_t)n_lp * cb, on_device, &dl));
+  double *d_est = nullptr, *d_err = nullptr, *d_lpm = nullptr, *d_cm = nullptr;
+  if (loops) TSM_TRY(stage_out_ptr(c, "out_est", loops, cb, on_device, &d_est));
+  if (err) TSM_TRY(stage_out_ptr(c, "out_err", err, rb, on_device, &d_err));
+  if (lp_mean) TSM_TRY(stage_out_ptr(c, "out_lpm", lp_mean, cb, on_device, &d_lpm));
+  if (corr_mean) TSM_TRY(stage_out_ptr(c, "out_cm", corr_mean, cb, on_device, &d_cm));
+  TSM_TRY(launch_combine(c, reinterpret_cast<const double2*>(dc), n_hp, reinterpret_cast<const double2*>(dl), n_lp,
+                         n_entries, reinterpret_cast<double2*>(d_est), d_err, reinterpret_cast<double2*>(d_lpm),
+                         reinterpret_cast<double2*>(d_cm)));
+  if (loops) TSM_TRY(stage_out_finish(c, loops, d_est, cb, on_device));
+  if (err) TSM_TRY(stage_out_finish(c, err, d_err, rb, on_device));
+  if (lp_mean) TSM_TRY(stage_out_finish(c, lp_mean, d_lpm, cb, on_device));
+  if (corr_mean) TSM_TRY(stage_out_finish(c, corr_mean, d_cm, cb, on_device));
+  TSM_CUDA(cudaStreamSynchronize(c.stream));
+  return TSM_OK;
+}
+
+int tsm_profile(tsm_ctx* h, int enable) {
+  if (h == nullptr) return bad(TSM_ERR_ARG, "null context");
+  Ctx& c = h->c;
+  TSM_TRY(select_device(c));
+  TSM_TRY(c.harvest_events());
+  c.profile = enable != 0;
+  if (enable) {
+    for (int k = 0; k < 4; ++k) {
+      c.prof_ms[k] = 0.0;
+      c.prof_cnt[k] = 0;
+      c.prof_bytes[k] = 0.0;
+    }
+  }
+  return TSM_OK;
+}
+
+int tsm_profile_read(tsm_ctx* h, double ms[4], long long count[4], double bytes[4]) {
+  if (h == nullptr) return bad(TSM_ERR_ARG, "null context");
+  Ctx& c = h->c;
+  TSM_TRY(select_device(c));
+  TSM_TRY(c.harvest_events());
+  for (int k = 0; k < 4; ++k) {
+    if (ms) ms[k] = c.prof_ms[k];
+    if (count) count[k] = c.prof_cnt[k];
+    if (bytes) bytes[k] = c.prof_bytes[k];
+  }
+  return TSM_OK;
+}
+
+long long tsm_launch_count(tsm_ctx* h) { return h ? h->c.launches : -1; }
+
+}  // extern "C"

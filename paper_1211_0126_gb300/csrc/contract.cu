@@ -1,0 +1,202 @@
+// contract.cu -- host side of the loop contraction: insertion tables, phase
+// tables, launches of the contraction / reduction / combine kernels.
+#include <cmath>
+#include <complex>
+
+#include "contract.h"
+
+namespace tsm {
+
+// The 16 insertions in the chiral basis, reduced to (column, power of i) per
+// row.  Built here from the gamma matrices themselves:
+// gamma_k = [[0, -i sigma_k], [i sigma_k, 0]], gamma_4 = [[0, 1], [1, 0]].
+static void build_insertions(std::complex<double> G[16][4][4]) {
+  using C = std::complex<double>;
+  const C I(0.0, 1.0);
+  C sig[3][2][2] = {{{0.0, 1.0}, {1.0, 0.0}}, {{0.0, -I}, {I, 0.0}}, {{1.0, 0.0}, {0.0, -1.0}}};
+  C g[4][4][4] = {};
+  for (int k = 0; k < 3; ++k)
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        g[k][a][2 + b] = -I * sig[k][a][b];
+        g[k][2 + a][b] = I * sig[k][a][b];
+      }
+  for (int a = 0; a < 2; ++a) {
+    g[3][a][2 + a] = 1.0;
+    g[3][2 + a][a] = 1.0;
+  }
+  auto mul = [](const C A[4][4], const C B[4][4], C out[4][4]) {
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        C s = 0.0;
+        for (int k = 0; k < 4; ++k) s += A[i][k] * B[k][j];
+        out[i][j] = s;
+      }
+  };
+  C g5[4][4], t1[4][4], t2[4][4];
+  mul(g[0], g[1], t1);
+  mul(t1, g[2], t2);
+  mul(t2, g[3], g5);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) G[0][i][j] = (i == j) ? 1.0 : 0.0;
+  for (int m = 0; m < 4; ++m)
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) G[1 + m][i][j] = g[m][i][j];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) G[5][i][j] = g5[i][j];
+  for (int m = 0; m < 4; ++m) mul(g[m], g5, G[6 + m]);
+  const int pairs[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+  for (int k = 0; k < 6; ++k) {
+    C ab[4][4], ba[4][4];
+    mul(g[pairs[k][0]], g[pairs[k][1]], ab);
+    mul(g[pairs[k][1]], g[pairs[k][0]], ba);
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) G[10 + k][i][j] = 0.5 * I * (ab[i][j] - ba[i][j]);
+  }
+}
+
+int make_gamma_tab(const int* gammas, int n, GammaTab* tab) {
+  if (n < 1 || n > CT_MAXG) {
+    set_error("n_gamma must be in [1, %d]", CT_MAXG);
+    return TSM_ERR_ARG;
+  }
+  std::complex<double> G[16][4][4];
+  build_insertions(G);
+  tab->n = n;
+  for (int k = 0; k < n; ++k) {
+    const int gi = gammas[k];
+    if (gi < 0 || gi > 15) {
+      set_error("gamma index %d out of [0, 16)", gi);
+      return TSM_ERR_ARG;
+    }
+    for (int row = 0; row < 4; ++row) {
+      int found = 0;
+      for (int col = 0; col < 4; ++col) {
+        const std::complex<double> v = G[gi][row][col];
+        if (std::abs(v) < 1e-12) continue;
+        int ph;
+        if (std::abs(v - 1.0) < 1e-12) ph = 0;
+        else if (std::abs(v - std::complex<double>(0, 1)) < 1e-12) ph = 1;
+        else if (std::abs(v + 1.0) < 1e-12) ph = 2;
+        else if (std::abs(v - std::complex<double>(0, -1)) < 1e-12) ph = 3;
+        else {
+          set_error("insertion %d is not a signed permutation", gi);
+          return TSM_ERR_ARG;
+        }
+        tab->col[k][row] = (int8_t)col;
+        tab->ph[k][row] = (int8_t)ph;
+        ++found;
+      }
+      if (found != 1) {
+        set_error("insertion %d row %d has %d non-zeros", gi, row, found);
+        return TSM_ERR_ARG;
+      }
+    }
+  }
+  return TSM_OK;
+}
+
+int ContractPlan::prepare(Ctx& c, const int* gammas, int n_gamma, const int* moms, int n_q_) {
+  if (moms == nullptr || gammas == nullptr || n_q_ < 1) {
+    set_error("gammas / moms must be non-null, n_q >= 1");
+    return TSM_ERR_ARG;
+  }
+  TSM_TRY(make_gamma_tab(gammas, n_gamma, &gam));
+  n_q = n_q_;
+  ng = n_gamma;
+  const int* L = c.lat.L;
+  std::vector<double2> tab((size_t)n_q * (L[0] + L[1] + L[2]));
+  const double twopi = 2.0 * std::acos(-1.0);
+  size_t off = 0;
+  for (int ax = 0; ax < 3; ++ax)
+    for (int q = 0; q < n_q; ++q)
+      for (int x = 0; x < L[ax]; ++x) {
+        // reduce n*x mod L exactly in integers before the angle is formed
+        long long nx = (long long)moms[3 * q + ax] * x;
+        nx %= L[ax];
+        if (nx < 0) nx += L[ax];
+        const double ang = twopi * (double)nx / (double)L[ax];
+        tab[off++] = make_double2(std::cos(ang), std::sin(ang));
+      }
+  void* dev = nullptr;
+  TSM_TRY(c.buffer("phase_tab", tab.size() * sizeof(double2), &dev));
+  TSM_CUDA(cudaMemcpyAsync(dev, tab.data(), tab.size() * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
+  TSM_CUDA(cudaStreamSynchronize(c.stream));
+  phx = static_cast<double2*>(dev);
+  phy = phx + (size_t)n_q * L[0];
+  phz = phy + (size_t)n_q * L[1];
+  return TSM_OK;
+}
+
+template <class R, class SA, class SB>
+int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint32_t source, EOField a,
+                    const EOField* b, double2* out) {
+  constexpr int NT = ContractNT<R>::value;
+  const int vs2 = c.lat.L[0] * c.lat.L[1] * c.lat.L[2] / 2;
+  const int T = c.lat.L[3];
+  const int nbx = (vs2 + NT - 1) / NT;
+  for (int q0 = 0; q0 < plan.n_q; q0 += CT_MAXQ) {
+    const int nq = std::min(CT_MAXQ, plan.n_q - q0);
+    const int nout = plan.ng * nq;
+    void* part = nullptr;
+    TSM_TRY(c.buffer("contract_partial", (size_t)T * 2 * nbx * CT_MAXG * CT_MAXQ * sizeof(double2), &part));
+    ContractArgs<SA, SB> args{};
+    args.g = c.g;
+    args.noise = ns;
+    args.source = source;
+    args.a[0] = a.e.as<SA>();
+    args.a[1] = a.o.as<SA>();
+    args.b[0] = b ? b->e.as<SB>() : nullptr;
+    args.b[1] = b ? b->o.as<SB>() : nullptr;
+    args.sstride = c.sstride;
+    args.gam = plan.gam;
+    args.nq = nq;
+    args.phx = plan.phx + (size_t)q0 * c.lat.L[0];
+    args.phy = plan.phy + (size_t)q0 * c.lat.L[1];
+    args.phz = plan.phz + (size_t)q0 * c.lat.L[2];
+    args.partial = static_cast<double2*>(part);
+    args.nbx = nbx;
+    dim3 grid(nbx, T, 2);
+    contract_kernel<R, SA, SB><<<grid, NT, 0, c.stream>>>(args);
+    c.launches++;
+    TSM_TRY(check_launch(c, "contract_kernel"));
+    const int nred = nout * T;
+    contract_reduce_kernel<<<(nred + 127) / 128, 128, 0, c.stream>>>(static_cast<double2*>(part), T, nbx, plan.ng,
+                                                                      nq, plan.n_q, q0, out);
+    c.launches++;
+    TSM_TRY(check_launch(c, "contract_reduce_kernel"));
+  }
+  return TSM_OK;
+}
+
+template int launch_contract<double, F64, F64>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
+                                               const EOField*, double2*);
+template int launch_contract<float, F64, F64>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
+                                              const EOField*, double2*);
+template int launch_contract<float, F32, F32>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
+                                              const EOField*, double2*);
+template int launch_contract<float, F64, F32>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
+                                              const EOField*, double2*);
+template int launch_contract<double, F64, F32>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
+                                               const EOField*, double2*);
+template int launch_contract<float, F32, F64>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
+                                              const EOField*, double2*);
+
+int launch_combine(Ctx& c, const double2* corr, int n_hp, const double2* lp, int n_lp, int E, double2* est,
+                   double* err, double2* lp_mean, double2* corr_mean) {
+  if (E <= 0) return TSM_OK;
+  combine_kernel<<<(E + 127) / 128, 128, 0, c.stream>>>(corr, n_hp, lp, n_lp, E, est, err, lp_mean, corr_mean);
+  c.launches++;
+  return check_launch(c, "combine_kernel");
+}
+
+NoiseSpec make_noise(uint64_t seed, int kind) {
+  NoiseSpec n{};
+  n.k0 = (uint32_t)(seed & 0xffffffffull);
+  n.k1 = (uint32_t)(seed >> 32);
+  n.kind = kind;
+  n.amp = (kind == 4) ? 1.0 / std::sqrt(2.0) : 1.0;
+  return n;
+}
+
+}  // namespace tsm

@@ -1,0 +1,207 @@
+// contract.cuh -- loop contraction with timeslice / momentum reduction, and the
+// TSM combine.
+//
+// Per source j and site x:  S_ab(x) = sum_c conj(eta_a,c(x)) s_b,c(x)  (4x4 in spin),
+// Gamma_g trace  G_g(x) = sum_a Gamma_g[a][col_g(a)] S_{a, col_g(a)}  (every
+// insertion has one non-zero per row, a power of i), and
+// L(g, q, t) = sum_{x: x_4 = t} e^{i q.x} G_g(x).
+// The noise is regenerated from the counter generator, never read from memory.
+// Phases come from per-axis FP64 tables built on the host (no device sin/cos).
+#pragma once
+
+#include "common.cuh"
+
+namespace tsm {
+
+constexpr int CT_MAXG = 16;
+constexpr int CT_MAXQ = 16;
+
+struct GammaTab {
+  int n;                       // insertions in use
+  int8_t col[CT_MAXG][4];      // column of the non-zero in row a
+  int8_t ph[CT_MAXG][4];       // its value i^ph (0: 1, 1: i, 2: -1, 3: -i)
+};
+
+template <class SA, class SB>
+struct ContractArgs {
+  Geom g;
+  NoiseSpec noise;
+  uint32_t source;
+  const typename SA::schunk* a[2];   // even, odd
+  const typename SB::schunk* b[2];   // may be null
+  int sstride;
+  GammaTab gam;
+  int nq;
+  const double2* phx;   // [nq][Lx]
+  const double2* phy;   // [nq][Ly]
+  const double2* phz;   // [nq][Lz]
+  double2* partial;     // [T][2][nbx][ng*nq]
+  int nbx;
+};
+
+template <class R>
+__device__ __forceinline__ cx<R> times_ipow(cx<R> v, int p) {
+  switch (p & 3) {
+    case 0: return v;
+    case 1: return {-v.im, v.re};
+    case 2: return {-v.re, -v.im};
+    default: return {v.im, -v.re};
+  }
+}
+
+template <class R> struct ContractNT { static constexpr int value = 128; };
+template <> struct ContractNT<double> { static constexpr int value = 64; };
+
+template <class R, class SA, class SB>
+__global__ void __launch_bounds__(ContractNT<R>::value) contract_kernel(const ContractArgs<SA, SB> a) {
+  constexpr int NT = ContractNT<R>::value;
+  __shared__ cx<R> Gs[NT][CT_MAXG + 1];
+  __shared__ cx<R> Ps[NT][CT_MAXQ + 1];
+  const int t = blockIdx.y, parity = blockIdx.z;
+  const int vs2 = a.g.L[0] * a.g.L[1] * a.g.L[2] / 2;
+  const int local = blockIdx.x * NT + threadIdx.x;
+  const int ng = a.gam.n, nq = a.nq;
+  if (local < vs2) {
+    const int ih = t * vs2 + local;
+    int c[4];
+    site_coords(a.g, parity, ih, c);
+    const uint32_t lex = (uint32_t)(((c[3] * a.g.L[2] + c[2]) * a.g.L[1] + c[1]) * a.g.L[0] + c[0]);
+    cx<R> eta[12], s[12];
+    noise_site<R>(a.noise, lex, a.source, eta);
+    {
+      cx<typename SA::real> va[12];
+      load_spinor<SA>(a.a[parity], a.sstride, ih, va);
+      if (a.b[0] != nullptr) {
+        cx<typename SB::real> vb[12];
+        load_spinor<SB>(a.b[parity], a.sstride, ih, vb);
+        using W = typename SA::real;  // subtract in the solution's own precision
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          const W re = va[k].re - (W)vb[k].re, im = va[k].im - (W)vb[k].im;
+          s[k] = {(R)re, (R)im};
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) s[k] = {(R)va[k].re, (R)va[k].im};
+      }
+    }
+    cx<R> S[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        cx<R> acc = cjmul(eta[3 * x], s[3 * y]);
+        acc = acc + cjmul(eta[3 * x + 1], s[3 * y + 1]);
+        acc = acc + cjmul(eta[3 * x + 2], s[3 * y + 2]);
+        S[x][y] = acc;
+      }
+    for (int k = 0; k < ng; ++k) {
+      cx<R> v = {0, 0};
+#pragma unroll
+      for (int row = 0; row < 4; ++row) {
+        const int col = a.gam.col[k][row];
+        cx<R> sv;
+        switch (col) {   // keep S in registers: no dynamic indexing
+          case 0: sv = S[row][0]; break;
+          case 1: sv = S[row][1]; break;
+          case 2: sv = S[row][2]; break;
+          default: sv = S[row][3]; break;
+        }
+        v = v + times_ipow(sv, a.gam.ph[k][row]);
+      }
+      Gs[threadIdx.x][k] = v;
+    }
+    for (int q = 0; q < nq; ++q) {
+      const double2 ex = __ldg(a.phx + q * a.g.L[0] + c[0]);
+      const double2 ey = __ldg(a.phy + q * a.g.L[1] + c[1]);
+      const double2 ez = __ldg(a.phz + q * a.g.L[2] + c[2]);
+      cx<R> p = cx<R>{(R)ex.x, (R)ex.y} * cx<R>{(R)ey.x, (R)ey.y};
+      p = p * cx<R>{(R)ez.x, (R)ez.y};
+      Ps[threadIdx.x][q] = p;
+    }
+  } else {
+    for (int k = 0; k < ng; ++k) Gs[threadIdx.x][k] = {0, 0};
+    for (int q = 0; q < nq; ++q) Ps[threadIdx.x][q] = {0, 0};
+  }
+  __syncthreads();
+  // one (g, q) output per thread: sum over the block's sites in site order
+  const int nout = ng * nq;
+  double2* dst = a.partial + ((size_t)(t * 2 + parity) * a.nbx + blockIdx.x) * nout;
+  for (int k = threadIdx.x; k < nout; k += NT) {
+    const int gi = k % ng, q = k / ng;
+    cx<R> acc = {0, 0};
+    for (int s2 = 0; s2 < NT; ++s2) acc = acc + Ps[s2][q] * Gs[s2][gi];
+    dst[k] = make_double2((double)acc.re, (double)acc.im);
+  }
+}
+
+// sum the block partials of one timeslice in fixed order into the output
+// layout [g][q][t] (momenta q0 .. q0+nq-1 of nq_total)
+static __global__ void contract_reduce_kernel(const double2* __restrict__ partial, int T, int nbx, int ng, int nq,
+                                       int nq_total, int q0, double2* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // k = (q * ng + g) * T + t
+  const int nout = ng * nq;
+  if (k >= nout * T) return;
+  const int t = k % T, gq = k / T;
+  double re = 0.0, im = 0.0;
+  for (int par = 0; par < 2; ++par)
+    for (int b = 0; b < nbx; ++b) {
+      const double2 v = partial[((size_t)(t * 2 + par) * nbx + b) * nout + gq];
+      re += v.x;
+      im += v.y;
+    }
+  const int gi = gq % ng, q = gq / ng;
+  out[((size_t)gi * nq_total + q0 + q) * T + t] = make_double2(re, im);
+}
+
+// Eq. 2.4 per entry: mean of the corrections + mean of the LP set; error from
+// the unbiased complex sample variances, two passes in source order.
+static __global__ void combine_kernel(const double2* __restrict__ corr, int n_hp, const double2* __restrict__ lp, int n_lp,
+                               int E, double2* __restrict__ est, double* __restrict__ err,
+                               double2* __restrict__ lp_mean, double2* __restrict__ corr_mean) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  double mcr = 0.0, mci = 0.0, mlr = 0.0, mli = 0.0, var = 0.0;
+  if (n_hp > 0) {
+    for (int j = 0; j < n_hp; ++j) {
+      const double2 v = corr[(size_t)j * E + e];
+      mcr += v.x;
+      mci += v.y;
+    }
+    mcr /= n_hp;
+    mci /= n_hp;
+    if (n_hp > 1) {
+      double s = 0.0;
+      for (int j = 0; j < n_hp; ++j) {
+        const double2 v = corr[(size_t)j * E + e];
+        const double dr = v.x - mcr, di = v.y - mci;
+        s += dr * dr + di * di;
+      }
+      var += s / (n_hp - 1) / n_hp;
+    }
+  }
+  if (n_lp > 0) {
+    for (int j = 0; j < n_lp; ++j) {
+      const double2 v = lp[(size_t)j * E + e];
+      mlr += v.x;
+      mli += v.y;
+    }
+    mlr /= n_lp;
+    mli /= n_lp;
+    if (n_lp > 1) {
+      double s = 0.0;
+      for (int j = 0; j < n_lp; ++j) {
+        const double2 v = lp[(size_t)j * E + e];
+        const double dr = v.x - mlr, di = v.y - mli;
+        s += dr * dr + di * di;
+      }
+      var += s / (n_lp - 1) / n_lp;
+    }
+  }
+  if (est) est[e] = make_double2(mcr + mlr, mci + mli);
+  if (err) err[e] = sqrt(var);
+  if (lp_mean) lp_mean[e] = make_double2(mlr, mli);
+  if (corr_mean) corr_mean[e] = make_double2(mcr, mci);
+}
+
+}  // namespace tsm

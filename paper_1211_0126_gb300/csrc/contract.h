@@ -1,0 +1,30 @@
+// contract.h -- host interface of the contraction and combine kernels.
+#pragma once
+
+#include "context.h"
+#include "contract.cuh"
+
+namespace tsm {
+
+struct ContractPlan {
+  GammaTab gam{};
+  int ng = 0, n_q = 0;
+  const double2* phx = nullptr;   // device phase tables [n_q][Lx], [n_q][Ly], [n_q][Lz]
+  const double2* phy = nullptr;
+  const double2* phz = nullptr;
+  int prepare(Ctx& c, const int* gammas, int n_gamma, const int* moms, int n_q);
+  int entries(int T) const { return ng * n_q * T; }
+};
+
+int make_gamma_tab(const int* gammas, int n, GammaTab* tab);
+NoiseSpec make_noise(uint64_t seed, int kind);
+
+// out[g][q][t] (device, complex) = sum_t-slice e^{iqx} eta^dag Gamma_g (a - b)
+template <class R, class SA, class SB>
+int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint32_t source, EOField a,
+                    const EOField* b, double2* out);
+
+int launch_combine(Ctx& c, const double2* corr, int n_hp, const double2* lp, int n_lp, int E, double2* est,
+                   double* err, double2* lp_mean, double2* corr_mean);
+
+}  // namespace tsm

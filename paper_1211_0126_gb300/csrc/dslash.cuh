@@ -1,0 +1,308 @@
+// dslash.cuh -- the half-lattice Wilson hopping stencil with twisted-mass
+// epilogues, and the fused CG-update kernel.
+//
+// H_{p <- 1-p} psi (x) = sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+//                               + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu) ]
+// evaluated for the sites x of one parity p; the adjoint stencil H^dag swaps
+// the two projectors.  Each hop projects the neighbour spinor onto two spin
+// components (the (1 +- gamma_mu) projectors have rank 2 in the chiral basis),
+// multiplies by the two-row-reconstructed SU(3) link and rebuilds the lower
+// spin components from the upper ones.  Hops crossing t = T-1 <-> 0 are
+// multiplied by -1 for an antiperiodic fermion field.
+#pragma once
+
+#include "common.cuh"
+
+namespace tsm {
+
+// ------------------------------------------------------------- projectors
+// (1 + s gamma_mu) psi = [h ; M_mu^s h] with h = psi_up - s (i sigma_mu) psi_dn
+// (k = x, y, z) or h = psi_up + s psi_dn (t).  i sigma_1 v = (i v1, i v0),
+// i sigma_2 v = (v1, -v0), i sigma_3 v = (i v0, -i v1).
+template <int MU, int SG, class R>
+__device__ __forceinline__ void project(const cx<R> v[12], cx<R> h[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cx<R> p0 = v[c], p1 = v[3 + c], p2 = v[6 + c], p3 = v[9 + c];
+    if constexpr (MU == 0) {
+      h[c] = (SG > 0) ? p0 - times_i(p3) : p0 + times_i(p3);
+      h[3 + c] = (SG > 0) ? p1 - times_i(p2) : p1 + times_i(p2);
+    } else if constexpr (MU == 1) {
+      h[c] = (SG > 0) ? p0 - p3 : p0 + p3;
+      h[3 + c] = (SG > 0) ? p1 + p2 : p1 - p2;
+    } else if constexpr (MU == 2) {
+      h[c] = (SG > 0) ? p0 - times_i(p2) : p0 + times_i(p2);
+      h[3 + c] = (SG > 0) ? p1 + times_i(p3) : p1 - times_i(p3);
+    } else {
+      h[c] = (SG > 0) ? p0 + p2 : p0 - p2;
+      h[3 + c] = (SG > 0) ? p1 + p3 : p1 - p3;
+    }
+  }
+}
+
+// acc += (1 + s gamma_mu)-reconstruction of the link-multiplied half spinor u
+template <int MU, int SG, class R>
+__device__ __forceinline__ void accumulate(cx<R> acc[12], const cx<R> u[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cx<R> u0 = u[c], u1 = u[3 + c];
+    acc[c] = acc[c] + u0;
+    acc[3 + c] = acc[3 + c] + u1;
+    if constexpr (MU == 0) {        // lower = s i sigma_1 h = s (i h1, i h0)
+      acc[6 + c] = (SG > 0) ? acc[6 + c] + times_i(u1) : acc[6 + c] - times_i(u1);
+      acc[9 + c] = (SG > 0) ? acc[9 + c] + times_i(u0) : acc[9 + c] - times_i(u0);
+    } else if constexpr (MU == 1) { // lower = s (h1, -h0)
+      acc[6 + c] = (SG > 0) ? acc[6 + c] + u1 : acc[6 + c] - u1;
+      acc[9 + c] = (SG > 0) ? acc[9 + c] - u0 : acc[9 + c] + u0;
+    } else if constexpr (MU == 2) { // lower = s (i h0, -i h1)
+      acc[6 + c] = (SG > 0) ? acc[6 + c] + times_i(u0) : acc[6 + c] - times_i(u0);
+      acc[9 + c] = (SG > 0) ? acc[9 + c] - times_i(u1) : acc[9 + c] + times_i(u1);
+    } else {                        // lower = s h
+      acc[6 + c] = (SG > 0) ? acc[6 + c] + u0 : acc[6 + c] - u0;
+      acc[9 + c] = (SG > 0) ? acc[9 + c] + u1 : acc[9 + c] - u1;
+    }
+  }
+}
+
+// u = U h (dag = false) or U^dag h (dag = true) on both spin components of h
+template <bool DAGU, class R>
+__device__ __forceinline__ void su3_mul(const cx<R> r[6], const cx<R> h[6], cx<R> u[6]) {
+  cx<R> w[3];
+  third_row(r, w);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const cx<R> a = h[3 * s], b = h[3 * s + 1], c = h[3 * s + 2];
+    if constexpr (!DAGU) {
+      u[3 * s + 0] = r[0] * a + r[1] * b + r[2] * c;
+      u[3 * s + 1] = r[3] * a + r[4] * b + r[5] * c;
+      u[3 * s + 2] = w[0] * a + w[1] * b + w[2] * c;
+    } else {
+      u[3 * s + 0] = cjmul(r[0], a) + cjmul(r[3], b) + cjmul(w[0], c);
+      u[3 * s + 1] = cjmul(r[1], a) + cjmul(r[4], b) + cjmul(w[1], c);
+      u[3 * s + 2] = cjmul(r[2], a) + cjmul(r[5], b) + cjmul(w[2], c);
+    }
+  }
+}
+
+// One direction of the stencil at output site (c, ih) of parity p.
+// Uout: links of the output parity, Uin: links of the input parity.
+template <class S, int DAG, int MU>
+__device__ __forceinline__ void hop_dir(const Geom& g, int ih, const int c[4],
+                                        const typename S::lchunk* __restrict__ Uout,
+                                        const typename S::lchunk* __restrict__ Uin, int lstride,
+                                        const typename S::schunk* __restrict__ in, int sstride,
+                                        cx<typename S::real> acc[12]) {
+  using R = typename S::real;
+  constexpr int SF = DAG ? +1 : -1;   // forward hop: (1 + SF gamma_mu)
+  constexpr int SB = -SF;             // backward hop
+  cx<R> v[12], h[6], u[6], r[6];
+  // forward neighbour x + mu
+  {
+    int x = c[0], y = c[1], z = c[2], t = c[3];
+    if constexpr (MU == 0) x = (x + 1 == g.L[0]) ? 0 : x + 1;
+    if constexpr (MU == 1) y = (y + 1 == g.L[1]) ? 0 : y + 1;
+    if constexpr (MU == 2) z = (z + 1 == g.L[2]) ? 0 : z + 1;
+    if constexpr (MU == 3) t = (t + 1 == g.L[3]) ? 0 : t + 1;
+    const int nf = half_index(g, x, y, z, t);
+    load_spinor<S>(in, sstride, nf, v);
+    project<MU, SF>(v, h);
+    if constexpr (MU == 3) {
+      if (g.apbc && c[3] == g.L[3] - 1) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) h[k] = (R)(-1) * h[k];
+      }
+    }
+    load_link<S>(Uout, lstride, MU, ih, r);
+    su3_mul<false>(r, h, u);
+    accumulate<MU, SF>(acc, u);
+  }
+  // backward neighbour x - mu
+  {
+    int x = c[0], y = c[1], z = c[2], t = c[3];
+    if constexpr (MU == 0) x = (x == 0) ? g.L[0] - 1 : x - 1;
+    if constexpr (MU == 1) y = (y == 0) ? g.L[1] - 1 : y - 1;
+    if constexpr (MU == 2) z = (z == 0) ? g.L[2] - 1 : z - 1;
+    if constexpr (MU == 3) t = (t == 0) ? g.L[3] - 1 : t - 1;
+    const int nb = half_index(g, x, y, z, t);
+    load_spinor<S>(in, sstride, nb, v);
+    project<MU, SB>(v, h);
+    if constexpr (MU == 3) {
+      if (g.apbc && c[3] == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) h[k] = (R)(-1) * h[k];
+      }
+    }
+    load_link<S>(Uin, lstride, MU, nb, r);
+    su3_mul<true>(r, h, u);
+    accumulate<MU, SB>(acc, u);
+  }
+}
+
+template <class S, int DAG>
+__device__ __forceinline__ void hop_site(const Geom& g, int ih, const int c[4],
+                                         const typename S::lchunk* __restrict__ Uout,
+                                         const typename S::lchunk* __restrict__ Uin, int lstride,
+                                         const typename S::schunk* __restrict__ in, int sstride,
+                                         cx<typename S::real> acc[12]) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = {0, 0};
+  hop_dir<S, DAG, 0>(g, ih, c, Uout, Uin, lstride, in, sstride, acc);
+  hop_dir<S, DAG, 1>(g, ih, c, Uout, Uin, lstride, in, sstride, acc);
+  hop_dir<S, DAG, 2>(g, ih, c, Uout, Uin, lstride, in, sstride, acc);
+  hop_dir<S, DAG, 3>(g, ih, c, Uout, Uin, lstride, in, sstride, acc);
+}
+
+// ------------------------------------------------------------- generic hop kernel
+// out(x) = ts * q,  q = base(x) + to * (ac * tc * center(x) + ah * H psi (x))
+// with optional <q, q> reduction.  MODE bits select center / base / norm.
+enum { HOP_CENTER = 1, HOP_NORM = 2, HOP_BASE = 4 };
+
+template <class S>
+struct HopArgs {
+  Geom g;
+  int p_out;                               // parity of the output sites
+  const typename S::lchunk* Uout;          // links of parity p_out
+  const typename S::lchunk* Uin;           // links of parity 1 - p_out
+  int lstride;
+  const typename S::schunk* in;            // parity 1 - p_out
+  const typename S::schunk* center;        // parity p_out (HOP_CENTER)
+  const typename S::schunk* base;          // parity p_out (HOP_BASE)
+  typename S::schunk* out;                 // parity p_out
+  int sstride;
+  double ac, ah;
+  Twist tc, to, ts;
+  const CGState* skip;                     // optional: return at once when skip->done
+  CGState* st;                             // state receiving the HOP_NORM post action
+  RedSlot red;                             // HOP_NORM
+  int post;                                // PostOp for HOP_NORM
+};
+
+constexpr int HOP_NT = 128;
+
+template <class S, int DAG, int MODE>
+__global__ void __launch_bounds__(HOP_NT) hop_kernel(const HopArgs<S> a) {
+  using R = typename S::real;
+  if (a.skip != nullptr && a.skip->done) return;
+  const int ih = blockIdx.x * HOP_NT + threadIdx.x;
+  double part = 0.0;
+  if (ih < a.g.Vh) {
+    int c[4];
+    site_coords(a.g, a.p_out, ih, c);
+    cx<R> acc[12];
+    hop_site<S, DAG>(a.g, ih, c, a.Uout, a.Uin, a.lstride, a.in, a.sstride, acc);
+    const R ah = (R)a.ah;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = ah * acc[k];
+    if constexpr (MODE & HOP_CENTER) {
+      cx<R> v[12];
+      load_spinor<S>(a.center, a.sstride, ih, v);
+      apply_twist(a.tc, v);
+      const R ac = (R)a.ac;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[k] = acc[k] + ac * v[k];
+    }
+    apply_twist(a.to, acc);
+    if constexpr (MODE & HOP_BASE) {
+      cx<R> v[12];
+      load_spinor<S>(a.base, a.sstride, ih, v);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[k] = acc[k] + v[k];
+    }
+    if constexpr (MODE & HOP_NORM) {
+      R s = 0;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) s += norm2(acc[k]);
+      part = (double)s;
+    }
+    apply_twist(a.ts, acc);
+    store_spinor<S>(a.out, a.sstride, ih, acc);
+  }
+  if constexpr (MODE & HOP_NORM) {
+    double total;
+    if (grid_sum<HOP_NT>(part, a.red, &total) && threadIdx.x == 0) post_action(a.st, a.post, total);
+  }
+}
+
+// ------------------------------------------------------------- fused CG update
+// For even output sites:  v = A(-mu) w - kappa^2 (H^dag)_eo t  (= Dhat^dag Dhat p),
+// r -= alpha v,  x += alpha p,  <r, r> -> post POST_RR (beta, iteration, stop).
+// Sloppy storage S for w, t, p and links; SA for r and x.
+template <class S, class SA>
+struct CGUpdArgs {
+  Geom g;
+  const typename S::lchunk* Ue;
+  const typename S::lchunk* Uo;
+  int lstride;
+  const typename S::schunk* t;     // odd
+  const typename S::schunk* w;     // even
+  const typename S::schunk* p;     // even
+  typename SA::schunk* r;          // even
+  typename SA::schunk* x;          // even
+  int sstride;
+  double kappa2;
+  Twist tw;                         // A(-mu)
+  CGState* st;
+  RedSlot red;
+};
+
+template <class S, class SA>
+__global__ void __launch_bounds__(HOP_NT) cg_update_kernel(const CGUpdArgs<S, SA> a) {
+  using R = typename S::real;
+  using RA = typename SA::real;
+  if (a.st->done) return;
+  const int ih = blockIdx.x * HOP_NT + threadIdx.x;
+  double part = 0.0;
+  if (ih < a.g.Vh) {
+    int c[4];
+    site_coords(a.g, 0, ih, c);
+    cx<R> acc[12], v[12];
+    hop_site<S, 1>(a.g, ih, c, a.Ue, a.Uo, a.lstride, a.t, a.sstride, acc);
+    load_spinor<S>(a.w, a.sstride, ih, v);
+    apply_twist(a.tw, v);
+    const R k2 = (R)a.kappa2;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = v[k] - k2 * acc[k];
+    const RA alpha = (RA)a.st->alpha;
+    cx<RA> rv[12], xv[12];
+    load_spinor<SA>(a.r, a.sstride, ih, rv);
+    load_spinor<SA>(a.x, a.sstride, ih, xv);
+    load_spinor<S>(a.p, a.sstride, ih, v);
+    RA s = 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      rv[k] = rv[k] - alpha * cx<RA>{(RA)acc[k].re, (RA)acc[k].im};
+      xv[k] = xv[k] + alpha * cx<RA>{(RA)v[k].re, (RA)v[k].im};
+      s += norm2(rv[k]);
+    }
+    part = (double)s;
+    store_spinor<SA>(a.r, a.sstride, ih, rv);
+    store_spinor<SA>(a.x, a.sstride, ih, xv);
+  }
+  double total;
+  if (grid_sum<HOP_NT>(part, a.red, &total) && threadIdx.x == 0) post_action(a.st, POST_RR, total);
+}
+
+// p = r + beta p
+template <class S, class SA>
+__global__ void __launch_bounds__(256) cg_p_kernel(const typename SA::schunk* __restrict__ r,
+                                                   typename S::schunk* __restrict__ p, int sstride, int Vh,
+                                                   const CGState* st) {
+  if (st->done) return;
+  const int ih = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ih >= Vh) return;
+  using R = typename S::real;
+  using RA = typename SA::real;
+  const RA beta = (RA)st->beta;
+  cx<RA> rv[12];
+  cx<R> pv[12];
+  load_spinor<SA>(r, sstride, ih, rv);
+  load_spinor<S>(p, sstride, ih, pv);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    cx<RA> q = rv[k] + beta * cx<RA>{(RA)pv[k].re, (RA)pv[k].im};
+    pv[k] = {(R)q.re, (R)q.im};
+  }
+  store_spinor<S>(p, sstride, ih, pv);
+}
+
+}  // namespace tsm

@@ -1,0 +1,209 @@
+// fields.cuh -- site-local kernels: layout conversion between the canonical
+// FP64 host format and the even/odd chunked formats, link packing with the
+// SU(3) check, noise generation, twist, precision casts and the BLAS-1 pieces
+// of the reliable-update step.
+#pragma once
+
+#include "common.cuh"
+
+namespace tsm {
+
+constexpr int SITE_NT = 256;
+
+// canonical spinor (24 doubles per lexicographic site) -> parity field in S
+template <class S>
+__global__ void __launch_bounds__(SITE_NT) pack_spinor_kernel(Geom g, int parity, const double2* __restrict__ canon,
+                                                              typename S::schunk* __restrict__ out, int sstride) {
+  using R = typename S::real;
+  const int ih = blockIdx.x * SITE_NT + threadIdx.x;
+  if (ih >= g.Vh) return;
+  int c[4];
+  site_coords(g, parity, ih, c);
+  const int lex = ((c[3] * g.L[2] + c[2]) * g.L[1] + c[1]) * g.L[0] + c[0];
+  cx<R> v[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    double2 d = canon[(size_t)lex * 12 + k];
+    v[k] = {(R)d.x, (R)d.y};
+  }
+  store_spinor<S>(out, sstride, ih, v);
+}
+
+template <class S>
+__global__ void __launch_bounds__(SITE_NT) unpack_spinor_kernel(Geom g, int parity, const typename S::schunk* __restrict__ in,
+                                                                int sstride, double2* __restrict__ canon) {
+  using R = typename S::real;
+  const int ih = blockIdx.x * SITE_NT + threadIdx.x;
+  if (ih >= g.Vh) return;
+  int c[4];
+  site_coords(g, parity, ih, c);
+  const int lex = ((c[3] * g.L[2] + c[2]) * g.L[1] + c[1]) * g.L[0] + c[0];
+  cx<R> v[12];
+  if (in != nullptr) {
+    load_spinor<S>(in, sstride, ih, v);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = {0, 0};
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) canon[(size_t)lex * 12 + k] = make_double2((double)v[k].re, (double)v[k].im);
+}
+
+// canonical links [lex][mu][3][3] complex -> two-row parity fields in every
+// precision; records max deviation from SU(3) (as float bits, atomicMax).
+static __global__ void __launch_bounds__(SITE_NT) pack_links_kernel(Geom g, const double2* __restrict__ U,
+                                                             double2* __restrict__ l64, float4* __restrict__ l32,
+                                                             uint2* __restrict__ l16, uint2* __restrict__ lbf,
+                                                             int lstride, unsigned int* __restrict__ maxdev) {
+  const int tid = blockIdx.x * SITE_NT + threadIdx.x;
+  if (tid >= g.V * 4) return;
+  const int lex = tid >> 2, mu = tid & 3;
+  int rem = lex;
+  const int x = rem % g.L[0];
+  rem /= g.L[0];
+  const int y = rem % g.L[1];
+  rem /= g.L[1];
+  const int z = rem % g.L[2];
+  const int t = rem / g.L[2];
+  const int parity = (x + y + z + t) & 1;
+  const int ih = lex >> 1;
+  const double2* m = U + ((size_t)lex * 4 + mu) * 9;
+  cx<double> r[6], w[3];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r[k] = {m[k].x, m[k].y};
+  third_row(r, w);
+  // SU(3) check: unit rows, orthogonal rows, stored row 2 equals the reconstruction
+  double dev = fabs(norm2(r[0]) + norm2(r[1]) + norm2(r[2]) - 1.0);
+  dev = fmax(dev, fabs(norm2(r[3]) + norm2(r[4]) + norm2(r[5]) - 1.0));
+  const cx<double> o = cjmul(r[0], r[3]) + cjmul(r[1], r[4]) + cjmul(r[2], r[5]);
+  dev = fmax(dev, sqrt(norm2(o)));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const cx<double> d = cx<double>{m[6 + k].x, m[6 + k].y} - w[k];
+    dev = fmax(dev, sqrt(norm2(d)));
+  }
+  if (!(dev <= 1e30)) dev = 1e30;  // NaN -> huge
+  atomicMax(maxdev, __float_as_uint((float)dev));
+  const size_t off64 = (size_t)parity * 4 * F64::LN * lstride;
+  const size_t off32 = (size_t)parity * 4 * F32::LN * lstride;
+  store_link<F64>(l64 + off64, lstride, mu, ih, r);
+  cx<float> rf[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) rf[k] = {(float)r[k].re, (float)r[k].im};
+  store_link<F32>(l32 + off32, lstride, mu, ih, rf);
+  store_link<F16>(l16 + off32, lstride, mu, ih, rf);
+  store_link<BF16>(lbf + off32, lstride, mu, ih, rf);
+}
+
+// noise source -> parity field in S (eta is exactly representable in every tier
+// except the 1/sqrt 2 amplitude, which is rounded once)
+template <class S>
+__global__ void __launch_bounds__(SITE_NT) noise_kernel(Geom g, int parity, NoiseSpec n, uint32_t source,
+                                                        typename S::schunk* __restrict__ out, int sstride) {
+  using R = typename S::real;
+  const int ih = blockIdx.x * SITE_NT + threadIdx.x;
+  if (ih >= g.Vh) return;
+  int c[4];
+  site_coords(g, parity, ih, c);
+  const uint32_t lex = (uint32_t)(((c[3] * g.L[2] + c[2]) * g.L[1] + c[1]) * g.L[0] + c[0]);
+  cx<R> v[12];
+  noise_site<R>(n, lex, source, v);
+  store_spinor<S>(out, sstride, ih, v);
+}
+
+// noise source in the canonical layout (for exact comparisons)
+static __global__ void __launch_bounds__(SITE_NT) noise_canon_kernel(int V, NoiseSpec n, uint32_t source,
+                                                              double2* __restrict__ out) {
+  const int lex = blockIdx.x * SITE_NT + threadIdx.x;
+  if (lex >= V) return;
+  cx<double> v[12];
+  noise_site<double>(n, (uint32_t)lex, source, v);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) out[(size_t)lex * 12 + k] = make_double2(v[k].re, v[k].im);
+}
+
+// out = f * in (site-local chiral twist), optional skip on st->done
+template <class S>
+__global__ void __launch_bounds__(SITE_NT) twist_kernel(int Vh, Twist f, const typename S::schunk* __restrict__ in,
+                                                        typename S::schunk* __restrict__ out, int sstride,
+                                                        const CGState* st) {
+  if (st != nullptr && st->done) return;
+  const int ih = blockIdx.x * SITE_NT + threadIdx.x;
+  if (ih >= Vh) return;
+  cx<typename S::real> v[12];
+  load_spinor<S>(in, sstride, ih, v);
+  apply_twist(f, v);
+  store_spinor<S>(out, sstride, ih, v);
+}
+
+// out (So) = in (Si), precision cast; in == nullptr writes zero
+template <class Si, class So>
+__global__ void __launch_bounds__(SITE_NT) convert_kernel(int Vh, const typename Si::schunk* __restrict__ in,
+                                                          typename So::schunk* __restrict__ out, int sstride) {
+  const int ih = blockIdx.x * SITE_NT + threadIdx.x;
+  if (ih >= Vh) return;
+  cx<typename Si::real> v[12];
+  cx<typename So::real> w[12];
+  if (in != nullptr) {
+    load_spinor<Si>(in, sstride, ih, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) w[k] = {(typename So::real)v[k].re, (typename So::real)v[k].im};
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) w[k] = {0, 0};
+  }
+  store_spinor<So>(out, sstride, ih, w);
+}
+
+// reliable update, step 1: x64 += y (y in F32), y = 0
+static __global__ void __launch_bounds__(SITE_NT) accumulate_solution_kernel(int Vh, float4* __restrict__ y,
+                                                                      double2* __restrict__ x, int sstride) {
+  const int ih = blockIdx.x * SITE_NT + threadIdx.x;
+  if (ih >= Vh) return;
+  cx<float> yv[12];
+  cx<double> xv[12];
+  load_spinor<F32>(y, sstride, ih, yv);
+  load_spinor<F64>(x, sstride, ih, xv);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    xv[k] = xv[k] + cx<double>{(double)yv[k].re, (double)yv[k].im};
+    yv[k] = {0.f, 0.f};
+  }
+  store_spinor<F64>(x, sstride, ih, xv);
+  store_spinor<F32>(y, sstride, ih, yv);
+}
+
+// <v, v> over one parity field with post action (deterministic two-stage sum)
+template <class S>
+__global__ void __launch_bounds__(SITE_NT) norm_kernel(int Vh, const typename S::schunk* __restrict__ v, int sstride,
+                                                       RedSlot red, CGState* st, int post) {
+  const int ih = blockIdx.x * SITE_NT + threadIdx.x;
+  double part = 0.0;
+  if (ih < Vh) {
+    cx<typename S::real> w[12];
+    load_spinor<S>(v, sstride, ih, w);
+    typename S::real s = 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s += norm2(w[k]);
+    part = (double)s;
+  }
+  double total;
+  if (grid_sum<SITE_NT>(part, red, &total) && threadIdx.x == 0) post_action(st, post, total);
+}
+
+static __global__ void state_init_kernel(CGState* st, double tol, int max_iter) {
+  st->tol = tol;
+  st->max_iter = max_iter;
+  st->iter = 0;
+  st->done = 0;
+  st->status = 0;
+  st->rr = st->rr0 = st->pAp = st->alpha = st->beta = st->aux = 0.0;
+}
+
+// clear `done` so that iterations resume (after a reliable update that found
+// the true residual still above tolerance)
+static __global__ void state_resume_kernel(CGState* st) {
+  if (st->status == 0 && st->iter < st->max_iter) st->done = 0;
+}
+
+}  // namespace tsm

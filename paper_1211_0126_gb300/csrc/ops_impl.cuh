@@ -1,0 +1,160 @@
+// ops_impl.cuh -- definitions of the launch helpers declared in context.h.
+// Included by ops_f64.cu / ops_f32.cu / ops_f16.cu, each of which
+// instantiates them for its storage types (parallel compilation).
+#pragma once
+
+#include "context.h"
+#include "fields.cuh"
+
+namespace tsm {
+
+inline int blocks_for(int n, int nt) { return (n + nt - 1) / nt; }
+
+template <class S>
+static int hop_kind_of(int dag, int mode) {
+  if (dag) return PK_HOP_DAG;
+  return (mode & HOP_CENTER) ? PK_HOP_XPAY : PK_HOP;
+}
+
+// record a timed launch when instrumentation is on for this launch
+struct TimedLaunch {
+  Ctx& c;
+  Ctx::EvRec rec{};
+  bool on = false;
+  TimedLaunch(Ctx& cc, int kind, double bytes) : c(cc) {
+    if (!c.profile || !c.prof_this_launch) return;
+    if (c.ev_free.empty()) {
+      Ctx::EvRec r{};
+      if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
+      c.ev_free.push_back(r);
+    }
+    rec = c.ev_free.back();
+    c.ev_free.pop_back();
+    rec.kind = kind;
+    rec.bytes = bytes;
+    on = (cudaEventRecord(rec.a, c.stream) == cudaSuccess);
+    if (!on) c.ev_free.push_back(rec);
+  }
+  void done() {
+    if (!on) return;
+    if (cudaEventRecord(rec.b, c.stream) == cudaSuccess) c.ev_pending.push_back(rec);
+    else c.ev_free.push_back(rec);
+    on = false;
+  }
+};
+
+template <class S>
+int launch_hop(Ctx& c, const HopArgs<S>& a, int dag, int mode, int prof_kind) {
+  const int nb = blocks_for(a.g.Vh, HOP_NT);
+  if (nb == 0) return TSM_OK;
+  const int kind = prof_kind >= 0 ? prof_kind : hop_kind_of<S>(dag, mode);
+  const double sb = spinor_site_bytes(S::id), lb = link_site_bytes(S::id);
+  const double bytes = (double)a.g.Vh * (lb + sb * (2 + ((mode & HOP_CENTER) ? 1 : 0) + ((mode & HOP_BASE) ? 1 : 0)));
+  TimedLaunch tl(c, kind, bytes);
+#define TSM_HOP_CASE(D, M) \
+  if (dag == D && mode == M) hop_kernel<S, D, M><<<nb, HOP_NT, 0, c.stream>>>(a);
+  TSM_HOP_CASE(0, 0)
+  else TSM_HOP_CASE(0, HOP_CENTER)
+  else TSM_HOP_CASE(0, HOP_CENTER | HOP_NORM)
+  else TSM_HOP_CASE(0, HOP_CENTER | HOP_NORM | HOP_BASE)
+  else TSM_HOP_CASE(1, 0)
+  else TSM_HOP_CASE(1, HOP_CENTER)
+  else TSM_HOP_CASE(1, HOP_CENTER | HOP_NORM)
+  else TSM_HOP_CASE(1, HOP_CENTER | HOP_NORM | HOP_BASE)
+  else {
+    set_error("hop kernel variant dag=%d mode=%d not built", dag, mode);
+    return TSM_ERR_ARG;
+  }
+#undef TSM_HOP_CASE
+  tl.done();
+  c.launches++;
+  return check_launch(c, "hop_kernel");
+}
+
+template <class S, class SA>
+int launch_cg_update(Ctx& c, const CGUpdArgs<S, SA>& a) {
+  const int nb = blocks_for(a.g.Vh, HOP_NT);
+  if (nb == 0) return TSM_OK;
+  const double sb = spinor_site_bytes(S::id), lb = link_site_bytes(S::id), sa = spinor_site_bytes(SA::id);
+  TimedLaunch tl(c, PK_HOP_UPDATE, (double)a.g.Vh * (lb + 3 * sb + 4 * sa));
+  cg_update_kernel<S, SA><<<nb, HOP_NT, 0, c.stream>>>(a);
+  tl.done();
+  c.launches++;
+  return check_launch(c, "cg_update_kernel");
+}
+
+template <class S, class SA>
+int launch_cg_p(Ctx& c, const PField& r, const PField& p, CGState* st) {
+  const int nb = blocks_for(c.g.Vh, SITE_NT);
+  if (nb == 0) return TSM_OK;
+  cg_p_kernel<S, SA><<<nb, SITE_NT, 0, c.stream>>>(r.as<SA>(), p.as<S>(), c.sstride, c.g.Vh, st);
+  c.launches++;
+  return check_launch(c, "cg_p_kernel");
+}
+
+template <class S>
+int launch_pack(Ctx& c, int parity, const double* canon, const PField& out) {
+  const int nb = blocks_for(c.g.Vh, SITE_NT);
+  pack_spinor_kernel<S><<<nb, SITE_NT, 0, c.stream>>>(c.g, parity, reinterpret_cast<const double2*>(canon),
+                                                      out.as<S>(), c.sstride);
+  c.launches++;
+  return check_launch(c, "pack_spinor_kernel");
+}
+
+template <class S>
+int launch_unpack(Ctx& c, int parity, const PField& in, double* canon) {
+  const int nb = blocks_for(c.g.Vh, SITE_NT);
+  unpack_spinor_kernel<S><<<nb, SITE_NT, 0, c.stream>>>(c.g, parity, in.as<S>(), c.sstride,
+                                                        reinterpret_cast<double2*>(canon));
+  c.launches++;
+  return check_launch(c, "unpack_spinor_kernel");
+}
+
+template <class S>
+int launch_noise(Ctx& c, int parity, const NoiseSpec& n, uint32_t source, const PField& out) {
+  const int nb = blocks_for(c.g.Vh, SITE_NT);
+  noise_kernel<S><<<nb, SITE_NT, 0, c.stream>>>(c.g, parity, n, source, out.as<S>(), c.sstride);
+  c.launches++;
+  return check_launch(c, "noise_kernel");
+}
+
+template <class S>
+int launch_twist(Ctx& c, const Twist& f, const PField& in, const PField& out, const CGState* st) {
+  const int nb = blocks_for(c.g.Vh, SITE_NT);
+  twist_kernel<S><<<nb, SITE_NT, 0, c.stream>>>(c.g.Vh, f, in.as<S>(), out.as<S>(), c.sstride, st);
+  c.launches++;
+  return check_launch(c, "twist_kernel");
+}
+
+template <class S>
+int launch_norm(Ctx& c, const PField& v, CGState* st, int post) {
+  const int nb = blocks_for(c.g.Vh, SITE_NT);
+  norm_kernel<S><<<nb, SITE_NT, 0, c.stream>>>(c.g.Vh, v.as<S>(), c.sstride, c.red, st, post);
+  c.launches++;
+  return check_launch(c, "norm_kernel");
+}
+
+template <class Si, class So>
+int launch_convert(Ctx& c, const PField& in, const PField& out) {
+  const int nb = blocks_for(c.g.Vh, SITE_NT);
+  convert_kernel<Si, So><<<nb, SITE_NT, 0, c.stream>>>(c.g.Vh, in.as<Si>(), out.as<So>(), c.sstride);
+  c.launches++;
+  return check_launch(c, "convert_kernel");
+}
+
+}  // namespace tsm
+
+#define TSM_INSTANTIATE_STORAGE(S)                                                                  \
+  template int tsm::launch_hop<S>(Ctx&, const HopArgs<S>&, int, int, int);                         \
+  template int tsm::launch_pack<S>(Ctx&, int, const double*, const PField&);                       \
+  template int tsm::launch_unpack<S>(Ctx&, int, const PField&, double*);                           \
+  template int tsm::launch_noise<S>(Ctx&, int, const NoiseSpec&, uint32_t, const PField&);         \
+  template int tsm::launch_twist<S>(Ctx&, const Twist&, const PField&, const PField&, const CGState*); \
+  template int tsm::launch_norm<S>(Ctx&, const PField&, CGState*, int);
+
+#define TSM_INSTANTIATE_PAIR(S, SA)                                               \
+  template int tsm::launch_cg_update<S, SA>(Ctx&, const CGUpdArgs<S, SA>&);      \
+  template int tsm::launch_cg_p<S, SA>(Ctx&, const PField&, const PField&, CGState*);
+
+#define TSM_INSTANTIATE_CONVERT(Si, So) \
+  template int tsm::launch_convert<Si, So>(Ctx&, const PField&, const PField&);

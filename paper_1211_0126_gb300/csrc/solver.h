@@ -1,0 +1,46 @@
+// solver.h -- CG on the normal equations of the even/odd Schur complement.
+#pragma once
+
+#include "context.h"
+
+namespace tsm {
+
+struct SolveResult {
+  int iters = 0;
+  int status = TSM_OK;     // TSM_OK or TSM_ERR_NONFINITE
+  int converged = 0;       // stopping rule met (fixed-count rule: max_iter reached)
+  double rel_res = 0.0;    // final ||r|| / ||Dhat^dag bhat|| as tracked by the solver
+};
+
+// Storage tier of a solve's source and solution fields: FP64 for the FP64
+// tier and for FP32 with FP64 reliable updates, FP32 otherwise.
+int solution_prec(const tm_stop& stop);
+
+// Solve D_tm s = b for one source.  b and s are even/odd fields of tier
+// solution_prec(stop); `slot` selects the device solver state.
+int solve_source(Ctx& c, const tm_stop& stop, int slot, EOField b, EOField s, SolveResult* res);
+
+// ||b - D_tm s|| / ||b|| in FP64 (fields of tier prec).
+int true_residual(Ctx& c, int prec, EOField b, EOField s, double* out);
+
+// hop arguments pre-filled for this context (links of storage S, unit twists)
+template <class S>
+HopArgs<S> hop_args(const Ctx& c, int p_out) {
+  HopArgs<S> a{};
+  a.g = c.g;
+  a.p_out = p_out;
+  a.Uout = c.links_of<S>(p_out);
+  a.Uin = c.links_of<S>(1 - p_out);
+  a.lstride = c.lstride;
+  a.sstride = c.sstride;
+  a.ac = 0.0;
+  a.ah = 1.0;
+  a.tc = twist_one();
+  a.to = twist_one();
+  a.ts = twist_one();
+  a.red = c.red;
+  a.post = POST_NONE;
+  return a;
+}
+
+}  // namespace tsm

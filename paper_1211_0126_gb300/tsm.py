@@ -1,0 +1,385 @@
+"""Python binding of libtsm (include/tsm.h): argument marshalling only.
+
+Every entry point of the C ABI has a function of the same name here
+(``tsm_create``, ``tsm_load_gauge``, ``tm_dslash``, ``tm_solve_batch``,
+``tsm_noise``, ``tsm_contract``, ``tsm_loops``, ``tsm_combine``, ...).  Arrays
+are either numpy arrays in host memory (copied in/out by the library) or torch
+CUDA tensors (passed as device pointers).  All arithmetic runs in the CUDA
+library; if the library has not been built this module raises at import of
+the library, it never falls back to another implementation.
+
+Array layouts (complex128 numpy arrays, or torch complex128 / float64 tensors):
+    gauge  [T, Z, Y, X, 4, 3, 3]
+    spinor [T, Z, Y, X, 4, 3]        (batches: leading axis)
+    loops  [n_gamma, n_q, T]
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libtsm.so")
+
+TSM_F64, TSM_F32, TSM_BF16, TSM_F16 = 0, 1, 2, 3
+TM_OP_FULL, TM_OP_HOP_EO, TM_OP_HOP_OE, TM_OP_SCHUR, TM_OP_NORMAL = 0, 1, 2, 3, 4
+STATUS = {0: "TSM_OK", -1: "TSM_ERR_ARG", -2: "TSM_ERR_DIMS", -3: "TSM_ERR_CUDA",
+          -4: "TSM_ERR_NOT_CONVERGED", -5: "TSM_ERR_NONFINITE", -6: "TSM_ERR_TIMEOUT",
+          -7: "TSM_ERR_NOT_UNITARY", -8: "TSM_ERR_NO_GAUGE", -9: "TSM_ERR_TOO_LARGE"}
+TSM_ERR_NOT_CONVERGED = -4
+
+
+class TmLattice(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int * 4), ("kappa", ctypes.c_double), ("mu", ctypes.c_double),
+                ("t_antiperiodic", ctypes.c_int)]
+
+
+class TmStop(ctypes.Structure):
+    _fields_ = [("rel_tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("prec", ctypes.c_int),
+                ("reliable", ctypes.c_int), ("reliable_delta", ctypes.c_double)]
+
+
+class TsmLoopStats(ctypes.Structure):
+    _fields_ = [("n_sources", ctypes.c_int), ("lp_iters", ctypes.c_longlong), ("hp_iters", ctypes.c_longlong),
+                ("hp_not_converged", ctypes.c_int), ("hp_max_true_res", ctypes.c_double),
+                ("lp_max_true_res", ctypes.c_double)]
+
+
+class TsmParams(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("noise", ctypes.c_int),
+                ("hp_begin", ctypes.c_uint32), ("hp_end", ctypes.c_uint32),
+                ("lp_begin", ctypes.c_uint32), ("lp_end", ctypes.c_uint32),
+                ("hp", TmStop), ("lp", TmStop), ("batch", ctypes.c_int),
+                ("gammas", ctypes.POINTER(ctypes.c_int)), ("n_gamma", ctypes.c_int),
+                ("moms", ctypes.POINTER(ctypes.c_int)), ("n_q", ctypes.c_int)]
+
+
+# exported symbol -> (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "tsm_create": (ctypes.c_int, [ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "tsm_destroy": (ctypes.c_int, [_P]),
+    "tsm_load_gauge": (ctypes.c_int, [_P, ctypes.POINTER(TmLattice), _P, ctypes.c_int]),
+    "tm_dslash": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int]),
+    "tm_solve_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.POINTER(TmStop), ctypes.c_int,
+                                      _P, _P]),
+    "tsm_noise": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, _P, ctypes.c_int]),
+    "tsm_contract": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, _P, _P,
+                                    _P, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int]),
+    "tsm_loops": (ctypes.c_int, [_P, ctypes.POINTER(TsmParams), _P, _P, _P, _P, _P, _P, ctypes.c_int,
+                                 ctypes.POINTER(TsmLoopStats)]),
+    "tsm_combine": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
+                                   ctypes.c_int]),
+    "tsm_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tsm_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
+    "tsm_launch_count": (ctypes.c_longlong, [_P]),
+    "tsm_last_error": (ctypes.c_char_p, []),
+    "tsm_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lib = None
+
+
+def _preload_cudart():
+    for d in ("/usr/local/cuda/lib64", "/usr/local/cuda/targets/sbsa-linux/lib",
+              "/usr/local/cuda/targets/x86_64-linux/lib"):
+        for name in ("libcudart.so.13", "libcudart.so"):
+            p = os.path.join(d, name)
+            if os.path.exists(p):
+                try:
+                    ctypes.CDLL(p, mode=ctypes.RTLD_GLOBAL)
+                    return
+                except OSError:
+                    pass
+
+
+def library():
+    """Load libtsm.so (built in-tree by build.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libtsm.so is not built (%s); run `python -c \"import __graft_entry__ as g; "
+                           "g.build()\"` first" % LIB_PATH)
+    try:
+        lib = ctypes.CDLL(LIB_PATH)
+    except OSError:
+        _preload_cudart()
+        lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class TsmError(RuntimeError):
+    def __init__(self, status, where):
+        msg = library().tsm_last_error().decode(errors="replace")
+        super().__init__("%s: %s (%s)" % (where, STATUS.get(status, status), msg))
+        self.status = status
+
+
+def _check(status, where, allow=()):
+    if status != 0 and status not in allow:
+        raise TsmError(status, where)
+    return status
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, writable=False):
+    """(pointer, on_device) of a numpy array or torch tensor, checked for layout."""
+    if a is None:
+        return None, None
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("torch tensor must be contiguous")
+        if a.dtype not in (__import__("torch").complex128, __import__("torch").float64):
+            raise ValueError("torch tensor must be complex128 or float64")
+        return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    if not isinstance(a, np.ndarray):
+        raise TypeError("expected a numpy array or torch tensor")
+    if a.dtype not in (np.complex128, np.float64) or not a.flags.c_contiguous:
+        raise ValueError("numpy array must be C-contiguous complex128/float64")
+    if writable and not a.flags.writeable:
+        raise ValueError("output array is read-only")
+    return ctypes.c_void_p(a.ctypes.data), 0
+
+
+def _same_side(*flags):
+    fl = [f for f in flags if f is not None]
+    if fl and any(f != fl[0] for f in fl):
+        raise ValueError("mix of host and device arrays in one call")
+    return fl[0] if fl else 0
+
+
+# ------------------------------------------------------------ C-ABI names
+def tsm_create(device=0, stream=None):
+    """Create a context; `stream` is a cudaStream_t as int (e.g. torch's cuda_stream) or None."""
+    h = ctypes.c_void_p()
+    _check(library().tsm_create(int(device), ctypes.c_void_p(stream or 0), ctypes.byref(h)), "tsm_create")
+    return h
+
+
+def tsm_destroy(h):
+    _check(library().tsm_destroy(h), "tsm_destroy")
+
+
+def lattice(dims, kappa, mu, antiperiodic_t=True):
+    lat = TmLattice()
+    for k in range(4):
+        lat.L[k] = int(dims[k])
+    lat.kappa = float(kappa)
+    lat.mu = float(mu)
+    lat.t_antiperiodic = 1 if antiperiodic_t else 0
+    return lat
+
+
+def stop(rel_tol, max_iter, prec=TSM_F64, reliable=False, reliable_delta=0.0):
+    return TmStop(float(rel_tol), int(max_iter), int(prec), 1 if reliable else 0, float(reliable_delta))
+
+
+def tsm_load_gauge(h, lat, U):
+    p, dev = _ptr(U)
+    return _check(library().tsm_load_gauge(h, ctypes.byref(lat), p, dev), "tsm_load_gauge")
+
+
+def tm_dslash(h, prec, op, dagger, psi, out):
+    pi, di = _ptr(psi)
+    po, do = _ptr(out, True)
+    return _check(library().tm_dslash(h, int(prec), int(op), int(dagger), pi, po, _same_side(di, do)),
+                  "tm_dslash")
+
+
+def tm_solve_batch(h, b, s, stp, nrhs=1, allow_not_converged=True):
+    """Solve D_tm s = b for nrhs stacked sources; returns (status, iters, true_res)."""
+    pb, db = _ptr(b)
+    ps, ds = _ptr(s, True)
+    iters = np.zeros(nrhs, dtype=np.int32)
+    tres = np.zeros(nrhs, dtype=np.float64)
+    st = library().tm_solve_batch(h, int(nrhs), pb, ps, ctypes.byref(stp), _same_side(db, ds),
+                                  ctypes.c_void_p(iters.ctypes.data), ctypes.c_void_p(tres.ctypes.data))
+    _check(st, "tm_solve_batch", allow=(TSM_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return st, iters, tres
+
+
+def tsm_noise(h, seed, kind, source, out):
+    po, do = _ptr(out, True)
+    return _check(library().tsm_noise(h, ctypes.c_uint64(seed), int(kind), ctypes.c_uint32(source), po, do),
+                  "tsm_noise")
+
+
+def _int_array(vals, name):
+    arr = np.ascontiguousarray(np.asarray(vals, dtype=np.int32).reshape(-1))
+    return arr, ctypes.c_void_p(arr.ctypes.data)
+
+
+def tsm_contract(h, prec, seed, kind, source, s_a, s_b, gammas, moms, out):
+    g, gp = _int_array(gammas, "gammas")
+    m, mp = _int_array(moms, "moms")
+    pa, da = _ptr(s_a)
+    pb, db = _ptr(s_b)
+    po, do = _ptr(out, True)
+    return _check(library().tsm_contract(h, int(prec), ctypes.c_uint64(seed), int(kind), ctypes.c_uint32(source),
+                                         pa, pb, gp, len(g), mp, len(m) // 3, po, _same_side(da, db, do)),
+                  "tsm_contract")
+
+
+def params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batch=1):
+    """TsmParams; keeps the integer arrays alive on the returned object."""
+    p = TsmParams()
+    p.seed = int(seed)
+    p.noise = int(noise)
+    p.hp_begin, p.hp_end = int(hp_range[0]), int(hp_range[1])
+    p.lp_begin, p.lp_end = int(lp_range[0]), int(lp_range[1])
+    p.hp = hp_stop
+    p.lp = lp_stop
+    p.batch = int(batch)
+    g = np.ascontiguousarray(np.asarray(gammas, dtype=np.int32).reshape(-1))
+    m = np.ascontiguousarray(np.asarray(moms, dtype=np.int32).reshape(-1))
+    p._keep = (g, m)
+    p.gammas = g.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    p.n_gamma = len(g)
+    p.moms = m.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    p.n_q = len(m) // 3
+    return p
+
+
+def tsm_loops(h, p, loops=None, err=None, lp_mean=None, corr_mean=None, per_corr=None, per_lp=None):
+    ptrs = [_ptr(a, True) for a in (loops, err, lp_mean, corr_mean, per_corr, per_lp)]
+    dev = _same_side(*[d for _, d in ptrs])
+    stats = TsmLoopStats()
+    _check(library().tsm_loops(h, ctypes.byref(p), *[q for q, _ in ptrs], dev, ctypes.byref(stats)), "tsm_loops")
+    return stats
+
+
+def tsm_combine(h, per_corr, per_lp, n_entries, loops=None, err=None, lp_mean=None, corr_mean=None):
+    n_hp = 0 if per_corr is None else per_corr.shape[0]
+    n_lp = 0 if per_lp is None else per_lp.shape[0]
+    ins = [_ptr(per_corr), _ptr(per_lp)]
+    outs = [_ptr(a, True) for a in (loops, err, lp_mean, corr_mean)]
+    dev = _same_side(*[d for _, d in ins + outs])
+    return _check(library().tsm_combine(h, ins[0][0], n_hp, ins[1][0], n_lp, int(n_entries),
+                                        *[q for q, _ in outs], dev), "tsm_combine")
+
+
+def tsm_profile(h, enable):
+    return _check(library().tsm_profile(h, 1 if enable else 0), "tsm_profile")
+
+
+def tsm_profile_read(h):
+    ms = np.zeros(4)
+    cnt = np.zeros(4, dtype=np.int64)
+    by = np.zeros(4)
+    _check(library().tsm_profile_read(h, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(cnt.ctypes.data),
+                                      ctypes.c_void_p(by.ctypes.data)), "tsm_profile_read")
+    return ms, cnt, by
+
+
+def tsm_launch_count(h):
+    return int(library().tsm_launch_count(h))
+
+
+# ------------------------------------------------------------ convenience
+class Context:
+    """Owning wrapper around a tsm_ctx handle with numpy-returning helpers."""
+
+    def __init__(self, device=0, stream=None):
+        self.h = tsm_create(device, stream)
+        self.dims = None
+
+    def close(self):
+        if self.h is not None:
+            tsm_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_gauge(self, U, dims, kappa, mu, antiperiodic_t=True):
+        self.dims = tuple(int(d) for d in dims)
+        self.lat = lattice(dims, kappa, mu, antiperiodic_t)
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.complex128)
+        tsm_load_gauge(self.h, self.lat, U)
+
+    def _spinor_shape(self):
+        lx, ly, lz, lt = self.dims
+        return (lt, lz, ly, lx, 4, 3)
+
+    def dslash(self, psi, op=TM_OP_FULL, dagger=False, prec=TSM_F64):
+        psi = np.ascontiguousarray(psi, dtype=np.complex128)
+        out = np.zeros(self._spinor_shape(), dtype=np.complex128)
+        tm_dslash(self.h, prec, op, dagger, psi, out)
+        return out
+
+    def solve(self, b, stp):
+        b = np.ascontiguousarray(b, dtype=np.complex128)
+        nrhs = 1 if b.ndim == 6 else b.shape[0]
+        s = np.zeros_like(b)
+        st, iters, tres = tm_solve_batch(self.h, b, s, stp, nrhs)
+        return s, iters, tres, st
+
+    def noise(self, seed, source, kind=4):
+        out = np.zeros(self._spinor_shape(), dtype=np.complex128)
+        tsm_noise(self.h, seed, kind, source, out)
+        return out
+
+    def contract(self, seed, source, s_a, gammas, moms, s_b=None, kind=4, prec=TSM_F64):
+        s_a = np.ascontiguousarray(s_a, dtype=np.complex128)
+        if s_b is not None:
+            s_b = np.ascontiguousarray(s_b, dtype=np.complex128)
+        out = np.zeros((len(gammas), len(moms), self.dims[3]), dtype=np.complex128)
+        tsm_contract(self.h, prec, seed, kind, source, s_a, s_b, gammas, moms, out)
+        return out
+
+    def loops(self, seed, noise, n_hp, n_lp, hp_stop, lp_stop, gammas, moms, hp_range=None, lp_range=None,
+              per_source=False, batch=1):
+        hp_range = hp_range or (0, n_hp)
+        lp_range = lp_range or (n_hp, n_hp + n_lp)
+        p = params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batch)
+        shape = (len(gammas), len(moms), self.dims[3])
+        out = {k: np.zeros(shape, dtype=np.complex128) for k in ("loops", "lp_mean", "corr_mean")}
+        out["err"] = np.zeros(shape, dtype=np.float64)
+        pc = pl = None
+        if per_source:
+            pc = np.zeros((hp_range[1] - hp_range[0],) + shape, dtype=np.complex128)
+            pl = np.zeros((lp_range[1] - lp_range[0],) + shape, dtype=np.complex128)
+        stats = tsm_loops(self.h, p, out["loops"], out["err"], out["lp_mean"], out["corr_mean"], pc, pl)
+        out["stats"] = {f: getattr(stats, f) for f, _ in TsmLoopStats._fields_}
+        if per_source:
+            out["per_corr"], out["per_lp"] = pc, pl
+        return out
+
+    def combine(self, per_corr, per_lp):
+        ref = per_corr if per_corr is not None and per_corr.shape[0] else per_lp
+        shape = ref.shape[1:]
+        n = int(np.prod(shape))
+        out = {k: np.zeros(shape, dtype=np.complex128) for k in ("loops", "lp_mean", "corr_mean")}
+        out["err"] = np.zeros(shape, dtype=np.float64)
+        pc = None if per_corr is None else np.ascontiguousarray(per_corr)
+        pl = None if per_lp is None else np.ascontiguousarray(per_lp)
+        tsm_combine(self.h, pc, pl, n, out["loops"], out["err"], out["lp_mean"], out["corr_mean"])
+        return out
+
+    def profile(self, enable=True):
+        tsm_profile(self.h, enable)
+
+    def profile_read(self):
+        return tsm_profile_read(self.h)
+
+    def launch_count(self):
+        return tsm_launch_count(self.h)

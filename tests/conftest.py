@@ -27,3 +27,20 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def libtsm():
+    """The CUDA library, built in-tree if it is not there yet (nvcc cross-compiles)."""
+    from paper_1211_0126_gb300 import build, tsm
+    if not os.path.exists(tsm.LIB_PATH):
+        build.build()
+    return tsm.library()
+
+
+@pytest.fixture(scope="module")
+def ctx(libtsm):
+    from paper_1211_0126_gb300 import tsm
+    c = tsm.Context(0)
+    yield c
+    c.close()
