@@ -52,7 +52,7 @@ int launch_hop(Ctx& c, const HopArgs<S>& a, int dag, int mode, int prof_kind) {
   const double bytes = (double)a.g.Vh * (lb + sb * (2 + ((mode & HOP_CENTER) ? 1 : 0) + ((mode & HOP_BASE) ? 1 : 0)));
   TimedLaunch tl(c, kind, bytes);
 #define TSM_HOP_CASE(D, M) \
-  if (dag == D && mode == M) hop_kernel<S, D, M><<<nb, HOP_NT, 0, c.stream>>>(a);
+  if (dag == (D) && mode == (M)) hop_kernel<S, (D), (M)><<<nb, HOP_NT, 0, c.stream>>>(a);
   TSM_HOP_CASE(0, 0)
   else TSM_HOP_CASE(0, HOP_CENTER)
   else TSM_HOP_CASE(0, HOP_CENTER | HOP_NORM)
