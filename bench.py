@@ -48,7 +48,34 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / equal-error / cpu-baseline legs")
+    ap.add_argument("--dslash-only", default=None,
+                    help="comma list of tiers (f64,f32,f16,bf16): only run 3 standalone H_eo launches per tier "
+                         "at 24^3x48 (a small case for ncu captures of the hop kernel)")
     return ap.parse_args()
+
+
+def run_dslash_only(tiers):
+    import torch
+    from paper_1211_0126_gb300 import build, tsm
+    from paper_1211_0126_gb300 import synthetic as S
+    if not os.path.exists(tsm.LIB_PATH):
+        build.build()
+    stream = torch.cuda.current_stream()
+    ctx = tsm.Context(0, stream.cuda_stream)
+    ctx.load_gauge(S.gauge_field(DIMS, EPS, GAUGE_SEED), DIMS, KAPPA, MU)
+    psi = S.random_spinor(DIMS, 99)
+    out = np.zeros_like(psi)
+    names = {"f64": tsm.TSM_F64, "f32": tsm.TSM_F32, "f16": tsm.TSM_F16, "bf16": tsm.TSM_BF16}
+    res = {}
+    for name in tiers.split(","):
+        tsm.tsm_profile(ctx.h, True)
+        for _ in range(3):
+            tsm.tm_dslash(ctx.h, names[name], tsm.TM_OP_HOP_EO, 0, psi, out)
+        ms, cnt, by = ctx.profile_read()
+        tsm.tsm_profile(ctx.h, False)
+        res[name] = {"us_per_launch": 1e3 * ms.sum() / cnt.sum(), "gbs": by.sum() / (ms.sum() * 1e-3) / 1e9}
+    print(json.dumps({"dslash_only": res}), flush=True)
+    ctx.close()
 
 
 def measured_peaks():
@@ -427,7 +454,9 @@ def main():
     args = parse()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.impl == "reference":
+    if args.dslash_only:
+        run_dslash_only(args.dslash_only)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
