@@ -211,12 +211,14 @@ int tsm_combine(tsm_ctx* ctx, const double* per_corr, int n_hp, const double* pe
 
 /* Instrumentation.  tsm_profile(ctx, 1) starts recording CUDA-event times of
  * hop-kernel launches on the context's stream (in CG solves: the hop kernels
- * of the first iteration of every chunk); tsm_profile_read returns, per hop
- * kind k = 0..3 (plain hop, hop + xpay/norm, adjoint hop, adjoint hop + CG
- * update), the summed milliseconds, launch count and algorithmic bytes.
+ * of the first iteration of every chunk of 8 iterations); tsm_profile_read
+ * returns, per bucket b = 4 * tier + kind (tier: tsm_prec; kind 0 plain hop
+ * K1, 1 hop + xpay/norm K2, 2 adjoint hop K3, 3 adjoint hop + CG update K4),
+ * the summed milliseconds, launch count and algorithmic bytes (links once per
+ * launch, spinor streams once per right-hand side).  Arrays hold 16 entries.
  * tsm_launch_count returns the number of library kernels launched so far. */
 int tsm_profile(tsm_ctx* ctx, int enable);
-int tsm_profile_read(tsm_ctx* ctx, double ms[4], long long count[4], double bytes[4]);
+int tsm_profile_read(tsm_ctx* ctx, double ms[16], long long count[16], double bytes[16]);
 long long tsm_launch_count(tsm_ctx* ctx);
 
 /* One-line message for the last failed call on this thread ("" if none). */

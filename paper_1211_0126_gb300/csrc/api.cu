@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "contract.h"
 #include "fields.cuh"
@@ -74,9 +75,9 @@ int unpack_eo(Ctx& c, int prec, EOField f, double* canon) {
   });
 }
 
-int eo_fields(Ctx& c, const std::string& name, int prec, EOField* f) {
-  TSM_TRY(c.field(name + "_e", prec, &f->e));
-  return c.field(name + "_o", prec, &f->o);
+int eo_fields(Ctx& c, const std::string& name, int prec, EOField* f, int nrhs = 1) {
+  TSM_TRY(c.field(name + "_e", prec, &f->e, nrhs));
+  return c.field(name + "_o", prec, &f->o, nrhs);
 }
 
 int check_stop(const tm_stop* s) {
@@ -90,12 +91,7 @@ template <class S>
 int apply_operator(Ctx& c, int op, int dagger, EOField in, EOField out) {
   const double k = c.lat.kappa, mu = c.lat.mu, k2 = k * k;
   const double m = dagger ? -mu : mu;
-  const int zb = (c.g.Vh + SITE_NT - 1) / SITE_NT;
-  auto zero = [&](PField f) {
-    convert_kernel<S, S><<<zb, SITE_NT, 0, c.stream>>>(c.g.Vh, nullptr, f.as<S>(), c.sstride);
-    c.launches++;
-    return check_launch(c, "convert_kernel");
-  };
+  auto zero = [&](PField f) { return launch_convert<S, S>(c, PField{}, f); };
   switch (op) {
     case TM_OP_FULL:
       for (int par = 0; par < 2; ++par) {
@@ -205,8 +201,13 @@ int tsm_create(int device, void* cuda_stream, tsm_ctx** out) {
   if (rc == TSM_OK && cudaMalloc(&c.states, Ctx::kMaxStates * sizeof(CGState)) != cudaSuccess) rc = TSM_ERR_CUDA;
   if (rc == TSM_OK && cudaMallocHost(&c.h_states, Ctx::kMaxStates * sizeof(CGState)) != cudaSuccess)
     rc = TSM_ERR_CUDA;
-  if (rc == TSM_OK && cudaMalloc(&c.red.counter, sizeof(unsigned int)) != cudaSuccess) rc = TSM_ERR_CUDA;
-  if (rc == TSM_OK && cudaMemset(c.red.counter, 0, sizeof(unsigned int)) != cudaSuccess) rc = TSM_ERR_CUDA;
+  if (rc == TSM_OK && cudaMalloc(&c.red.counter, Ctx::kMaxStates * sizeof(unsigned int)) != cudaSuccess)
+    rc = TSM_ERR_CUDA;
+  if (rc == TSM_OK && cudaMemset(c.red.counter, 0, Ctx::kMaxStates * sizeof(unsigned int)) != cudaSuccess)
+    rc = TSM_ERR_CUDA;
+  if (rc == TSM_OK && cudaMalloc(&c.d_lists, 3 * Ctx::kMaxStates * sizeof(int)) != cudaSuccess) rc = TSM_ERR_CUDA;
+  if (rc == TSM_OK && cudaMallocHost(&c.h_lists, 3 * Ctx::kMaxStates * sizeof(int)) != cudaSuccess)
+    rc = TSM_ERR_CUDA;
   if (rc == TSM_OK && cudaMemset(c.states, 0, Ctx::kMaxStates * sizeof(CGState)) != cudaSuccess) rc = TSM_ERR_CUDA;
   if (rc != TSM_OK) {
     set_error("tsm_create: device allocation failed");
@@ -265,7 +266,9 @@ int tsm_load_gauge(tsm_ctx* h, const tm_lattice* lat, const double* U, int on_de
     TSM_CUDA(cudaMalloc(&c.links[TSM_F16], 2 * 4 * F16::LN * vh * sizeof(uint2)));
     if (c.red.partials) cudaFree(c.red.partials);
     c.red_cap = vh / 64 + 64;
-    TSM_CUDA(cudaMalloc(&c.red.partials, c.red_cap * sizeof(double)));
+    c.red.stride = (int)c.red_cap;
+    TSM_CUDA(cudaMalloc(&c.red.partials, Ctx::kMaxStates * c.red_cap * sizeof(double)));
+    c.batch_cap = 1;
   }
   const double* dU = nullptr;
   TSM_TRY(stage_in(c, "gauge_canon", U, (size_t)V * 4 * 9 * 2 * sizeof(double), on_device, &dU));
@@ -330,29 +333,37 @@ int tm_solve_batch(tsm_ctx* h, int nrhs, const double* b, double* s, const tm_st
   TSM_TRY(select_device(c));
   const size_t bytes = spinor_bytes(c);
   const int sp = solution_prec(*stop);
+  const int width = std::min(std::max(nrhs, 1), Ctx::kMaxBatch);
+  c.batch_cap = std::max(c.batch_cap, width);
   EOField fb, fs;
-  TSM_TRY(eo_fields(c, "sv_b", sp, &fb));
-  TSM_TRY(eo_fields(c, "sv_s", sp, &fs));
+  TSM_TRY(eo_fields(c, "sv_b", sp, &fb, c.batch_cap));
+  TSM_TRY(eo_fields(c, "sv_s", sp, &fs, c.batch_cap));
   int worst = TSM_OK;
-  for (int r = 0; r < nrhs; ++r) {
-    const double* db = nullptr;
-    double* ds = nullptr;
-    TSM_TRY(stage_in(c, "io_in", b + (size_t)r * c.g.V * 24, bytes, on_device, &db));
-    TSM_TRY(stage_out_ptr(c, "io_out", s + (size_t)r * c.g.V * 24, bytes, on_device, &ds));
-    TSM_TRY(pack_eo(c, sp, db, fb));
-    SolveResult res;
-    TSM_TRY(solve_source(c, *stop, 0, fb, fs, &res));
-    if (iters) iters[r] = res.iters;
-    if (true_res) {
-      double tr = 0.0;
-      TSM_TRY(true_residual(c, sp, fb, fs, &tr));
-      true_res[r] = tr;
+  std::vector<SolveResult> res(width);
+  for (int r0 = 0; r0 < nrhs; r0 += width) {
+    const int n = std::min(width, nrhs - r0);
+    for (int r = 0; r < n; ++r) {
+      const double* db = nullptr;
+      TSM_TRY(stage_in(c, "io_in", b + (size_t)(r0 + r) * c.g.V * 24, bytes, on_device, &db));
+      TSM_TRY(pack_eo(c, sp, db, eo_at(fb, sp, c.g.Vh, r)));
     }
-    TSM_TRY(unpack_eo(c, sp, fs, ds));
-    TSM_TRY(stage_out_finish(c, s + (size_t)r * c.g.V * 24, ds, bytes, on_device));
-    TSM_CUDA(cudaStreamSynchronize(c.stream));
-    if (res.status != TSM_OK) worst = res.status;
-    else if (!res.converged && worst == TSM_OK) worst = TSM_ERR_NOT_CONVERGED;
+    TSM_TRY(solve_batch(c, *stop, 0, n, fb, fs, res.data()));
+    for (int r = 0; r < n; ++r) {
+      const SolveResult& q = res[r];
+      if (iters) iters[r0 + r] = q.iters;
+      if (true_res) {
+        double tr = 0.0;
+        TSM_TRY(true_residual(c, sp, eo_at(fb, sp, c.g.Vh, r), eo_at(fs, sp, c.g.Vh, r), &tr));
+        true_res[r0 + r] = tr;
+      }
+      double* ds = nullptr;
+      TSM_TRY(stage_out_ptr(c, "io_out", s + (size_t)(r0 + r) * c.g.V * 24, bytes, on_device, &ds));
+      TSM_TRY(unpack_eo(c, sp, eo_at(fs, sp, c.g.Vh, r), ds));
+      TSM_TRY(stage_out_finish(c, s + (size_t)(r0 + r) * c.g.V * 24, ds, bytes, on_device));
+      TSM_CUDA(cudaStreamSynchronize(c.stream));
+      if (q.status != TSM_OK) worst = q.status;
+      else if (!q.converged && worst == TSM_OK) worst = TSM_ERR_NOT_CONVERGED;
+    }
   }
   TSM_TRY(c.harvest_events());
   if (worst != TSM_OK) set_error("at least one solve %s", worst == TSM_ERR_NONFINITE ? "met NaN/Inf" : "did not converge");
@@ -439,19 +450,22 @@ int tsm_loops(tsm_ctx* h, const tsm_params* p, double* loops, double* err, doubl
   TSM_TRY(c.buffer("tsm_per_lp", (size_t)std::max(n_lp, 1) * E * sizeof(double2), &vl));
   double2* d_corr = static_cast<double2*>(vc);
   double2* d_lp = static_cast<double2*>(vl);
+  const int B = std::min(std::max(p->batch, 1), Ctx::kMaxBatch);
+  c.batch_cap = std::max(c.batch_cap, B);
   EOField b_lp, s_lp, b_hp, s_hp;
-  TSM_TRY(eo_fields(c, "tsm_b_lp", sp_lp, &b_lp));
-  TSM_TRY(eo_fields(c, "tsm_s_lp", sp_lp, &s_lp));
-  TSM_TRY(eo_fields(c, "tsm_b_hp", sp_hp, &b_hp));
-  TSM_TRY(eo_fields(c, "tsm_s_hp", sp_hp, &s_hp));
+  TSM_TRY(eo_fields(c, "tsm_b_lp", sp_lp, &b_lp, c.batch_cap));
+  TSM_TRY(eo_fields(c, "tsm_s_lp", sp_lp, &s_lp, c.batch_cap));
+  TSM_TRY(eo_fields(c, "tsm_b_hp", sp_hp, &b_hp, c.batch_cap));
+  TSM_TRY(eo_fields(c, "tsm_s_hp", sp_hp, &s_hp, c.batch_cap));
   const NoiseSpec ns = make_noise(p->seed, p->noise);
   tsm_loop_stats st{};
   st.lp_max_true_res = -1.0;
-  auto gen = [&](int prec, uint32_t j, EOField f) {
+  // noise of sources j0 .. j0+n-1 into a batch of fields
+  auto gen = [&](int prec, uint32_t j0, EOField f, int n) {
     return dispatch_prec(prec, [&](auto tag) {
       using S = decltype(tag);
-      TSM_TRY(launch_noise<S>(c, 0, ns, j, f.e));
-      return launch_noise<S>(c, 1, ns, j, f.o);
+      TSM_TRY(launch_noise<S>(c, 0, ns, j0, f.e, n));
+      return launch_noise<S>(c, 1, ns, j0, f.o, n);
     });
   };
   auto contract = [&](uint32_t j, EOField a, int pa, const EOField* b, int pb, double2* out) {
@@ -461,29 +475,39 @@ int tsm_loops(tsm_ctx* h, const tsm_params* p, double* loops, double* err, doubl
     if (b == nullptr || pb == TSM_F32) return launch_contract<float, F32, F32>(c, plan, ns, j, a, b, out);
     return launch_contract<float, F32, F64>(c, plan, ns, j, a, b, out);
   };
-  for (uint32_t j = p->hp_begin; j < p->hp_end; ++j) {
-    SolveResult r_lp, r_hp;
-    TSM_TRY(gen(sp_lp, j, b_lp));
-    TSM_TRY(solve_source(c, p->lp, 0, b_lp, s_lp, &r_lp));
-    if (sp_hp != sp_lp) TSM_TRY(gen(sp_hp, j, b_hp));
+  std::vector<SolveResult> r_lp(B), r_hp(B);
+  // HP set: the LP map and the HP solve of every source, then L(s_HP - s_LP)
+  for (uint32_t j0 = p->hp_begin; j0 < p->hp_end; j0 += B) {
+    const int n = (int)std::min<uint32_t>(B, p->hp_end - j0);
+    TSM_TRY(gen(sp_lp, j0, b_lp, n));
+    TSM_TRY(solve_batch(c, p->lp, 0, n, b_lp, s_lp, r_lp.data()));
+    if (sp_hp != sp_lp) TSM_TRY(gen(sp_hp, j0, b_hp, n));
     EOField bh = (sp_hp != sp_lp) ? b_hp : b_lp;
-    TSM_TRY(solve_source(c, p->hp, 1, bh, s_hp, &r_hp));
-    if (r_lp.status != TSM_OK || r_hp.status != TSM_OK) return bad(TSM_ERR_NONFINITE, "NaN/Inf in a solve");
-    double tr = 0.0;
-    TSM_TRY(true_residual(c, sp_hp, bh, s_hp, &tr));
-    st.hp_max_true_res = std::max(st.hp_max_true_res, tr);
-    st.lp_iters += r_lp.iters;
-    st.hp_iters += r_hp.iters;
-    if (!r_hp.converged) st.hp_not_converged++;
-    TSM_TRY(contract(j, s_hp, sp_hp, &s_lp, sp_lp, d_corr + (size_t)(j - p->hp_begin) * E));
+    TSM_TRY(solve_batch(c, p->hp, 0, n, bh, s_hp, r_hp.data()));
+    for (int r = 0; r < n; ++r) {
+      if (r_lp[r].status != TSM_OK || r_hp[r].status != TSM_OK) return bad(TSM_ERR_NONFINITE, "NaN/Inf in a solve");
+      double tr = 0.0;
+      TSM_TRY(true_residual(c, sp_hp, eo_at(bh, sp_hp, c.g.Vh, r), eo_at(s_hp, sp_hp, c.g.Vh, r), &tr));
+      st.hp_max_true_res = std::max(st.hp_max_true_res, tr);
+      st.lp_iters += r_lp[r].iters;
+      st.hp_iters += r_hp[r].iters;
+      if (!r_hp[r].converged) st.hp_not_converged++;
+      const EOField sl = eo_at(s_lp, sp_lp, c.g.Vh, r);
+      TSM_TRY(contract(j0 + r, eo_at(s_hp, sp_hp, c.g.Vh, r), sp_hp, &sl, sp_lp,
+                       d_corr + (size_t)(j0 + r - p->hp_begin) * E));
+    }
   }
-  for (uint32_t j = p->lp_begin; j < p->lp_end; ++j) {
-    SolveResult r_lp;
-    TSM_TRY(gen(sp_lp, j, b_lp));
-    TSM_TRY(solve_source(c, p->lp, 0, b_lp, s_lp, &r_lp));
-    if (r_lp.status != TSM_OK) return bad(TSM_ERR_NONFINITE, "NaN/Inf in a solve");
-    st.lp_iters += r_lp.iters;
-    TSM_TRY(contract(j, s_lp, sp_lp, nullptr, sp_lp, d_lp + (size_t)(j - p->lp_begin) * E));
+  // LP set: the same LP map, L(s_LP)
+  for (uint32_t j0 = p->lp_begin; j0 < p->lp_end; j0 += B) {
+    const int n = (int)std::min<uint32_t>(B, p->lp_end - j0);
+    TSM_TRY(gen(sp_lp, j0, b_lp, n));
+    TSM_TRY(solve_batch(c, p->lp, 0, n, b_lp, s_lp, r_lp.data()));
+    for (int r = 0; r < n; ++r) {
+      if (r_lp[r].status != TSM_OK) return bad(TSM_ERR_NONFINITE, "NaN/Inf in a solve");
+      st.lp_iters += r_lp[r].iters;
+      TSM_TRY(contract(j0 + r, eo_at(s_lp, sp_lp, c.g.Vh, r), sp_lp, nullptr, sp_lp,
+                       d_lp + (size_t)(j0 + r - p->lp_begin) * E));
+    }
   }
   st.n_sources = n_hp + n_lp;
   // Eq. 2.4 combine
@@ -541,7 +565,7 @@ int tsm_profile(tsm_ctx* h, int enable) {
   TSM_TRY(c.harvest_events());
   c.profile = enable != 0;
   if (enable) {
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < Ctx::kProfBuckets; ++k) {
       c.prof_ms[k] = 0.0;
       c.prof_cnt[k] = 0;
       c.prof_bytes[k] = 0.0;
@@ -550,12 +574,12 @@ int tsm_profile(tsm_ctx* h, int enable) {
   return TSM_OK;
 }
 
-int tsm_profile_read(tsm_ctx* h, double ms[4], long long count[4], double bytes[4]) {
+int tsm_profile_read(tsm_ctx* h, double ms[16], long long count[16], double bytes[16]) {
   if (h == nullptr) return bad(TSM_ERR_ARG, "null context");
   Ctx& c = h->c;
   TSM_TRY(select_device(c));
   TSM_TRY(c.harvest_events());
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < Ctx::kProfBuckets; ++k) {
     if (ms) ms[k] = c.prof_ms[k];
     if (count) count[k] = c.prof_cnt[k];
     if (bytes) bytes[k] = c.prof_bytes[k];

@@ -357,13 +357,17 @@ __device__ __forceinline__ void post_action(CGState* st, int op, double sum) {
 }
 
 // ---------------------------------------------------------------- reductions
-// Two-stage deterministic sum: every block writes its partial to
-// partials[block]; the last block to finish (atomic ticket) adds the partials
-// in block order and applies the post action.  The ticket counter is reset
-// by that block so the slot can be reused by the next launch.
+// Two-stage deterministic sum per right-hand side: the blocks of one RHS are
+// blockIdx.y = 0 .. gridDim.y-1 (blockIdx.x selects the RHS); every block
+// writes its partial to partials[rhs * stride + block]; the last block of
+// that RHS to finish (atomic ticket) adds the partials in block order and
+// applies the post action.  The ticket counter is reset by that block so the
+// slot can be reused by the next launch.  The sum of one RHS therefore does
+// not depend on which other right-hand sides share the launch.
 struct RedSlot {
-  double* partials;
-  unsigned int* counter;
+  double* partials;       // [rhs][stride]
+  unsigned int* counter;  // [rhs]
+  int stride;
 };
 
 template <int NT>
@@ -382,32 +386,46 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return s;  // valid in thread 0
 }
 
-// Called by all threads of every block.  Returns true in the last block, in
-// which thread 0 holds the grid total in *total.
+// Called by all threads of every block of right-hand side `rhs`.  Returns
+// true in the last block of that RHS, in which thread 0 holds its total.
 template <int NT>
-__device__ __forceinline__ bool grid_sum(double v, RedSlot slot, double* total) {
+__device__ __forceinline__ bool grid_sum(double v, RedSlot slot, int rhs, double* total) {
   __shared__ double sh[NT / 32];
   __shared__ bool is_last;
-  const int nblocks = gridDim.x;
+  const int nblocks = gridDim.y;
+  double* partials = slot.partials + (size_t)rhs * slot.stride;
+  unsigned int* counter = slot.counter + rhs;
   double s = block_sum<NT>(v, sh);
   if (threadIdx.x == 0) {
-    slot.partials[blockIdx.x] = s;
+    partials[blockIdx.y] = s;
     __threadfence();
-    const unsigned int ticket = atomicAdd(slot.counter, 1u);
+    const unsigned int ticket = atomicAdd(counter, 1u);
     is_last = (ticket == (unsigned int)(nblocks - 1));
   }
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
   double acc = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += NT) acc += __ldcg(slot.partials + b);
+  for (int b = threadIdx.x; b < nblocks; b += NT) acc += __ldcg(partials + b);
   // fixed-order tree over the threads' strided partial sums
   double tot = block_sum<NT>(acc, sh);
   if (threadIdx.x == 0) {
     *total = tot;
-    *slot.counter = 0u;
+    *counter = 0u;
   }
   return true;
+}
+
+// right-hand side handled by this block: blockIdx.x, or the entry of an
+// active list (converged right-hand sides are left out of later launches)
+__device__ __forceinline__ int rhs_slot(const int* active) {
+  return active != nullptr ? active[blockIdx.x] : (int)blockIdx.x;
+}
+
+// offset of right-hand side `rhs` in a batch of contiguous fields of storage S
+template <class S>
+__device__ __forceinline__ size_t rhs_offset(int rhs, int sstride) {
+  return (size_t)rhs * S::SN * (size_t)sstride;
 }
 
 }  // namespace tsm

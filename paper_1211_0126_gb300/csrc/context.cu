@@ -69,8 +69,8 @@ int Ctx::buffer(const std::string& name, size_t bytes, void** out) {
   return TSM_OK;
 }
 
-int Ctx::field(const std::string& name, int prec, PField* f) {
-  return buffer(name + "#" + std::to_string(prec), field_bytes(prec, sstride), &f->p);
+int Ctx::field(const std::string& name, int prec, PField* f, int nrhs) {
+  return buffer(name + "#" + std::to_string(prec), field_bytes(prec, sstride) * (size_t)(nrhs > 0 ? nrhs : 1), &f->p);
 }
 
 int Ctx::harvest_events() {
@@ -102,8 +102,12 @@ void Ctx::free_all() {
   red = RedSlot{};
   if (states) cudaFree(states);
   if (h_states) cudaFreeHost(h_states);
+  if (d_lists) cudaFree(d_lists);
+  if (h_lists) cudaFreeHost(h_lists);
   states = nullptr;
   h_states = nullptr;
+  d_lists = nullptr;
+  h_lists = nullptr;
   for (auto& r : ev_free) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);

@@ -61,7 +61,11 @@ struct Ctx {
   size_t red_cap = 0;
   CGState* states = nullptr;    // device, kMaxStates
   CGState* h_states = nullptr;  // pinned mirror
-  static constexpr int kMaxStates = 64;
+  static constexpr int kMaxStates = 256;   // last 4 reserved for auxiliary reductions
+  static constexpr int kMaxBatch = 64;     // right-hand sides per batched solve
+  int* d_lists = nullptr;       // device: 3 lists of kMaxStates right-hand-side indices
+  int* h_lists = nullptr;       // pinned staging of the lists
+  int batch_cap = 1;            // batch width the solver workspace is laid out for
   // instrumentation
   bool profile = false;
   struct EvRec {
@@ -70,9 +74,10 @@ struct Ctx {
     double bytes;
   };
   std::vector<EvRec> ev_free, ev_pending;
-  double prof_ms[4] = {0, 0, 0, 0};
-  long long prof_cnt[4] = {0, 0, 0, 0};
-  double prof_bytes[4] = {0, 0, 0, 0};
+  static constexpr int kProfBuckets = 16;   // 4 storage tiers x 4 hop kinds
+  double prof_ms[kProfBuckets] = {};
+  long long prof_cnt[kProfBuckets] = {};
+  double prof_bytes[kProfBuckets] = {};
   bool prof_this_launch = false;   // solver sets it for the instrumented iteration
   long long launches = 0;
 
@@ -81,12 +86,20 @@ struct Ctx {
   template <class S> const typename S::lchunk* links_of(int parity) const {
     return static_cast<const typename S::lchunk*>(links[S::id]) + (size_t)parity * 4 * S::LN * lstride;
   }
-  int field(const std::string& name, int prec, PField* f);    // one parity field of tier prec
+  int field(const std::string& name, int prec, PField* f, int nrhs = 1);   // nrhs parity fields of tier prec
   int harvest_events();                                        // sync + accumulate profile times
   void free_all();
 };
 
 size_t field_bytes(int prec, int vh);
+
+// field of right-hand side `rhs` inside a batch of contiguous parity fields
+inline PField field_at(const PField& f, int prec, int vh, int rhs) {
+  return PField{static_cast<char*>(f.p) + field_bytes(prec, vh) * (size_t)rhs};
+}
+inline EOField eo_at(const EOField& f, int prec, int vh, int rhs) {
+  return EOField{field_at(f.e, prec, vh, rhs), field_at(f.o, prec, vh, rhs)};
+}
 
 // Twist factors (diagonal in the chiral basis)
 inline Twist twist_one() { return Twist{{1.0, 1.0}, {0.0, 0.0}}; }
@@ -101,16 +114,25 @@ inline Twist twist_Ainv(double kappa, double m) {
   return Twist{{1.0 / d, 1.0 / d}, {-2.0 * kappa * m / d, 2.0 * kappa * m / d}};
 }
 
-// ---- launch helpers (instantiated per storage type in ops_*.cu)
-template <class S> int launch_hop(Ctx& c, const HopArgs<S>& a, int dag, int mode, int prof_kind);
-template <class S, class SA> int launch_cg_update(Ctx& c, const CGUpdArgs<S, SA>& a);
-template <class S, class SA> int launch_cg_p(Ctx& c, const PField& r, const PField& p, CGState* st);
+// ---- launch helpers (instantiated per storage type in ops_*.cu).  Batched
+// helpers take nrhs right-hand sides stored as contiguous parity fields (the
+// grid's x dimension), optionally through a device list `active` of the
+// right-hand sides still iterating.
+template <class S> int launch_hop(Ctx& c, const HopArgs<S>& a, int dag, int mode, int prof_kind, int nrhs = 1);
+template <class S, class SA> int launch_cg_update(Ctx& c, const CGUpdArgs<S, SA>& a, int nrhs);
+template <class S, class SA>
+int launch_cg_p(Ctx& c, const PField& r, const PField& p, CGState* st, const int* active, int nrhs);
 template <class S> int launch_pack(Ctx& c, int parity, const double* canon, const PField& out);
 template <class S> int launch_unpack(Ctx& c, int parity, const PField& in, double* canon);
-template <class S> int launch_noise(Ctx& c, int parity, const NoiseSpec& n, uint32_t source, const PField& out);
-template <class S> int launch_twist(Ctx& c, const Twist& f, const PField& in, const PField& out, const CGState* st);
-template <class S> int launch_norm(Ctx& c, const PField& v, CGState* st, int post);
-template <class Si, class So> int launch_convert(Ctx& c, const PField& in, const PField& out);
+template <class S>
+int launch_noise(Ctx& c, int parity, const NoiseSpec& n, uint32_t source0, const PField& out, int nrhs = 1);
+template <class S>
+int launch_twist(Ctx& c, const Twist& f, const PField& in, const PField& out, const CGState* st,
+                 const int* active = nullptr, int nrhs = 1);
+template <class S>
+int launch_norm(Ctx& c, const PField& v, CGState* st, int post, const int* active = nullptr, int nrhs = 1);
+template <class Si, class So>
+int launch_convert(Ctx& c, const PField& in, const PField& out, const int* active = nullptr, int nrhs = 1);
 
 // runtime dispatch on a tier id (0 F64, 1 F32, 2 BF16, 3 F16):
 // f receives an empty tag object of the storage type

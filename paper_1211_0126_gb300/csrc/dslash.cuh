@@ -155,6 +155,11 @@ __device__ __forceinline__ void hop_site(const Geom& g, int ih, const int c[4],
 // ------------------------------------------------------------- generic hop kernel
 // out(x) = ts * q,  q = base(x) + to * (ac * tc * center(x) + ah * H psi (x))
 // with optional <q, q> reduction.  MODE bits select center / base / norm.
+// Grid: blockIdx.x = right-hand side (through an optional active list),
+// blockIdx.y = block of HOP_NT output sites.  in / center / base / out are
+// batches of contiguous parity fields, one per right-hand side; the links are
+// shared by all of them (their reuse across right-hand sides comes from L2,
+// since consecutive blocks in launch order handle the same sites).
 enum { HOP_CENTER = 1, HOP_NORM = 2, HOP_BASE = 4 };
 
 template <class S>
@@ -171,8 +176,9 @@ struct HopArgs {
   int sstride;
   double ac, ah;
   Twist tc, to, ts;
-  const CGState* skip;                     // optional: return at once when skip->done
-  CGState* st;                             // state receiving the HOP_NORM post action
+  const int* active;                       // optional list of right-hand sides
+  const CGState* skip;                     // optional: a RHS returns at once when skip[rhs].done
+  CGState* st;                             // states receiving the HOP_NORM post action
   RedSlot red;                             // HOP_NORM
   int post;                                // PostOp for HOP_NORM
 };
@@ -182,20 +188,22 @@ constexpr int HOP_NT = 128;
 template <class S, int DAG, int MODE>
 __global__ void __launch_bounds__(HOP_NT) hop_kernel(const HopArgs<S> a) {
   using R = typename S::real;
-  if (a.skip != nullptr && a.skip->done) return;
-  const int ih = blockIdx.x * HOP_NT + threadIdx.x;
+  const int rhs = rhs_slot(a.active);
+  if (a.skip != nullptr && a.skip[rhs].done) return;
+  const size_t off = rhs_offset<S>(rhs, a.sstride);
+  const int ih = blockIdx.y * HOP_NT + threadIdx.x;
   double part = 0.0;
   if (ih < a.g.Vh) {
     int c[4];
     site_coords(a.g, a.p_out, ih, c);
     cx<R> acc[12];
-    hop_site<S, DAG>(a.g, ih, c, a.Uout, a.Uin, a.lstride, a.in, a.sstride, acc);
+    hop_site<S, DAG>(a.g, ih, c, a.Uout, a.Uin, a.lstride, a.in + off, a.sstride, acc);
     const R ah = (R)a.ah;
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = ah * acc[k];
     if constexpr (MODE & HOP_CENTER) {
       cx<R> v[12];
-      load_spinor<S>(a.center, a.sstride, ih, v);
+      load_spinor<S>(a.center + off, a.sstride, ih, v);
       apply_twist(a.tc, v);
       const R ac = (R)a.ac;
 #pragma unroll
@@ -204,7 +212,7 @@ __global__ void __launch_bounds__(HOP_NT) hop_kernel(const HopArgs<S> a) {
     apply_twist(a.to, acc);
     if constexpr (MODE & HOP_BASE) {
       cx<R> v[12];
-      load_spinor<S>(a.base, a.sstride, ih, v);
+      load_spinor<S>(a.base + off, a.sstride, ih, v);
 #pragma unroll
       for (int k = 0; k < 12; ++k) acc[k] = acc[k] + v[k];
     }
@@ -215,18 +223,19 @@ __global__ void __launch_bounds__(HOP_NT) hop_kernel(const HopArgs<S> a) {
       part = (double)s;
     }
     apply_twist(a.ts, acc);
-    store_spinor<S>(a.out, a.sstride, ih, acc);
+    store_spinor<S>(a.out + off, a.sstride, ih, acc);
   }
   if constexpr (MODE & HOP_NORM) {
     double total;
-    if (grid_sum<HOP_NT>(part, a.red, &total) && threadIdx.x == 0) post_action(a.st, a.post, total);
+    if (grid_sum<HOP_NT>(part, a.red, rhs, &total) && threadIdx.x == 0 && a.st != nullptr)
+      post_action(a.st + rhs, a.post, total);
   }
 }
 
 // ------------------------------------------------------------- fused CG update
 // For even output sites:  v = A(-mu) w - kappa^2 (H^dag)_eo t  (= Dhat^dag Dhat p),
 // r -= alpha v,  x += alpha p,  <r, r> -> post POST_RR (beta, iteration, stop).
-// Sloppy storage S for w, t, p and links; SA for r and x.
+// Sloppy storage S for w, t, p and links; SA for r and x.  Batched like hop_kernel.
 template <class S, class SA>
 struct CGUpdArgs {
   Geom g;
@@ -241,6 +250,7 @@ struct CGUpdArgs {
   int sstride;
   double kappa2;
   Twist tw;                         // A(-mu)
+  const int* active;
   CGState* st;
   RedSlot red;
 };
@@ -249,24 +259,27 @@ template <class S, class SA>
 __global__ void __launch_bounds__(HOP_NT) cg_update_kernel(const CGUpdArgs<S, SA> a) {
   using R = typename S::real;
   using RA = typename SA::real;
-  if (a.st->done) return;
-  const int ih = blockIdx.x * HOP_NT + threadIdx.x;
+  const int rhs = rhs_slot(a.active);
+  CGState* st = a.st + rhs;
+  if (st->done) return;
+  const size_t off = rhs_offset<S>(rhs, a.sstride), offa = rhs_offset<SA>(rhs, a.sstride);
+  const int ih = blockIdx.y * HOP_NT + threadIdx.x;
   double part = 0.0;
   if (ih < a.g.Vh) {
     int c[4];
     site_coords(a.g, 0, ih, c);
     cx<R> acc[12], v[12];
-    hop_site<S, 1>(a.g, ih, c, a.Ue, a.Uo, a.lstride, a.t, a.sstride, acc);
-    load_spinor<S>(a.w, a.sstride, ih, v);
+    hop_site<S, 1>(a.g, ih, c, a.Ue, a.Uo, a.lstride, a.t + off, a.sstride, acc);
+    load_spinor<S>(a.w + off, a.sstride, ih, v);
     apply_twist(a.tw, v);
     const R k2 = (R)a.kappa2;
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = v[k] - k2 * acc[k];
-    const RA alpha = (RA)a.st->alpha;
+    const RA alpha = (RA)st->alpha;
     cx<RA> rv[12], xv[12];
-    load_spinor<SA>(a.r, a.sstride, ih, rv);
-    load_spinor<SA>(a.x, a.sstride, ih, xv);
-    load_spinor<S>(a.p, a.sstride, ih, v);
+    load_spinor<SA>(a.r + offa, a.sstride, ih, rv);
+    load_spinor<SA>(a.x + offa, a.sstride, ih, xv);
+    load_spinor<S>(a.p + off, a.sstride, ih, v);
     RA s = 0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
@@ -275,24 +288,27 @@ __global__ void __launch_bounds__(HOP_NT) cg_update_kernel(const CGUpdArgs<S, SA
       s += norm2(rv[k]);
     }
     part = (double)s;
-    store_spinor<SA>(a.r, a.sstride, ih, rv);
-    store_spinor<SA>(a.x, a.sstride, ih, xv);
+    store_spinor<SA>(a.r + offa, a.sstride, ih, rv);
+    store_spinor<SA>(a.x + offa, a.sstride, ih, xv);
   }
   double total;
-  if (grid_sum<HOP_NT>(part, a.red, &total) && threadIdx.x == 0) post_action(a.st, POST_RR, total);
+  if (grid_sum<HOP_NT>(part, a.red, rhs, &total) && threadIdx.x == 0) post_action(st, POST_RR, total);
 }
 
-// p = r + beta p
+// p = r + beta p   (grid: x = right-hand side, y = blocks of 256 sites)
 template <class S, class SA>
 __global__ void __launch_bounds__(256) cg_p_kernel(const typename SA::schunk* __restrict__ r,
                                                    typename S::schunk* __restrict__ p, int sstride, int Vh,
-                                                   const CGState* st) {
-  if (st->done) return;
-  const int ih = blockIdx.x * blockDim.x + threadIdx.x;
+                                                   const int* active, const CGState* st) {
+  const int rhs = rhs_slot(active);
+  if (st[rhs].done) return;
+  const int ih = blockIdx.y * blockDim.x + threadIdx.x;
   if (ih >= Vh) return;
   using R = typename S::real;
   using RA = typename SA::real;
-  const RA beta = (RA)st->beta;
+  r += rhs_offset<SA>(rhs, sstride);
+  p += rhs_offset<S>(rhs, sstride);
+  const RA beta = (RA)st[rhs].beta;
   cx<RA> rv[12];
   cx<R> pv[12];
   load_spinor<SA>(r, sstride, ih, rv);

@@ -95,25 +95,27 @@ static __global__ void __launch_bounds__(SITE_NT) pack_links_kernel(Geom g, cons
   store_link<BF16>(lbf + off32, lstride, mu, ih, rf);
 }
 
-// noise source -> parity field in S (eta is exactly representable in every tier
-// except the 1/sqrt 2 amplitude, which is rounded once)
+// noise sources source0 + rhs -> batch of parity fields in S (eta is exactly
+// representable in every tier except the 1/sqrt 2 amplitude, rounded once).
+// Grid: x = right-hand side, y = blocks of SITE_NT sites.
 template <class S>
-__global__ void __launch_bounds__(SITE_NT) noise_kernel(Geom g, int parity, NoiseSpec n, uint32_t source,
+__global__ void __launch_bounds__(SITE_NT) noise_kernel(Geom g, int parity, NoiseSpec n, uint32_t source0,
                                                         typename S::schunk* __restrict__ out, int sstride) {
   using R = typename S::real;
-  const int ih = blockIdx.x * SITE_NT + threadIdx.x;
+  const int rhs = blockIdx.x;
+  const int ih = blockIdx.y * SITE_NT + threadIdx.x;
   if (ih >= g.Vh) return;
   int c[4];
   site_coords(g, parity, ih, c);
   const uint32_t lex = (uint32_t)(((c[3] * g.L[2] + c[2]) * g.L[1] + c[1]) * g.L[0] + c[0]);
   cx<R> v[12];
-  noise_site<R>(n, lex, source, v);
-  store_spinor<S>(out, sstride, ih, v);
+  noise_site<R>(n, lex, source0 + (uint32_t)rhs, v);
+  store_spinor<S>(out + rhs_offset<S>(rhs, sstride), sstride, ih, v);
 }
 
 // noise source in the canonical layout (for exact comparisons)
 static __global__ void __launch_bounds__(SITE_NT) noise_canon_kernel(int V, NoiseSpec n, uint32_t source,
-                                                              double2* __restrict__ out) {
+                                                                     double2* __restrict__ out) {
   const int lex = blockIdx.x * SITE_NT + threadIdx.x;
   if (lex >= V) return;
   cx<double> v[12];
@@ -122,44 +124,52 @@ static __global__ void __launch_bounds__(SITE_NT) noise_canon_kernel(int V, Nois
   for (int k = 0; k < 12; ++k) out[(size_t)lex * 12 + k] = make_double2(v[k].re, v[k].im);
 }
 
-// out = f * in (site-local chiral twist), optional skip on st->done
+// out = f * in (site-local chiral twist); a RHS with st[rhs].done is skipped
 template <class S>
 __global__ void __launch_bounds__(SITE_NT) twist_kernel(int Vh, Twist f, const typename S::schunk* __restrict__ in,
                                                         typename S::schunk* __restrict__ out, int sstride,
-                                                        const CGState* st) {
-  if (st != nullptr && st->done) return;
-  const int ih = blockIdx.x * SITE_NT + threadIdx.x;
+                                                        const int* active, const CGState* st) {
+  const int rhs = rhs_slot(active);
+  if (st != nullptr && st[rhs].done) return;
+  const int ih = blockIdx.y * SITE_NT + threadIdx.x;
   if (ih >= Vh) return;
+  const size_t off = rhs_offset<S>(rhs, sstride);
   cx<typename S::real> v[12];
-  load_spinor<S>(in, sstride, ih, v);
+  load_spinor<S>(in + off, sstride, ih, v);
   apply_twist(f, v);
-  store_spinor<S>(out, sstride, ih, v);
+  store_spinor<S>(out + off, sstride, ih, v);
 }
 
 // out (So) = in (Si), precision cast; in == nullptr writes zero
 template <class Si, class So>
 __global__ void __launch_bounds__(SITE_NT) convert_kernel(int Vh, const typename Si::schunk* __restrict__ in,
-                                                          typename So::schunk* __restrict__ out, int sstride) {
-  const int ih = blockIdx.x * SITE_NT + threadIdx.x;
+                                                          typename So::schunk* __restrict__ out, int sstride,
+                                                          const int* active) {
+  const int rhs = rhs_slot(active);
+  const int ih = blockIdx.y * SITE_NT + threadIdx.x;
   if (ih >= Vh) return;
   cx<typename Si::real> v[12];
   cx<typename So::real> w[12];
   if (in != nullptr) {
-    load_spinor<Si>(in, sstride, ih, v);
+    load_spinor<Si>(in + rhs_offset<Si>(rhs, sstride), sstride, ih, v);
 #pragma unroll
     for (int k = 0; k < 12; ++k) w[k] = {(typename So::real)v[k].re, (typename So::real)v[k].im};
   } else {
 #pragma unroll
     for (int k = 0; k < 12; ++k) w[k] = {0, 0};
   }
-  store_spinor<So>(out, sstride, ih, w);
+  store_spinor<So>(out + rhs_offset<So>(rhs, sstride), sstride, ih, w);
 }
 
 // reliable update, step 1: x64 += y (y in F32), y = 0
 static __global__ void __launch_bounds__(SITE_NT) accumulate_solution_kernel(int Vh, float4* __restrict__ y,
-                                                                      double2* __restrict__ x, int sstride) {
-  const int ih = blockIdx.x * SITE_NT + threadIdx.x;
+                                                                             double2* __restrict__ x, int sstride,
+                                                                             const int* active) {
+  const int rhs = rhs_slot(active);
+  const int ih = blockIdx.y * SITE_NT + threadIdx.x;
   if (ih >= Vh) return;
+  y += rhs_offset<F32>(rhs, sstride);
+  x += rhs_offset<F64>(rhs, sstride);
   cx<float> yv[12];
   cx<double> xv[12];
   load_spinor<F32>(y, sstride, ih, yv);
@@ -173,37 +183,45 @@ static __global__ void __launch_bounds__(SITE_NT) accumulate_solution_kernel(int
   store_spinor<F32>(y, sstride, ih, yv);
 }
 
-// <v, v> over one parity field with post action (deterministic two-stage sum)
+// <v, v> per right-hand side with post action (deterministic two-stage sum)
 template <class S>
 __global__ void __launch_bounds__(SITE_NT) norm_kernel(int Vh, const typename S::schunk* __restrict__ v, int sstride,
-                                                       RedSlot red, CGState* st, int post) {
-  const int ih = blockIdx.x * SITE_NT + threadIdx.x;
+                                                       RedSlot red, const int* active, CGState* st, int post) {
+  const int rhs = rhs_slot(active);
+  const int ih = blockIdx.y * SITE_NT + threadIdx.x;
   double part = 0.0;
   if (ih < Vh) {
     cx<typename S::real> w[12];
-    load_spinor<S>(v, sstride, ih, w);
+    load_spinor<S>(v + rhs_offset<S>(rhs, sstride), sstride, ih, w);
     typename S::real s = 0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) s += norm2(w[k]);
     part = (double)s;
   }
   double total;
-  if (grid_sum<SITE_NT>(part, red, &total) && threadIdx.x == 0) post_action(st, post, total);
+  if (grid_sum<SITE_NT>(part, red, rhs, &total) && threadIdx.x == 0) post_action(st + rhs, post, total);
 }
 
-static __global__ void state_init_kernel(CGState* st, double tol, int max_iter) {
-  st->tol = tol;
-  st->max_iter = max_iter;
-  st->iter = 0;
-  st->done = 0;
-  st->status = 0;
-  st->rr = st->rr0 = st->pAp = st->alpha = st->beta = st->aux = 0.0;
+// states 0 .. n-1: fresh solve
+static __global__ void state_init_kernel(CGState* st, int n, double tol, int max_iter) {
+  const int k = threadIdx.x + blockIdx.x * blockDim.x;
+  if (k >= n) return;
+  CGState& s = st[k];
+  s.tol = tol;
+  s.max_iter = max_iter;
+  s.iter = 0;
+  s.done = 0;
+  s.status = 0;
+  s.rr = s.rr0 = s.pAp = s.alpha = s.beta = s.aux = 0.0;
 }
 
-// clear `done` so that iterations resume (after a reliable update that found
-// the true residual still above tolerance)
-static __global__ void state_resume_kernel(CGState* st) {
-  if (st->status == 0 && st->iter < st->max_iter) st->done = 0;
+// clear `done` of the listed states so that iterations resume (after a
+// reliable update that found the true residual still above tolerance)
+static __global__ void state_resume_kernel(CGState* st, const int* list, int n) {
+  const int k = threadIdx.x + blockIdx.x * blockDim.x;
+  if (k >= n) return;
+  CGState& s = st[list[k]];
+  if (s.status == 0 && s.iter < s.max_iter) s.done = 0;
 }
 
 }  // namespace tsm

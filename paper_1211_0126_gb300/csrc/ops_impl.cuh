@@ -44,15 +44,18 @@ struct TimedLaunch {
 };
 
 template <class S>
-int launch_hop(Ctx& c, const HopArgs<S>& a, int dag, int mode, int prof_kind) {
+int launch_hop(Ctx& c, const HopArgs<S>& a, int dag, int mode, int prof_kind, int nrhs) {
   const int nb = blocks_for(a.g.Vh, HOP_NT);
-  if (nb == 0) return TSM_OK;
+  if (nb == 0 || nrhs == 0) return TSM_OK;
   const int kind = prof_kind >= 0 ? prof_kind : hop_kind_of<S>(dag, mode);
   const double sb = spinor_site_bytes(S::id), lb = link_site_bytes(S::id);
-  const double bytes = (double)a.g.Vh * (lb + sb * (2 + ((mode & HOP_CENTER) ? 1 : 0) + ((mode & HOP_BASE) ? 1 : 0)));
-  TimedLaunch tl(c, kind, bytes);
+  // links once per launch (shared by the right-hand sides), spinor streams per RHS
+  const double bytes = (double)a.g.Vh *
+      (lb + nrhs * sb * (2 + ((mode & HOP_CENTER) ? 1 : 0) + ((mode & HOP_BASE) ? 1 : 0)));
+  TimedLaunch tl(c, 4 * S::id + kind, bytes);
+  const dim3 grid(nrhs, nb);
 #define TSM_HOP_CASE(D, M) \
-  if (dag == (D) && mode == (M)) hop_kernel<S, (D), (M)><<<nb, HOP_NT, 0, c.stream>>>(a);
+  if (dag == (D) && mode == (M)) hop_kernel<S, (D), (M)><<<grid, HOP_NT, 0, c.stream>>>(a);
   TSM_HOP_CASE(0, 0)
   else TSM_HOP_CASE(0, HOP_CENTER)
   else TSM_HOP_CASE(0, HOP_CENTER | HOP_NORM)
@@ -72,22 +75,22 @@ int launch_hop(Ctx& c, const HopArgs<S>& a, int dag, int mode, int prof_kind) {
 }
 
 template <class S, class SA>
-int launch_cg_update(Ctx& c, const CGUpdArgs<S, SA>& a) {
+int launch_cg_update(Ctx& c, const CGUpdArgs<S, SA>& a, int nrhs) {
   const int nb = blocks_for(a.g.Vh, HOP_NT);
-  if (nb == 0) return TSM_OK;
+  if (nb == 0 || nrhs == 0) return TSM_OK;
   const double sb = spinor_site_bytes(S::id), lb = link_site_bytes(S::id), sa = spinor_site_bytes(SA::id);
-  TimedLaunch tl(c, PK_HOP_UPDATE, (double)a.g.Vh * (lb + 3 * sb + 4 * sa));
-  cg_update_kernel<S, SA><<<nb, HOP_NT, 0, c.stream>>>(a);
+  TimedLaunch tl(c, 4 * S::id + PK_HOP_UPDATE, (double)a.g.Vh * (lb + nrhs * (3 * sb + 4 * sa)));
+  cg_update_kernel<S, SA><<<dim3(nrhs, nb), HOP_NT, 0, c.stream>>>(a);
   tl.done();
   c.launches++;
   return check_launch(c, "cg_update_kernel");
 }
 
 template <class S, class SA>
-int launch_cg_p(Ctx& c, const PField& r, const PField& p, CGState* st) {
+int launch_cg_p(Ctx& c, const PField& r, const PField& p, CGState* st, const int* active, int nrhs) {
   const int nb = blocks_for(c.g.Vh, SITE_NT);
-  if (nb == 0) return TSM_OK;
-  cg_p_kernel<S, SA><<<nb, SITE_NT, 0, c.stream>>>(r.as<SA>(), p.as<S>(), c.sstride, c.g.Vh, st);
+  if (nb == 0 || nrhs == 0) return TSM_OK;
+  cg_p_kernel<S, SA><<<dim3(nrhs, nb), SITE_NT, 0, c.stream>>>(r.as<SA>(), p.as<S>(), c.sstride, c.g.Vh, active, st);
   c.launches++;
   return check_launch(c, "cg_p_kernel");
 }
@@ -111,50 +114,57 @@ int launch_unpack(Ctx& c, int parity, const PField& in, double* canon) {
 }
 
 template <class S>
-int launch_noise(Ctx& c, int parity, const NoiseSpec& n, uint32_t source, const PField& out) {
+int launch_noise(Ctx& c, int parity, const NoiseSpec& n, uint32_t source0, const PField& out, int nrhs) {
   const int nb = blocks_for(c.g.Vh, SITE_NT);
-  noise_kernel<S><<<nb, SITE_NT, 0, c.stream>>>(c.g, parity, n, source, out.as<S>(), c.sstride);
+  noise_kernel<S><<<dim3(nrhs, nb), SITE_NT, 0, c.stream>>>(c.g, parity, n, source0, out.as<S>(), c.sstride);
   c.launches++;
   return check_launch(c, "noise_kernel");
 }
 
 template <class S>
-int launch_twist(Ctx& c, const Twist& f, const PField& in, const PField& out, const CGState* st) {
+int launch_twist(Ctx& c, const Twist& f, const PField& in, const PField& out, const CGState* st,
+                 const int* active, int nrhs) {
   const int nb = blocks_for(c.g.Vh, SITE_NT);
-  twist_kernel<S><<<nb, SITE_NT, 0, c.stream>>>(c.g.Vh, f, in.as<S>(), out.as<S>(), c.sstride, st);
+  if (nrhs == 0) return TSM_OK;
+  twist_kernel<S><<<dim3(nrhs, nb), SITE_NT, 0, c.stream>>>(c.g.Vh, f, in.as<S>(), out.as<S>(), c.sstride, active,
+                                                            st);
   c.launches++;
   return check_launch(c, "twist_kernel");
 }
 
 template <class S>
-int launch_norm(Ctx& c, const PField& v, CGState* st, int post) {
+int launch_norm(Ctx& c, const PField& v, CGState* st, int post, const int* active, int nrhs) {
   const int nb = blocks_for(c.g.Vh, SITE_NT);
-  norm_kernel<S><<<nb, SITE_NT, 0, c.stream>>>(c.g.Vh, v.as<S>(), c.sstride, c.red, st, post);
+  if (nrhs == 0) return TSM_OK;
+  norm_kernel<S><<<dim3(nrhs, nb), SITE_NT, 0, c.stream>>>(c.g.Vh, v.as<S>(), c.sstride, c.red, active, st, post);
   c.launches++;
   return check_launch(c, "norm_kernel");
 }
 
 template <class Si, class So>
-int launch_convert(Ctx& c, const PField& in, const PField& out) {
+int launch_convert(Ctx& c, const PField& in, const PField& out, const int* active, int nrhs) {
   const int nb = blocks_for(c.g.Vh, SITE_NT);
-  convert_kernel<Si, So><<<nb, SITE_NT, 0, c.stream>>>(c.g.Vh, in.as<Si>(), out.as<So>(), c.sstride);
+  if (nrhs == 0) return TSM_OK;
+  convert_kernel<Si, So><<<dim3(nrhs, nb), SITE_NT, 0, c.stream>>>(c.g.Vh, in.as<Si>(), out.as<So>(), c.sstride,
+                                                                   active);
   c.launches++;
   return check_launch(c, "convert_kernel");
 }
 
 }  // namespace tsm
 
-#define TSM_INSTANTIATE_STORAGE(S)                                                                  \
-  template int tsm::launch_hop<S>(Ctx&, const HopArgs<S>&, int, int, int);                         \
-  template int tsm::launch_pack<S>(Ctx&, int, const double*, const PField&);                       \
-  template int tsm::launch_unpack<S>(Ctx&, int, const PField&, double*);                           \
-  template int tsm::launch_noise<S>(Ctx&, int, const NoiseSpec&, uint32_t, const PField&);         \
-  template int tsm::launch_twist<S>(Ctx&, const Twist&, const PField&, const PField&, const CGState*); \
-  template int tsm::launch_norm<S>(Ctx&, const PField&, CGState*, int);
+#define TSM_INSTANTIATE_STORAGE(S)                                                                    \
+  template int tsm::launch_hop<S>(Ctx&, const HopArgs<S>&, int, int, int, int);                      \
+  template int tsm::launch_pack<S>(Ctx&, int, const double*, const PField&);                         \
+  template int tsm::launch_unpack<S>(Ctx&, int, const PField&, double*);                             \
+  template int tsm::launch_noise<S>(Ctx&, int, const NoiseSpec&, uint32_t, const PField&, int);      \
+  template int tsm::launch_twist<S>(Ctx&, const Twist&, const PField&, const PField&, const CGState*, \
+                                    const int*, int);                                                \
+  template int tsm::launch_norm<S>(Ctx&, const PField&, CGState*, int, const int*, int);
 
-#define TSM_INSTANTIATE_PAIR(S, SA)                                               \
-  template int tsm::launch_cg_update<S, SA>(Ctx&, const CGUpdArgs<S, SA>&);      \
-  template int tsm::launch_cg_p<S, SA>(Ctx&, const PField&, const PField&, CGState*);
+#define TSM_INSTANTIATE_PAIR(S, SA)                                                    \
+  template int tsm::launch_cg_update<S, SA>(Ctx&, const CGUpdArgs<S, SA>&, int);      \
+  template int tsm::launch_cg_p<S, SA>(Ctx&, const PField&, const PField&, CGState*, const int*, int);
 
 #define TSM_INSTANTIATE_CONVERT(Si, So) \
-  template int tsm::launch_convert<Si, So>(Ctx&, const PField&, const PField&);
+  template int tsm::launch_convert<Si, So>(Ctx&, const PField&, const PField&, const int*, int);

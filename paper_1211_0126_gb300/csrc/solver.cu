@@ -1,4 +1,5 @@
-// solver.cu -- CGNR on the even/odd Schur complement of D_tm.
+// solver.cu -- CGNR on the even/odd Schur complement of D_tm, for a batch of
+// independent right-hand sides.
 //
 // With A = 1 + 2 i kappa mu gamma_5 (site-local) the full system
 //   [[A_ee, -kappa H_eo], [-kappa H_oe, A_oo]] s = b
@@ -7,16 +8,23 @@
 //   bhat_e = A_ee^-1 (b_e + kappa H_eo A_oo^-1 b_o),   s_o = A_oo^-1 (b_o + kappa H_oe s_e),
 // and CG runs on Dhat^dag Dhat s_e = Dhat^dag bhat_e from a zero start, where
 //   Dhat^dag = 1 - kappa^2 (H^dag)_eo A_oo(-mu)^-1 (H^dag)_oe A_ee(-mu)^-1.
-// One iteration is five kernels:
+// One iteration is five kernels, each over all right-hand sides still iterating:
 //   K1  t = A^-1(mu) H_oe p
 //   K2  q = Dhat p = A^-1(mu) (A(mu) p - kappa^2 H_eo t);  <q, q>;  store w = A^-1(-mu) q
 //   K3  t = A^-1(-mu) (H^dag)_oe w
 //   K4  v = A(-mu) w - kappa^2 (H^dag)_eo t = Dhat^dag q;  r -= alpha v;  x += alpha p;  <r, r>
 //   K5  p = r + beta p
-// alpha, beta and the stopping rule are evaluated on the device by the last
-// block of K2 / K4; once the rule is met every queued kernel returns at once,
-// so the host only polls the state once per chunk of iterations.
+// alpha, beta and the stopping rule of every right-hand side are evaluated on
+// the device by the last block of K2 / K4 for that right-hand side; once its
+// rule is met every queued kernel skips it, so its iterates freeze exactly at
+// that iteration.  The host polls the states once per chunk of iterations and
+// leaves converged right-hand sides out of the following launches.  The
+// arithmetic of one right-hand side (including every reduction order) does not
+// depend on the others, so a batched solve gives the same bits as a
+// single-source one.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "fields.cuh"
 #include "solver.h"
@@ -29,25 +37,39 @@ int solution_prec(const tm_stop& stop) {
   return TSM_F32;
 }
 
-static int read_state(Ctx& c, int slot, CGState* out) {
-  TSM_CUDA(cudaMemcpyAsync(c.h_states + slot, c.states + slot, sizeof(CGState), cudaMemcpyDeviceToHost, c.stream));
+static int read_states(Ctx& c, int s0, int n, std::vector<CGState>& out) {
+  TSM_CUDA(cudaMemcpyAsync(c.h_states + s0, c.states + s0, n * sizeof(CGState), cudaMemcpyDeviceToHost, c.stream));
   TSM_CUDA(cudaStreamSynchronize(c.stream));
-  *out = c.h_states[slot];
+  out.assign(c.h_states + s0, c.h_states + s0 + n);
   return c.harvest_events();
 }
 
-// r = b - Dhat^dag Dhat x in FP64 (reliable update / true normal residual), <r,r> -> st->rr
-static int normal_residual_f64(Ctx& c, PField x, PField b, PField r, CGState* st) {
+// copy a host list of right-hand-side indices to device list `which` (0..2)
+static int upload_list(Ctx& c, int which, const std::vector<int>& list, const int** dev) {
+  int* h = c.h_lists + which * Ctx::kMaxStates;
+  for (size_t k = 0; k < list.size(); ++k) h[k] = list[k];
+  int* d = c.d_lists + which * Ctx::kMaxStates;
+  if (!list.empty())
+    TSM_CUDA(cudaMemcpyAsync(d, h, list.size() * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+  *dev = d;
+  return TSM_OK;
+}
+
+// r = b - Dhat^dag Dhat x in FP64 for the listed right-hand sides (reliable
+// update / true normal residual); <r, r> -> st[rhs].rr
+static int normal_residual_f64(Ctx& c, PField x, PField b, PField r, CGState* st, const int* list, int n) {
   const double k = c.lat.kappa, mu = c.lat.mu, k2 = k * k;
   PField t, w;
-  TSM_TRY(c.field("rel_t", TSM_F64, &t));
-  TSM_TRY(c.field("rel_w", TSM_F64, &w));
+  TSM_TRY(c.field("rel_t", TSM_F64, &t, c.batch_cap));
+  TSM_TRY(c.field("rel_w", TSM_F64, &w, c.batch_cap));
   HopArgs<F64> h = hop_args<F64>(c, 1);
+  h.active = list;
   h.in = x.as<F64>();
   h.out = t.as<F64>();
   h.to = twist_Ainv(k, mu);
-  TSM_TRY(launch_hop<F64>(c, h, 0, 0, -1));
+  TSM_TRY(launch_hop<F64>(c, h, 0, 0, -1, n));
   h = hop_args<F64>(c, 0);
+  h.active = list;
   h.in = t.as<F64>();
   h.center = x.as<F64>();
   h.tc = twist_A(k, mu);
@@ -56,13 +78,15 @@ static int normal_residual_f64(Ctx& c, PField x, PField b, PField r, CGState* st
   h.to = twist_Ainv(k, mu);
   h.ts = twist_Ainv(k, -mu);
   h.out = w.as<F64>();
-  TSM_TRY(launch_hop<F64>(c, h, 0, HOP_CENTER, -1));
+  TSM_TRY(launch_hop<F64>(c, h, 0, HOP_CENTER, -1, n));
   h = hop_args<F64>(c, 1);
+  h.active = list;
   h.in = w.as<F64>();
   h.out = t.as<F64>();
   h.to = twist_Ainv(k, -mu);
-  TSM_TRY(launch_hop<F64>(c, h, 1, 0, -1));
+  TSM_TRY(launch_hop<F64>(c, h, 1, 0, -1, n));
   h = hop_args<F64>(c, 0);
+  h.active = list;
   h.in = t.as<F64>();
   h.center = w.as<F64>();
   h.tc = twist_A(k, -mu);
@@ -73,25 +97,26 @@ static int normal_residual_f64(Ctx& c, PField x, PField b, PField r, CGState* st
   h.out = r.as<F64>();
   h.st = st;
   h.post = POST_SETRR;
-  return launch_hop<F64>(c, h, 1, HOP_CENTER | HOP_NORM | HOP_BASE, -1);
+  return launch_hop<F64>(c, h, 1, HOP_CENTER | HOP_NORM | HOP_BASE, -1, n);
 }
 
 // S: sloppy storage (links, p, t, w); SA: storage of r and x; SP: source /
 // solution storage (also used for bhat and the initial Dhat^dag bhat);
 // REL: FP32 iterations with an FP64 solution and FP64 residual replacement.
 template <class S, class SA, class SP, bool REL>
-static int cg_solve(Ctx& c, const tm_stop& stop, int slot, EOField b, EOField s, SolveResult* res) {
+static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EOField s, SolveResult* res) {
   const double k = c.lat.kappa, mu = c.lat.mu, k2 = k * k;
-  CGState* st = c.states + slot;
+  CGState* st = c.states + s0;
   const int pS = S::id, pA = SA::id, pP = SP::id;
+  const int nb = c.batch_cap;
   PField tmp_o, bhat, w0, t0, r0;
-  TSM_TRY(c.field("cg_tmp_o", pP, &tmp_o));
-  TSM_TRY(c.field("cg_bhat", pP, &bhat));
-  TSM_TRY(c.field("cg_w0", pP, &w0));
-  TSM_TRY(c.field("cg_t0", pP, &t0));
-  TSM_TRY(c.field("cg_r0", pP, &r0));
+  TSM_TRY(c.field("cg_tmp_o", pP, &tmp_o, nb));
+  TSM_TRY(c.field("cg_bhat", pP, &bhat, nb));
+  TSM_TRY(c.field("cg_w0", pP, &w0, nb));
+  TSM_TRY(c.field("cg_t0", pP, &t0, nb));
+  TSM_TRY(c.field("cg_r0", pP, &r0, nb));
   // bhat_e = A^-1 (b_e + kappa H_eo A^-1 b_o)
-  TSM_TRY(launch_twist<SP>(c, twist_Ainv(k, mu), b.o, tmp_o, nullptr));
+  TSM_TRY(launch_twist<SP>(c, twist_Ainv(k, mu), b.o, tmp_o, nullptr, nullptr, nrhs));
   {
     HopArgs<SP> h = hop_args<SP>(c, 0);
     h.in = tmp_o.as<SP>();
@@ -100,19 +125,19 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int slot, EOField b, EOField s,
     h.ah = k;
     h.to = twist_Ainv(k, mu);
     h.out = bhat.as<SP>();
-    TSM_TRY(launch_hop<SP>(c, h, 0, HOP_CENTER, -1));
+    TSM_TRY(launch_hop<SP>(c, h, 0, HOP_CENTER, -1, nrhs));
   }
-  // r0 = Dhat^dag bhat, <r0, r0> initialises the state
-  state_init_kernel<<<1, 1, 0, c.stream>>>(st, stop.rel_tol, stop.max_iter);
+  // r0 = Dhat^dag bhat, <r0, r0> initialises the states
+  state_init_kernel<<<1, Ctx::kMaxStates, 0, c.stream>>>(st, nrhs, stop.rel_tol, stop.max_iter);
   c.launches++;
   TSM_TRY(check_launch(c, "state_init_kernel"));
-  TSM_TRY(launch_twist<SP>(c, twist_Ainv(k, -mu), bhat, w0, nullptr));
+  TSM_TRY(launch_twist<SP>(c, twist_Ainv(k, -mu), bhat, w0, nullptr, nullptr, nrhs));
   {
     HopArgs<SP> h = hop_args<SP>(c, 1);
     h.in = w0.as<SP>();
     h.out = t0.as<SP>();
     h.to = twist_Ainv(k, -mu);
-    TSM_TRY(launch_hop<SP>(c, h, 1, 0, -1));
+    TSM_TRY(launch_hop<SP>(c, h, 1, 0, -1, nrhs));
     h = hop_args<SP>(c, 0);
     h.in = t0.as<SP>();
     h.center = w0.as<SP>();
@@ -122,46 +147,61 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int slot, EOField b, EOField s,
     h.out = r0.as<SP>();
     h.st = st;
     h.post = POST_INIT;
-    TSM_TRY(launch_hop<SP>(c, h, 1, HOP_CENTER | HOP_NORM, -1));
+    TSM_TRY(launch_hop<SP>(c, h, 1, HOP_CENTER | HOP_NORM, -1, nrhs));
   }
   PField p, t, w, r, x, x64, r64;
-  TSM_TRY(c.field("cg_p", pS, &p));
-  TSM_TRY(c.field("cg_t", pS, &t));
-  TSM_TRY(c.field("cg_w", pS, &w));
-  TSM_TRY(c.field("cg_r", pA, &r));
-  TSM_TRY(c.field("cg_x", pA, &x));
-  TSM_TRY((launch_convert<SP, SA>(c, r0, r)));
-  TSM_TRY((launch_convert<SP, S>(c, r0, p)));
-  TSM_TRY((launch_convert<SA, SA>(c, PField{}, x)));
+  TSM_TRY(c.field("cg_p", pS, &p, nb));
+  TSM_TRY(c.field("cg_t", pS, &t, nb));
+  TSM_TRY(c.field("cg_w", pS, &w, nb));
+  TSM_TRY(c.field("cg_r", pA, &r, nb));
+  TSM_TRY(c.field("cg_x", pA, &x, nb));
+  TSM_TRY((launch_convert<SP, SA>(c, r0, r, nullptr, nrhs)));
+  TSM_TRY((launch_convert<SP, S>(c, r0, p, nullptr, nrhs)));
+  TSM_TRY((launch_convert<SA, SA>(c, PField{}, x, nullptr, nrhs)));
   if constexpr (REL) {
-    TSM_TRY(c.field("cg_x64", TSM_F64, &x64));
-    TSM_TRY(c.field("cg_r64", TSM_F64, &r64));
-    TSM_TRY((launch_convert<F64, F64>(c, PField{}, x64)));
+    TSM_TRY(c.field("cg_x64", TSM_F64, &x64, nb));
+    TSM_TRY(c.field("cg_r64", TSM_F64, &r64, nb));
+    TSM_TRY((launch_convert<F64, F64>(c, PField{}, x64, nullptr, nrhs)));
   }
-  CGState hs{};
-  TSM_TRY(read_state(c, slot, &hs));
+  std::vector<CGState> hs;
+  TSM_TRY(read_states(c, s0, nrhs, hs));
   const double delta = (stop.reliable_delta > 0.0) ? stop.reliable_delta : 0.1;
-  double rr_ref = hs.rr0;
+  std::vector<double> rr_ref(nrhs);
+  for (int i = 0; i < nrhs; ++i) rr_ref[i] = hs[i].rr0;
+  auto iterating = [&](int i) { return !hs[i].done && hs[i].status == 0; };
   const int chunk = 8;
-  long long launched = 0;   // guards the host loop against a state that stops advancing
-  while (!hs.done && hs.status == 0) {
+  long long launched = 0;   // guards the host loop against states that stop advancing
+  for (;;) {
+    std::vector<int> act;
+    int min_left = stop.max_iter;
+    for (int i = 0; i < nrhs; ++i)
+      if (iterating(i)) {
+        act.push_back(i);
+        min_left = std::min(min_left, stop.max_iter - hs[i].iter);
+      }
+    if (act.empty()) break;
     if (launched > (long long)stop.max_iter + 64) {
       set_error("solver state stopped advancing after %lld iterations", launched);
       return TSM_ERR_CUDA;
     }
+    const int n = (int)act.size();
+    const int* dact = nullptr;
+    TSM_TRY(upload_list(c, 0, act, &dact));
     int m = chunk;
-    if (stop.max_iter - hs.iter < m) m = stop.max_iter - hs.iter;
+    if (min_left < m) m = min_left;
     if (m < 1) m = 1;
     launched += m;
     for (int it = 0; it < m; ++it) {
       c.prof_this_launch = c.profile && it == 0;
       HopArgs<S> h = hop_args<S>(c, 1);   // K1
+      h.active = dact;
       h.in = p.as<S>();
       h.out = t.as<S>();
       h.to = twist_Ainv(k, mu);
       h.skip = st;
-      TSM_TRY(launch_hop<S>(c, h, 0, 0, PK_HOP));
+      TSM_TRY(launch_hop<S>(c, h, 0, 0, PK_HOP, n));
       h = hop_args<S>(c, 0);              // K2
+      h.active = dact;
       h.in = t.as<S>();
       h.center = p.as<S>();
       h.tc = twist_A(k, mu);
@@ -173,13 +213,14 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int slot, EOField b, EOField s,
       h.skip = st;
       h.st = st;
       h.post = POST_ALPHA;
-      TSM_TRY(launch_hop<S>(c, h, 0, HOP_CENTER | HOP_NORM, PK_HOP_XPAY));
+      TSM_TRY(launch_hop<S>(c, h, 0, HOP_CENTER | HOP_NORM, PK_HOP_XPAY, n));
       h = hop_args<S>(c, 1);              // K3
+      h.active = dact;
       h.in = w.as<S>();
       h.out = t.as<S>();
       h.to = twist_Ainv(k, -mu);
       h.skip = st;
-      TSM_TRY(launch_hop<S>(c, h, 1, 0, PK_HOP_DAG));
+      TSM_TRY(launch_hop<S>(c, h, 1, 0, PK_HOP_DAG, n));
       CGUpdArgs<S, SA> u{};               // K4
       u.g = c.g;
       u.Ue = c.links_of<S>(0);
@@ -193,43 +234,58 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int slot, EOField b, EOField s,
       u.sstride = c.sstride;
       u.kappa2 = k2;
       u.tw = twist_A(k, -mu);
+      u.active = dact;
       u.st = st;
       u.red = c.red;
-      TSM_TRY((launch_cg_update<S, SA>(c, u)));
+      TSM_TRY((launch_cg_update<S, SA>(c, u, n)));
       c.prof_this_launch = false;
-      TSM_TRY((launch_cg_p<S, SA>(c, r, p, st)));   // K5
+      TSM_TRY((launch_cg_p<S, SA>(c, r, p, st, dact, n)));   // K5
     }
     c.prof_this_launch = false;
-    TSM_TRY(read_state(c, slot, &hs));
-    if (hs.status != 0) break;
+    TSM_TRY(read_states(c, s0, nrhs, hs));
     if constexpr (REL) {
-      if (hs.done || hs.rr < delta * delta * rr_ref) {
-        // reliable update: fold the FP32 increment into the FP64 solution and
-        // replace the iterated residual by the true FP64 normal residual
-        const int nb = (c.g.Vh + SITE_NT - 1) / SITE_NT;
-        accumulate_solution_kernel<<<nb, SITE_NT, 0, c.stream>>>(c.g.Vh, x.as<F32>(), x64.as<F64>(), c.sstride);
+      // reliable update of every right-hand side that just met its rule or whose
+      // residual fell by delta: fold the FP32 increment into the FP64 solution
+      // and replace the iterated residual by the true FP64 normal residual
+      std::vector<int> rel;
+      for (int i : act)
+        if (hs[i].status == 0 && (hs[i].done || hs[i].rr < delta * delta * rr_ref[i])) rel.push_back(i);
+      if (!rel.empty()) {
+        const int nr = (int)rel.size();
+        const int* drel = nullptr;
+        TSM_TRY(upload_list(c, 1, rel, &drel));
+        const int blocks = (c.g.Vh + SITE_NT - 1) / SITE_NT;
+        accumulate_solution_kernel<<<dim3(nr, blocks), SITE_NT, 0, c.stream>>>(c.g.Vh, x.as<F32>(), x64.as<F64>(),
+                                                                              c.sstride, drel);
         c.launches++;
         TSM_TRY(check_launch(c, "accumulate_solution_kernel"));
-        TSM_TRY(normal_residual_f64(c, x64, r0, r64, st));
-        TSM_TRY((launch_convert<F64, F32>(c, r64, r)));
-        TSM_TRY(read_state(c, slot, &hs));
-        rr_ref = hs.rr;
-        if (hs.done) {
-          const bool met = !(std::sqrt(hs.rr) >= stop.rel_tol * std::sqrt(hs.rr0));
-          if (met || hs.iter >= stop.max_iter || hs.status != 0) break;
-          state_resume_kernel<<<1, 1, 0, c.stream>>>(st);
+        TSM_TRY(normal_residual_f64(c, x64, r0, r64, st, drel, nr));
+        TSM_TRY((launch_convert<F64, F32>(c, r64, r, drel, nr)));
+        TSM_TRY(read_states(c, s0, nrhs, hs));
+        std::vector<int> resume;
+        for (int i : rel) {
+          rr_ref[i] = hs[i].rr;
+          if (hs[i].done && hs[i].status == 0) {
+            const bool met = !(std::sqrt(hs[i].rr) >= stop.rel_tol * std::sqrt(hs[i].rr0));
+            if (!met && hs[i].iter < stop.max_iter) resume.push_back(i);
+          }
+        }
+        if (!resume.empty()) {
+          const int* dres = nullptr;
+          TSM_TRY(upload_list(c, 2, resume, &dres));
+          state_resume_kernel<<<1, Ctx::kMaxStates, 0, c.stream>>>(st, dres, (int)resume.size());
           c.launches++;
           TSM_TRY(check_launch(c, "state_resume_kernel"));
-          TSM_TRY(read_state(c, slot, &hs));
+          TSM_TRY(read_states(c, s0, nrhs, hs));
         }
       }
     }
   }
   // solution: even part from CG, odd part reconstructed
   if constexpr (REL) {
-    TSM_TRY((launch_convert<F64, SP>(c, x64, s.e)));
+    TSM_TRY((launch_convert<F64, SP>(c, x64, s.e, nullptr, nrhs)));
   } else {
-    TSM_TRY((launch_convert<SA, SP>(c, x, s.e)));
+    TSM_TRY((launch_convert<SA, SP>(c, x, s.e, nullptr, nrhs)));
   }
   {
     HopArgs<SP> h = hop_args<SP>(c, 1);
@@ -239,26 +295,33 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int slot, EOField b, EOField s,
     h.ah = k;
     h.to = twist_Ainv(k, mu);
     h.out = s.o.as<SP>();
-    TSM_TRY(launch_hop<SP>(c, h, 0, HOP_CENTER, -1));
+    TSM_TRY(launch_hop<SP>(c, h, 0, HOP_CENTER, -1, nrhs));
   }
-  res->iters = hs.iter;
-  res->status = hs.status == 0 ? TSM_OK : TSM_ERR_NONFINITE;
-  res->rel_res = hs.rr0 > 0 ? std::sqrt(hs.rr / hs.rr0) : 0.0;
-  if (hs.rr0 == 0.0) res->converged = 1;
-  else if (stop.rel_tol <= 0.0) res->converged = hs.iter >= stop.max_iter;
-  else res->converged = !(std::sqrt(hs.rr) >= stop.rel_tol * std::sqrt(hs.rr0));
+  for (int i = 0; i < nrhs; ++i) {
+    const CGState& q = hs[i];
+    SolveResult& o = res[i];
+    o.iters = q.iter;
+    o.status = q.status == 0 ? TSM_OK : TSM_ERR_NONFINITE;
+    o.rel_res = q.rr0 > 0 ? std::sqrt(q.rr / q.rr0) : 0.0;
+    if (q.rr0 == 0.0) o.converged = 1;
+    else if (stop.rel_tol <= 0.0) o.converged = q.iter >= stop.max_iter;
+    else o.converged = !(std::sqrt(q.rr) >= stop.rel_tol * std::sqrt(q.rr0));
+  }
   return TSM_OK;
 }
 
-int solve_source(Ctx& c, const tm_stop& stop, int slot, EOField b, EOField s, SolveResult* res) {
-  if (slot < 0 || slot >= Ctx::kMaxStates - 4) return TSM_ERR_ARG;
+int solve_batch(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EOField s, SolveResult* res) {
+  if (nrhs < 1 || nrhs > c.batch_cap || s0 < 0 || s0 + nrhs > Ctx::kMaxStates - 4) {
+    set_error("batch of %d right-hand sides at state %d exceeds the capacity (%d)", nrhs, s0, c.batch_cap);
+    return TSM_ERR_TOO_LARGE;
+  }
   switch (stop.prec) {
-    case TSM_F64: return cg_solve<F64, F64, F64, false>(c, stop, slot, b, s, res);
+    case TSM_F64: return cg_solve<F64, F64, F64, false>(c, stop, s0, nrhs, b, s, res);
     case TSM_F32:
-      if (stop.reliable) return cg_solve<F32, F32, F64, true>(c, stop, slot, b, s, res);
-      return cg_solve<F32, F32, F32, false>(c, stop, slot, b, s, res);
-    case TSM_F16: return cg_solve<F16, F32, F32, false>(c, stop, slot, b, s, res);
-    case TSM_BF16: return cg_solve<BF16, F32, F32, false>(c, stop, slot, b, s, res);
+      if (stop.reliable) return cg_solve<F32, F32, F64, true>(c, stop, s0, nrhs, b, s, res);
+      return cg_solve<F32, F32, F32, false>(c, stop, s0, nrhs, b, s, res);
+    case TSM_F16: return cg_solve<F16, F32, F32, false>(c, stop, s0, nrhs, b, s, res);
+    case TSM_BF16: return cg_solve<BF16, F32, F32, false>(c, stop, s0, nrhs, b, s, res);
     default: set_error("unknown solver tier %d", stop.prec); return TSM_ERR_ARG;
   }
 }

@@ -16,9 +16,11 @@ struct SolveResult {
 // tier and for FP32 with FP64 reliable updates, FP32 otherwise.
 int solution_prec(const tm_stop& stop);
 
-// Solve D_tm s = b for one source.  b and s are even/odd fields of tier
-// solution_prec(stop); `slot` selects the device solver state.
-int solve_source(Ctx& c, const tm_stop& stop, int slot, EOField b, EOField s, SolveResult* res);
+// Solve D_tm s_r = b_r for nrhs independent sources at once.  b and s are
+// batches of nrhs contiguous even/odd fields of tier solution_prec(stop) laid
+// out for c.batch_cap sources; device solver states s0 .. s0+nrhs-1 are used;
+// res receives nrhs results.
+int solve_batch(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EOField s, SolveResult* res);
 
 // ||b - D_tm s|| / ||b|| in FP64 (fields of tier prec).
 int true_residual(Ctx& c, int prec, EOField b, EOField s, double* out);
@@ -40,6 +42,9 @@ HopArgs<S> hop_args(const Ctx& c, int p_out) {
   a.ts = twist_one();
   a.red = c.red;
   a.post = POST_NONE;
+  a.active = nullptr;
+  a.skip = nullptr;
+  a.st = nullptr;
   return a;
 }
 

@@ -272,9 +272,9 @@ def tsm_profile(h, enable):
 
 
 def tsm_profile_read(h):
-    ms = np.zeros(4)
-    cnt = np.zeros(4, dtype=np.int64)
-    by = np.zeros(4)
+    ms = np.zeros(16)
+    cnt = np.zeros(16, dtype=np.int64)
+    by = np.zeros(16)
     _check(library().tsm_profile_read(h, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(cnt.ctypes.data),
                                       ctypes.c_void_p(by.ctypes.data)), "tsm_profile_read")
     return ms, cnt, by

@@ -97,3 +97,23 @@ def test_production_lattice_solve(ctx):
     true_res = np.linalg.norm(r) / np.linalg.norm(b)
     assert abs(true_res - tres[0]) < 1e-6 * max(true_res, 1e-3)
     assert 0 < iters[0] <= 60 and true_res < 1.0
+
+
+@pytest.mark.parametrize("prec,reliable", [(tsm.TSM_F64, False), (tsm.TSM_F32, True), (tsm.TSM_F16, False),
+                                           (tsm.TSM_BF16, False), (tsm.TSM_F32, False)])
+def test_batched_solve_bit_identical_to_single(ctx, prec, reliable):
+    """Multi-RHS kernels (one launch over every right-hand side still iterating,
+    converged ones dropped) give exactly the single-source results."""
+    dims = (6, 4, 4, 6)
+    U = S.gauge_field(dims, 0.3, 91)
+    ctx.load_gauge(U, dims, KAPPA, MU)
+    b = S.random_spinor(dims, 92, batch=(5,))
+    b[2] *= 1e-3                     # different scales -> different iteration counts
+    b[3] = 0.0                       # converged before the first iteration
+    stp = tsm.stop(1e-9 if prec in (tsm.TSM_F64,) or reliable else 5e-3, 400, prec, reliable=reliable)
+    s_b, it_b, tr_b, _ = ctx.solve(b, stp)
+    for r in range(5):
+        s_1, it_1, tr_1, _ = ctx.solve(b[r], stp)
+        assert it_b[r] == it_1[0]
+        assert np.array_equal(s_b[r], s_1), r
+    assert it_b[3] == 0

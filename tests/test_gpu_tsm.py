@@ -96,3 +96,17 @@ def test_mixed_precision_tsm_unbiased(ctx, field, tiers):
     z = np.abs(got["loops"] - ref["loops"]) / np.sqrt(got["err"] ** 2 + ref["err"] ** 2 + 1e-300)
     assert np.median(z) < 1.0 and z.max() < 5.0
     assert np.isfinite(hp_got).all()
+
+
+@pytest.mark.parametrize("batch", [3, 8])
+def test_batched_tsm_bit_identical(ctx, field, batch):
+    """tsm_loops with multi-RHS batches equals the single-source run bit for bit
+    (the LP map does not depend on which sources share a batch)."""
+    ctx.load_gauge(field, DIMS, KAPPA, MU)
+    hp = tsm.stop(1e-10, 5000, tsm.TSM_F32, reliable=True)
+    lp = tsm.stop(5e-3, 60, tsm.TSM_F16)
+    one = ctx.loops(31, 4, 4, 13, hp, lp, GAM, MOMS, per_source=True, batch=1)
+    many = ctx.loops(31, 4, 4, 13, hp, lp, GAM, MOMS, per_source=True, batch=batch)
+    for k in ("loops", "err", "per_corr", "per_lp"):
+        assert np.array_equal(one[k], many[k]), k
+    assert one["stats"]["lp_iters"] == many["stats"]["lp_iters"]
