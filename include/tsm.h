@@ -221,6 +221,33 @@ int tsm_profile(tsm_ctx* ctx, int enable);
 int tsm_profile_read(tsm_ctx* ctx, double ms[16], long long count[16], double bytes[16]);
 long long tsm_launch_count(tsm_ctx* ctx);
 
+/* Contraction for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc where they need a contraction -- code running under
+ * a memory manager that owns the whole device, paths where cudaMalloc's
+ * implicit synchronisation and latency are not acceptable, or callers that
+ * hold no tsm_ctx.  It computes the same loops as tsm_contract with TSM_F64
+ * and s_b = NULL, allocates nothing, and needs no context:
+ *   s_dev    device pointer, canonical spinor (24 * V doubles) of one source
+ *   out_dev  device pointer, [n_gamma][n_q][T] complex (written)
+ *   gammas, moms  host arrays as for tsm_contract; 1 <= n_gamma <= 16,
+ *            1 <= n_q <= 16, Lx + Ly + Lz <= 3072
+ *   cuda_stream   cudaStream_t the work is ordered on (NULL = legacy stream);
+ *            the call returns once the work is queued, and runs on the
+ *            current CUDA device.
+ * Scratch: a fixed 1 MiB device array compiled into the library (one per
+ * device, held until the library is unloaded) stores the phase tables and the
+ * block partial sums; requests that need more return TSM_ERR_TOO_LARGE.  The
+ * first call on a device looks up that array's device address (once per
+ * device) -- make that first call before any stream capture.  Every call
+ * shares the array: calls whose work overlaps on the GPU race and must be
+ * serialised by the caller.  Nothing in the array needs clearing: each call
+ * writes every entry it reads. */
+int tsm_contract_noalloc(const tm_lattice* lat, uint64_t seed, int kind, uint32_t source,
+                         const double* s_dev, const int* gammas, int n_gamma, const int* moms, int n_q,
+                         double* out_dev, void* cuda_stream);
+
 /* One-line message for the last failed call on this thread ("" if none). */
 const char* tsm_last_error(void);
 /* Name of a status code. */

@@ -70,6 +70,8 @@ _SIGS = {
                                  ctypes.POINTER(TsmLoopStats)]),
     "tsm_combine": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
                                    ctypes.c_int]),
+    "tsm_contract_noalloc": (ctypes.c_int, [ctypes.POINTER(TmLattice), ctypes.c_uint64, ctypes.c_int,
+                                            ctypes.c_uint32, _P, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
     "tsm_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "tsm_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
     "tsm_launch_count": (ctypes.c_longlong, [_P]),
@@ -227,6 +229,21 @@ def tsm_contract(h, prec, seed, kind, source, s_a, s_b, gammas, moms, out):
     return _check(library().tsm_contract(h, int(prec), ctypes.c_uint64(seed), int(kind), ctypes.c_uint32(source),
                                          pa, pb, gp, len(g), mp, len(m) // 3, po, _same_side(da, db, do)),
                   "tsm_contract")
+
+
+def tsm_contract_noalloc(lat, seed, kind, source, s_dev, gammas, moms, out_dev, stream=None):
+    """Contraction that allocates nothing (for callers that cannot allocate
+    device memory); s_dev and out_dev are torch CUDA tensors (complex128).
+    Queued on `stream` (cudaStream_t as int, None = legacy stream)."""
+    g, gp = _int_array(gammas, "gammas")
+    m, mp = _int_array(moms, "moms")
+    ps, ds = _ptr(s_dev)
+    po, do = _ptr(out_dev, True)
+    if ds != 1 or do != 1:
+        raise ValueError("tsm_contract_noalloc takes device tensors")
+    return _check(library().tsm_contract_noalloc(ctypes.byref(lat), ctypes.c_uint64(seed), int(kind),
+                                                 ctypes.c_uint32(source), ps, gp, len(g), mp, len(m) // 3, po,
+                                                 ctypes.c_void_p(stream or 0)), "tsm_contract_noalloc")
 
 
 def params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batch=1):
