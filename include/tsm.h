@@ -182,6 +182,8 @@ typedef struct {
   int batch;                /* sources solved together (>= 1; 1 = single-RHS kernels) */
   const int* gammas; int n_gamma;
   const int* moms; int n_q; /* host pointers */
+  int verify;               /* 1: recompute every HP solution's true residual in FP64
+                               (tsm_loop_stats.hp_max_true_res; 2 extra FP64 hops per HP source) */
 } tsm_params;
 
 /* Run the TSM over this call's source ranges.  Outputs (host or device per

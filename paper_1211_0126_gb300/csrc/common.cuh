@@ -66,13 +66,17 @@ __device__ __forceinline__ int half_index(const Geom& g, int x, int y, int z, in
 // ---------------------------------------------------------------- storage
 // A spinor field of one parity is SN "chunks" of Vh elements each (chunk c of
 // site i at base[c * stride + i]), so that every load of a warp is coalesced.
-// A link field of one parity is 4 directions x LN chunks; only rows 0 and 1 of
-// each SU(3) link are stored (12 reals), row 2 = conj(row0 x row1).
+// A link field of one parity is 4 directions x LN chunks.  FP32 and 16-bit
+// links store rows 0 and 1 only (12 reals), row 2 = conj(row0 x row1) is
+// rebuilt in registers; FP64 links store all 18 reals (on GB300 the FP64 pipe,
+// not memory, bounds the FP64 stencil, so the rebuild would cost more than the
+// extra bytes).
 struct F64 {
   using real = double;
   using schunk = double2;   // 1 complex
   using lchunk = double2;
-  static constexpr int SN = 12, LN = 6;
+  static constexpr int SN = 12, LN = 9;
+  static constexpr bool full_links = true;
   static constexpr int id = 0;
 };
 struct F32 {
@@ -80,6 +84,7 @@ struct F32 {
   using schunk = float4;    // 2 complex
   using lchunk = float4;
   static constexpr int SN = 6, LN = 3;
+  static constexpr bool full_links = false;
   static constexpr int id = 1;
 };
 struct BF16 {
@@ -87,6 +92,7 @@ struct BF16 {
   using schunk = uint4;     // 4 complex as 8 bf16
   using lchunk = uint2;     // 2 complex as 4 bf16
   static constexpr int SN = 3, LN = 3;
+  static constexpr bool full_links = false;
   static constexpr int id = 2;
 };
 struct F16 {
@@ -94,6 +100,7 @@ struct F16 {
   using schunk = uint4;     // 4 complex as 8 fp16
   using lchunk = uint2;     // 2 complex as 4 fp16
   static constexpr int SN = 3, LN = 3;
+  static constexpr bool full_links = false;
   static constexpr int id = 3;
 };
 
@@ -173,14 +180,15 @@ __device__ __forceinline__ void store_spinor(typename S::schunk* __restrict__ b,
   }
 }
 
-// rows 0 and 1 of link (dir, site i): r[0..2] = row 0, r[3..5] = row 1
+// rows of link (dir, site i): r[0..2] = row 0, r[3..5] = row 1 (and r[6..8] =
+// row 2 for full-link storage)
 template <class S>
 __device__ __forceinline__ void load_link(const typename S::lchunk* __restrict__ b, int stride, int dir, int i,
-                                          cx<typename S::real> r[6]) {
+                                          cx<typename S::real> r[9]) {
   const typename S::lchunk* p = b + dir * S::LN * stride + i;
   if constexpr (S::id == 0) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
+    for (int c = 0; c < 9; ++c) {
       double2 d = p[c * stride];
       r[c] = {d.x, d.y};
     }
@@ -203,11 +211,11 @@ __device__ __forceinline__ void load_link(const typename S::lchunk* __restrict__
 
 template <class S>
 __device__ __forceinline__ void store_link(typename S::lchunk* __restrict__ b, int stride, int dir, int i,
-                                           const cx<typename S::real> r[6]) {
+                                           const cx<typename S::real> r[9]) {
   typename S::lchunk* p = b + dir * S::LN * stride + i;
   if constexpr (S::id == 0) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) p[c * stride] = make_double2(r[c].re, r[c].im);
+    for (int c = 0; c < 9; ++c) p[c * stride] = make_double2(r[c].re, r[c].im);
   } else if constexpr (S::id == 1) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) p[c * stride] = make_float4(r[2 * c].re, r[2 * c].im, r[2 * c + 1].re, r[2 * c + 1].im);
@@ -299,18 +307,28 @@ struct CGState {
   double alpha, beta;
   double tol;       // rel_tol
   double aux;       // scratch result (norms of helper reductions)
+  double rr_ref;    // <r, r> at the last reliable update
+  double delta2;    // reliable update when rr < delta2 * rr_ref
   int iter, max_iter;
   int done;         // 1: stopping rule met (or cap reached / error)
   int status;       // 0 ok, TSM_ERR_NONFINITE on NaN/Inf
+  int rel;          // 1: FP64 reliable updates (FP32 iterations)
+  int need_rel;     // 1: a reliable update is due before the next iteration
+  int final_check;  // 1: the iterated residual met the rule; the update decides
 };
 
 enum PostOp {
   POST_NONE = 0,    // write the sum to st->aux
-  POST_INIT = 1,    // rr = rr0 = sum, iter = 0, done per stopping rule
+  POST_INIT = 1,    // rr = rr0 = rr_ref = sum, iter = 0, done per stopping rule
   POST_ALPHA = 2,   // pAp = sum, alpha = rr / pAp
   POST_RR = 3,      // rr' = sum: beta = rr'/rr, rr = rr', iter++, stopping rule
-  POST_SETRR = 4    // rr = sum (after a reliable update)
+  POST_SETRR = 4    // rr = rr_ref = sum (true residual of a reliable update)
 };
+
+// stopping rule of the iterated residual: ||r|| < tol ||r0|| (NaN counts as met)
+__device__ __forceinline__ bool rule_met(const CGState* st, double rr) {
+  return !(sqrt(rr) >= st->tol * sqrt(st->rr0));
+}
 
 __device__ __forceinline__ void post_action(CGState* st, int op, double sum) {
   if (st == nullptr) return;
@@ -322,7 +340,10 @@ __device__ __forceinline__ void post_action(CGState* st, int op, double sum) {
     case POST_INIT:
       st->rr = sum;
       st->rr0 = sum;
+      st->rr_ref = sum;
       st->iter = 0;
+      st->need_rel = 0;
+      st->final_check = 0;
       st->status = finite ? 0 : -5;
       st->done = (!finite || sum == 0.0 || st->max_iter <= 0 || !(sqrt(sum) >= st->tol * sqrt(sum))) ? 1 : 0;
       break;
@@ -341,13 +362,22 @@ __device__ __forceinline__ void post_action(CGState* st, int op, double sum) {
       if (!finite) {
         st->status = -5;
         st->done = 1;
-      } else if (st->iter >= st->max_iter || !(sqrt(sum) >= st->tol * sqrt(st->rr0))) {
-        st->done = 1;
+      } else if (st->iter >= st->max_iter || rule_met(st, sum)) {
+        // with reliable updates the FP64 residual of the update decides
+        if (st->rel) {
+          st->need_rel = 1;
+          st->final_check = 1;
+        } else {
+          st->done = 1;
+        }
+      } else if (st->rel && sum < st->delta2 * st->rr_ref) {
+        st->need_rel = 1;
       }
       break;
     }
     case POST_SETRR:
       st->rr = sum;
+      st->rr_ref = sum;
       if (!finite) {
         st->status = -5;
         st->done = 1;

@@ -35,7 +35,7 @@ double spinor_site_bytes(int prec) {
 
 double link_site_bytes(int prec) {
   switch (prec) {
-    case TSM_F64: return 8.0 * 12 * 8;
+    case TSM_F64: return 8.0 * 18 * 8;   // FP64 links keep all three rows
     case TSM_F32: return 8.0 * 12 * 4;
     default: return 8.0 * 12 * 2;
   }

@@ -64,11 +64,11 @@ __device__ __forceinline__ void accumulate(cx<R> acc[12], const cx<R> u[6]) {
   }
 }
 
-// u = U h (dag = false) or U^dag h (dag = true) on both spin components of h
+// u = U h (dag = false) or U^dag h (dag = true) on both spin components of h;
+// r holds the three rows of U (r[6..8] = row 2)
 template <bool DAGU, class R>
-__device__ __forceinline__ void su3_mul(const cx<R> r[6], const cx<R> h[6], cx<R> u[6]) {
-  cx<R> w[3];
-  third_row(r, w);
+__device__ __forceinline__ void su3_mul(const cx<R> r[9], const cx<R> h[6], cx<R> u[6]) {
+  const cx<R>* w = r + 6;
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const cx<R> a = h[3 * s], b = h[3 * s + 1], c = h[3 * s + 2];
@@ -95,7 +95,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, int ih, const int c[4],
   using R = typename S::real;
   constexpr int SF = DAG ? +1 : -1;   // forward hop: (1 + SF gamma_mu)
   constexpr int SB = -SF;             // backward hop
-  cx<R> v[12], h[6], u[6], r[6];
+  cx<R> v[12], h[6], u[6], r[9];
   // forward neighbour x + mu
   {
     int x = c[0], y = c[1], z = c[2], t = c[3];
@@ -113,6 +113,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, int ih, const int c[4],
       }
     }
     load_link<S>(Uout, lstride, MU, ih, r);
+    if constexpr (!S::full_links) third_row(r, r + 6);
     su3_mul<false>(r, h, u);
     accumulate<MU, SF>(acc, u);
   }
@@ -133,6 +134,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, int ih, const int c[4],
       }
     }
     load_link<S>(Uin, lstride, MU, nb, r);
+    if constexpr (!S::full_links) third_row(r, r + 6);
     su3_mul<true>(r, h, u);
     accumulate<MU, SB>(acc, u);
   }
@@ -178,6 +180,7 @@ struct HopArgs {
   Twist tc, to, ts;
   const int* active;                       // optional list of right-hand sides
   const CGState* skip;                     // optional: a RHS returns at once when skip[rhs].done
+  int skip_rel;                            // 1: instead, return unless skip[rhs].need_rel
   CGState* st;                             // states receiving the HOP_NORM post action
   RedSlot red;                             // HOP_NORM
   int post;                                // PostOp for HOP_NORM
@@ -189,7 +192,7 @@ template <class S, int DAG, int MODE>
 __global__ void __launch_bounds__(HOP_NT) hop_kernel(const HopArgs<S> a) {
   using R = typename S::real;
   const int rhs = rhs_slot(a.active);
-  if (a.skip != nullptr && a.skip[rhs].done) return;
+  if (a.skip != nullptr && (a.skip_rel ? !a.skip[rhs].need_rel : a.skip[rhs].done)) return;
   const size_t off = rhs_offset<S>(rhs, a.sstride);
   const int ih = blockIdx.y * HOP_NT + threadIdx.x;
   double part = 0.0;

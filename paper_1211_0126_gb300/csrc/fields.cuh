@@ -49,8 +49,8 @@ __global__ void __launch_bounds__(SITE_NT) unpack_spinor_kernel(Geom g, int pari
   for (int k = 0; k < 12; ++k) canon[(size_t)lex * 12 + k] = make_double2((double)v[k].re, (double)v[k].im);
 }
 
-// canonical links [lex][mu][3][3] complex -> two-row parity fields in every
-// precision; records max deviation from SU(3) (as float bits, atomicMax).
+// canonical links [lex][mu][3][3] complex -> parity fields in every precision
+// (FP64: 3 rows, others: 2 rows); records the max deviation from SU(3).
 static __global__ void __launch_bounds__(SITE_NT) pack_links_kernel(Geom g, const double2* __restrict__ U,
                                                              double2* __restrict__ l64, float4* __restrict__ l32,
                                                              uint2* __restrict__ l16, uint2* __restrict__ lbf,
@@ -68,9 +68,9 @@ static __global__ void __launch_bounds__(SITE_NT) pack_links_kernel(Geom g, cons
   const int parity = (x + y + z + t) & 1;
   const int ih = lex >> 1;
   const double2* m = U + ((size_t)lex * 4 + mu) * 9;
-  cx<double> r[6], w[3];
+  cx<double> r[9], w[3];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) r[k] = {m[k].x, m[k].y};
+  for (int k = 0; k < 9; ++k) r[k] = {m[k].x, m[k].y};
   third_row(r, w);
   // SU(3) check: unit rows, orthogonal rows, stored row 2 equals the reconstruction
   double dev = fabs(norm2(r[0]) + norm2(r[1]) + norm2(r[2]) - 1.0);
@@ -86,10 +86,10 @@ static __global__ void __launch_bounds__(SITE_NT) pack_links_kernel(Geom g, cons
   atomicMax(maxdev, __float_as_uint((float)dev));
   const size_t off64 = (size_t)parity * 4 * F64::LN * lstride;
   const size_t off32 = (size_t)parity * 4 * F32::LN * lstride;
-  store_link<F64>(l64 + off64, lstride, mu, ih, r);
-  cx<float> rf[6];
+  store_link<F64>(l64 + off64, lstride, mu, ih, r);   // all three rows
+  cx<float> rf[9];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) rf[k] = {(float)r[k].re, (float)r[k].im};
+  for (int k = 0; k < 9; ++k) rf[k] = {(float)r[k].re, (float)r[k].im};
   store_link<F32>(l32 + off32, lstride, mu, ih, rf);
   store_link<F16>(l16 + off32, lstride, mu, ih, rf);
   store_link<BF16>(lbf + off32, lstride, mu, ih, rf);
@@ -161,11 +161,13 @@ __global__ void __launch_bounds__(SITE_NT) convert_kernel(int Vh, const typename
   store_spinor<So>(out + rhs_offset<So>(rhs, sstride), sstride, ih, w);
 }
 
-// reliable update, step 1: x64 += y (y in F32), y = 0
+// reliable update, step 1: x64 += y (y in F32), y = 0 -- only for right-hand
+// sides with a pending update (st[rhs].need_rel)
 static __global__ void __launch_bounds__(SITE_NT) accumulate_solution_kernel(int Vh, float4* __restrict__ y,
                                                                              double2* __restrict__ x, int sstride,
-                                                                             const int* active) {
+                                                                             const int* active, const CGState* st) {
   const int rhs = rhs_slot(active);
+  if (!st[rhs].need_rel) return;
   const int ih = blockIdx.y * SITE_NT + threadIdx.x;
   if (ih >= Vh) return;
   y += rhs_offset<F32>(rhs, sstride);
@@ -181,6 +183,38 @@ static __global__ void __launch_bounds__(SITE_NT) accumulate_solution_kernel(int
   }
   store_spinor<F64>(x, sstride, ih, xv);
   store_spinor<F32>(y, sstride, ih, yv);
+}
+
+// reliable update, last step: iterated residual r (F32) = true residual r64
+// (F64), only for right-hand sides with a pending update
+static __global__ void __launch_bounds__(SITE_NT) replace_residual_kernel(int Vh, const double2* __restrict__ r64,
+                                                                          float4* __restrict__ r, int sstride,
+                                                                          const int* active, const CGState* st) {
+  const int rhs = rhs_slot(active);
+  if (!st[rhs].need_rel) return;
+  const int ih = blockIdx.y * SITE_NT + threadIdx.x;
+  if (ih >= Vh) return;
+  cx<double> v[12];
+  cx<float> w[12];
+  load_spinor<F64>(r64 + rhs_offset<F64>(rhs, sstride), sstride, ih, v);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) w[k] = {(float)v[k].re, (float)v[k].im};
+  store_spinor<F32>(r + rhs_offset<F32>(rhs, sstride), sstride, ih, w);
+}
+
+// closes the reliable updates of one iteration: clears need_rel and, where the
+// iterated residual had met the stopping rule, lets the true FP64 residual
+// decide between stopping and iterating on
+static __global__ void rel_finish_kernel(CGState* st, const int* active, int n) {
+  const int k = threadIdx.x + blockIdx.x * blockDim.x;
+  if (k >= n) return;
+  CGState& s = st[active != nullptr ? active[k] : k];
+  if (!s.need_rel) return;
+  s.need_rel = 0;
+  if (s.final_check) {
+    s.final_check = 0;
+    if (s.status != 0 || s.iter >= s.max_iter || rule_met(&s, s.rr)) s.done = 1;
+  }
 }
 
 // <v, v> per right-hand side with post action (deterministic two-stage sum)
@@ -203,7 +237,7 @@ __global__ void __launch_bounds__(SITE_NT) norm_kernel(int Vh, const typename S:
 }
 
 // states 0 .. n-1: fresh solve
-static __global__ void state_init_kernel(CGState* st, int n, double tol, int max_iter) {
+static __global__ void state_init_kernel(CGState* st, int n, double tol, int max_iter, int rel, double delta2) {
   const int k = threadIdx.x + blockIdx.x * blockDim.x;
   if (k >= n) return;
   CGState& s = st[k];
@@ -212,16 +246,11 @@ static __global__ void state_init_kernel(CGState* st, int n, double tol, int max
   s.iter = 0;
   s.done = 0;
   s.status = 0;
-  s.rr = s.rr0 = s.pAp = s.alpha = s.beta = s.aux = 0.0;
-}
-
-// clear `done` of the listed states so that iterations resume (after a
-// reliable update that found the true residual still above tolerance)
-static __global__ void state_resume_kernel(CGState* st, const int* list, int n) {
-  const int k = threadIdx.x + blockIdx.x * blockDim.x;
-  if (k >= n) return;
-  CGState& s = st[list[k]];
-  if (s.status == 0 && s.iter < s.max_iter) s.done = 0;
+  s.rel = rel;
+  s.need_rel = 0;
+  s.final_check = 0;
+  s.delta2 = delta2;
+  s.rr = s.rr0 = s.pAp = s.alpha = s.beta = s.aux = s.rr_ref = 0.0;
 }
 
 }  // namespace tsm

@@ -55,8 +55,8 @@ static int upload_list(Ctx& c, int which, const std::vector<int>& list, const in
   return TSM_OK;
 }
 
-// r = b - Dhat^dag Dhat x in FP64 for the listed right-hand sides (reliable
-// update / true normal residual); <r, r> -> st[rhs].rr
+// r = b - Dhat^dag Dhat x in FP64 for the listed right-hand sides that have a
+// reliable update pending (st[rhs].need_rel); <r, r> -> st[rhs].rr
 static int normal_residual_f64(Ctx& c, PField x, PField b, PField r, CGState* st, const int* list, int n) {
   const double k = c.lat.kappa, mu = c.lat.mu, k2 = k * k;
   PField t, w;
@@ -64,12 +64,16 @@ static int normal_residual_f64(Ctx& c, PField x, PField b, PField r, CGState* st
   TSM_TRY(c.field("rel_w", TSM_F64, &w, c.batch_cap));
   HopArgs<F64> h = hop_args<F64>(c, 1);
   h.active = list;
+  h.skip = st;
+  h.skip_rel = 1;
   h.in = x.as<F64>();
   h.out = t.as<F64>();
   h.to = twist_Ainv(k, mu);
   TSM_TRY(launch_hop<F64>(c, h, 0, 0, -1, n));
   h = hop_args<F64>(c, 0);
   h.active = list;
+  h.skip = st;
+  h.skip_rel = 1;
   h.in = t.as<F64>();
   h.center = x.as<F64>();
   h.tc = twist_A(k, mu);
@@ -81,12 +85,16 @@ static int normal_residual_f64(Ctx& c, PField x, PField b, PField r, CGState* st
   TSM_TRY(launch_hop<F64>(c, h, 0, HOP_CENTER, -1, n));
   h = hop_args<F64>(c, 1);
   h.active = list;
+  h.skip = st;
+  h.skip_rel = 1;
   h.in = w.as<F64>();
   h.out = t.as<F64>();
   h.to = twist_Ainv(k, -mu);
   TSM_TRY(launch_hop<F64>(c, h, 1, 0, -1, n));
   h = hop_args<F64>(c, 0);
   h.active = list;
+  h.skip = st;
+  h.skip_rel = 1;
   h.in = t.as<F64>();
   h.center = w.as<F64>();
   h.tc = twist_A(k, -mu);
@@ -128,7 +136,9 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
     TSM_TRY(launch_hop<SP>(c, h, 0, HOP_CENTER, -1, nrhs));
   }
   // r0 = Dhat^dag bhat, <r0, r0> initialises the states
-  state_init_kernel<<<1, Ctx::kMaxStates, 0, c.stream>>>(st, nrhs, stop.rel_tol, stop.max_iter);
+  const double delta = (stop.reliable_delta > 0.0) ? stop.reliable_delta : 0.1;
+  state_init_kernel<<<1, Ctx::kMaxStates, 0, c.stream>>>(st, nrhs, stop.rel_tol, stop.max_iter, REL ? 1 : 0,
+                                                         delta * delta);
   c.launches++;
   TSM_TRY(check_launch(c, "state_init_kernel"));
   TSM_TRY(launch_twist<SP>(c, twist_Ainv(k, -mu), bhat, w0, nullptr, nullptr, nrhs));
@@ -163,11 +173,81 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
     TSM_TRY(c.field("cg_r64", TSM_F64, &r64, nb));
     TSM_TRY((launch_convert<F64, F64>(c, PField{}, x64, nullptr, nrhs)));
   }
+  // one CG iteration over the listed right-hand sides (n of them), followed,
+  // with reliable updates, by the FP64 update of those that asked for one
+  auto iteration = [&](const int* dact, int n, bool timed) -> int {
+    c.prof_this_launch = c.profile && timed;
+    HopArgs<S> h = hop_args<S>(c, 1);   // K1
+    h.active = dact;
+    h.in = p.as<S>();
+    h.out = t.as<S>();
+    h.to = twist_Ainv(k, mu);
+    h.skip = st;
+    TSM_TRY(launch_hop<S>(c, h, 0, 0, PK_HOP, n));
+    h = hop_args<S>(c, 0);              // K2
+    h.active = dact;
+    h.in = t.as<S>();
+    h.center = p.as<S>();
+    h.tc = twist_A(k, mu);
+    h.ac = 1.0;
+    h.ah = -k2;
+    h.to = twist_Ainv(k, mu);
+    h.ts = twist_Ainv(k, -mu);
+    h.out = w.as<S>();
+    h.skip = st;
+    h.st = st;
+    h.post = POST_ALPHA;
+    TSM_TRY(launch_hop<S>(c, h, 0, HOP_CENTER | HOP_NORM, PK_HOP_XPAY, n));
+    h = hop_args<S>(c, 1);              // K3
+    h.active = dact;
+    h.in = w.as<S>();
+    h.out = t.as<S>();
+    h.to = twist_Ainv(k, -mu);
+    h.skip = st;
+    TSM_TRY(launch_hop<S>(c, h, 1, 0, PK_HOP_DAG, n));
+    CGUpdArgs<S, SA> u{};               // K4
+    u.g = c.g;
+    u.Ue = c.links_of<S>(0);
+    u.Uo = c.links_of<S>(1);
+    u.lstride = c.lstride;
+    u.t = t.as<S>();
+    u.w = w.as<S>();
+    u.p = p.as<S>();
+    u.r = r.as<SA>();
+    u.x = x.as<SA>();
+    u.sstride = c.sstride;
+    u.kappa2 = k2;
+    u.tw = twist_A(k, -mu);
+    u.active = dact;
+    u.st = st;
+    u.red = c.red;
+    TSM_TRY((launch_cg_update<S, SA>(c, u, n)));
+    c.prof_this_launch = false;
+    TSM_TRY((launch_cg_p<S, SA>(c, r, p, st, dact, n)));   // K5
+    if constexpr (REL) {
+      // reliable update (Sleijpen & van der Vorst; Clark et al. for lattice QCD):
+      // for every right-hand side whose residual fell by delta since the last
+      // update, or that met its stopping rule, fold the FP32 increment into the
+      // FP64 solution and replace the iterated residual by the true FP64 normal
+      // residual; the others return at once from these kernels
+      const int blocks = (c.g.Vh + SITE_NT - 1) / SITE_NT;
+      accumulate_solution_kernel<<<dim3(n, blocks), SITE_NT, 0, c.stream>>>(c.g.Vh, x.as<F32>(), x64.as<F64>(),
+                                                                           c.sstride, dact, st);
+      c.launches++;
+      TSM_TRY(check_launch(c, "accumulate_solution_kernel"));
+      TSM_TRY(normal_residual_f64(c, x64, r0, r64, st, dact, n));
+      replace_residual_kernel<<<dim3(n, blocks), SITE_NT, 0, c.stream>>>(c.g.Vh, r64.as<F64>(), r.as<F32>(),
+                                                                        c.sstride, dact, st);
+      c.launches++;
+      TSM_TRY(check_launch(c, "replace_residual_kernel"));
+      rel_finish_kernel<<<1, Ctx::kMaxStates, 0, c.stream>>>(st, dact, n);
+      c.launches++;
+      TSM_TRY(check_launch(c, "rel_finish_kernel"));
+    }
+    return TSM_OK;
+  };
   std::vector<CGState> hs;
   TSM_TRY(read_states(c, s0, nrhs, hs));
-  const double delta = (stop.reliable_delta > 0.0) ? stop.reliable_delta : 0.1;
-  std::vector<double> rr_ref(nrhs);
-  for (int i = 0; i < nrhs; ++i) rr_ref[i] = hs[i].rr0;
   auto iterating = [&](int i) { return !hs[i].done && hs[i].status == 0; };
   const int chunk = 8;
   long long launched = 0;   // guards the host loop against states that stop advancing
@@ -180,7 +260,7 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
         min_left = std::min(min_left, stop.max_iter - hs[i].iter);
       }
     if (act.empty()) break;
-    if (launched > (long long)stop.max_iter + 64) {
+    if (launched > 2 * (long long)stop.max_iter + 64) {
       set_error("solver state stopped advancing after %lld iterations", launched);
       return TSM_ERR_CUDA;
     }
@@ -191,95 +271,8 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
     if (min_left < m) m = min_left;
     if (m < 1) m = 1;
     launched += m;
-    for (int it = 0; it < m; ++it) {
-      c.prof_this_launch = c.profile && it == 0;
-      HopArgs<S> h = hop_args<S>(c, 1);   // K1
-      h.active = dact;
-      h.in = p.as<S>();
-      h.out = t.as<S>();
-      h.to = twist_Ainv(k, mu);
-      h.skip = st;
-      TSM_TRY(launch_hop<S>(c, h, 0, 0, PK_HOP, n));
-      h = hop_args<S>(c, 0);              // K2
-      h.active = dact;
-      h.in = t.as<S>();
-      h.center = p.as<S>();
-      h.tc = twist_A(k, mu);
-      h.ac = 1.0;
-      h.ah = -k2;
-      h.to = twist_Ainv(k, mu);
-      h.ts = twist_Ainv(k, -mu);
-      h.out = w.as<S>();
-      h.skip = st;
-      h.st = st;
-      h.post = POST_ALPHA;
-      TSM_TRY(launch_hop<S>(c, h, 0, HOP_CENTER | HOP_NORM, PK_HOP_XPAY, n));
-      h = hop_args<S>(c, 1);              // K3
-      h.active = dact;
-      h.in = w.as<S>();
-      h.out = t.as<S>();
-      h.to = twist_Ainv(k, -mu);
-      h.skip = st;
-      TSM_TRY(launch_hop<S>(c, h, 1, 0, PK_HOP_DAG, n));
-      CGUpdArgs<S, SA> u{};               // K4
-      u.g = c.g;
-      u.Ue = c.links_of<S>(0);
-      u.Uo = c.links_of<S>(1);
-      u.lstride = c.lstride;
-      u.t = t.as<S>();
-      u.w = w.as<S>();
-      u.p = p.as<S>();
-      u.r = r.as<SA>();
-      u.x = x.as<SA>();
-      u.sstride = c.sstride;
-      u.kappa2 = k2;
-      u.tw = twist_A(k, -mu);
-      u.active = dact;
-      u.st = st;
-      u.red = c.red;
-      TSM_TRY((launch_cg_update<S, SA>(c, u, n)));
-      c.prof_this_launch = false;
-      TSM_TRY((launch_cg_p<S, SA>(c, r, p, st, dact, n)));   // K5
-    }
-    c.prof_this_launch = false;
+    for (int it = 0; it < m; ++it) TSM_TRY(iteration(dact, n, it == 0));
     TSM_TRY(read_states(c, s0, nrhs, hs));
-    if constexpr (REL) {
-      // reliable update of every right-hand side that just met its rule or whose
-      // residual fell by delta: fold the FP32 increment into the FP64 solution
-      // and replace the iterated residual by the true FP64 normal residual
-      std::vector<int> rel;
-      for (int i : act)
-        if (hs[i].status == 0 && (hs[i].done || hs[i].rr < delta * delta * rr_ref[i])) rel.push_back(i);
-      if (!rel.empty()) {
-        const int nr = (int)rel.size();
-        const int* drel = nullptr;
-        TSM_TRY(upload_list(c, 1, rel, &drel));
-        const int blocks = (c.g.Vh + SITE_NT - 1) / SITE_NT;
-        accumulate_solution_kernel<<<dim3(nr, blocks), SITE_NT, 0, c.stream>>>(c.g.Vh, x.as<F32>(), x64.as<F64>(),
-                                                                              c.sstride, drel);
-        c.launches++;
-        TSM_TRY(check_launch(c, "accumulate_solution_kernel"));
-        TSM_TRY(normal_residual_f64(c, x64, r0, r64, st, drel, nr));
-        TSM_TRY((launch_convert<F64, F32>(c, r64, r, drel, nr)));
-        TSM_TRY(read_states(c, s0, nrhs, hs));
-        std::vector<int> resume;
-        for (int i : rel) {
-          rr_ref[i] = hs[i].rr;
-          if (hs[i].done && hs[i].status == 0) {
-            const bool met = !(std::sqrt(hs[i].rr) >= stop.rel_tol * std::sqrt(hs[i].rr0));
-            if (!met && hs[i].iter < stop.max_iter) resume.push_back(i);
-          }
-        }
-        if (!resume.empty()) {
-          const int* dres = nullptr;
-          TSM_TRY(upload_list(c, 2, resume, &dres));
-          state_resume_kernel<<<1, Ctx::kMaxStates, 0, c.stream>>>(st, dres, (int)resume.size());
-          c.launches++;
-          TSM_TRY(check_launch(c, "state_resume_kernel"));
-          TSM_TRY(read_states(c, s0, nrhs, hs));
-        }
-      }
-    }
   }
   // solution: even part from CG, odd part reconstructed
   if constexpr (REL) {

@@ -51,7 +51,7 @@ class TsmParams(ctypes.Structure):
                 ("lp_begin", ctypes.c_uint32), ("lp_end", ctypes.c_uint32),
                 ("hp", TmStop), ("lp", TmStop), ("batch", ctypes.c_int),
                 ("gammas", ctypes.POINTER(ctypes.c_int)), ("n_gamma", ctypes.c_int),
-                ("moms", ctypes.POINTER(ctypes.c_int)), ("n_q", ctypes.c_int)]
+                ("moms", ctypes.POINTER(ctypes.c_int)), ("n_q", ctypes.c_int), ("verify", ctypes.c_int)]
 
 
 # exported symbol -> (restype, argtypes)
@@ -246,7 +246,7 @@ def tsm_contract_noalloc(lat, seed, kind, source, s_dev, gammas, moms, out_dev, 
                                                  ctypes.c_void_p(stream or 0)), "tsm_contract_noalloc")
 
 
-def params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batch=1):
+def params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batch=1, verify=False):
     """TsmParams; keeps the integer arrays alive on the returned object."""
     p = TsmParams()
     p.seed = int(seed)
@@ -263,6 +263,7 @@ def params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batc
     p.n_gamma = len(g)
     p.moms = m.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
     p.n_q = len(m) // 3
+    p.verify = 1 if verify else 0
     return p
 
 
@@ -364,10 +365,10 @@ class Context:
         return out
 
     def loops(self, seed, noise, n_hp, n_lp, hp_stop, lp_stop, gammas, moms, hp_range=None, lp_range=None,
-              per_source=False, batch=1):
+              per_source=False, batch=1, verify=True):
         hp_range = hp_range or (0, n_hp)
         lp_range = lp_range or (n_hp, n_hp + n_lp)
-        p = params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batch)
+        p = params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batch, verify)
         shape = (len(gammas), len(moms), self.dims[3])
         out = {k: np.zeros(shape, dtype=np.complex128) for k in ("loops", "lp_mean", "corr_mean")}
         out["err"] = np.zeros(shape, dtype=np.float64)
