@@ -201,6 +201,20 @@ int tsm_loops(tsm_ctx* ctx, const tsm_params* p,
               double* loops, double* err, double* lp_mean, double* corr_mean,
               double* per_corr, double* per_lp, int on_device, tsm_loop_stats* stats);
 
+/* Run the TSM of n contexts -- typically lattices of different volumes, all
+ * on one device -- as ONE captured CUDA graph.  Every batched CG solve becomes
+ * a graph while-loop whose condition a device kernel clears once each of its
+ * sources has met its stopping rule (no host round trip inside the graph);
+ * converged sources are skipped by the remaining iterations; the contexts'
+ * work forms parallel branches of the graph.  params[i] applies to ctxs[i]
+ * (verify is ignored).  Outputs are DEVICE pointers (arrays of n; the array
+ * itself or any entry may be NULL): loops[i], err[i], per_corr[i], per_lp[i]
+ * as in tsm_loops; stats (host, n entries, may be NULL) receives iteration
+ * counts.  The graph runs on ctxs[0]'s stream and has completed on return.
+ * Results are bit-identical to tsm_loops with the same parameters. */
+int tsm_loops_graph(tsm_ctx** ctxs, const tsm_params* params, int n, double** loops, double** err,
+                    double** per_corr, double** per_lp, tsm_loop_stats* stats);
+
 /* Combine per-source loops gathered from several processes into the estimate
  * of Eq. 2.4.  Runs the same device kernel, in the same summation order, as
  * the final step of tsm_loops, so any split of the source ranges gives

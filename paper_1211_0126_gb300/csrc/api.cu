@@ -164,6 +164,132 @@ int apply_operator(Ctx& c, int op, int dagger, EOField in, EOField out) {
   }
 }
 
+
+// ---------------------------------------------------------------- TSM runs
+// state of one tsm_loops call: plan, per-source loop buffers and source /
+// solution batches, all allocated before any work is recorded (so that the
+// recording can also run under stream capture)
+struct TsmRun {
+  ContractPlan plan;
+  NoiseSpec ns{};
+  int E = 0, n_hp = 0, n_lp = 0, B = 1;
+  int sp_lp = TSM_F32, sp_hp = TSM_F64;
+  bool fp64_path = false;
+  double2* d_corr = nullptr;
+  double2* d_lp = nullptr;
+  EOField b_lp, s_lp, b_hp, s_hp;
+};
+
+int prepare_run(Ctx& c, const tsm_params* p, TsmRun* run) {
+  if (!c.has_gauge) return bad(TSM_ERR_NO_GAUGE, "no gauge field loaded");
+  if (p->noise != 4 && p->noise != 2) return bad(TSM_ERR_ARG, "noise kind must be 4 or 2");
+  if (p->hp_end < p->hp_begin || p->lp_end < p->lp_begin) return bad(TSM_ERR_ARG, "empty-reversed source range");
+  if (p->batch < 1) return bad(TSM_ERR_ARG, "batch must be >= 1");
+  TSM_TRY(check_stop(&p->hp));
+  TSM_TRY(check_stop(&p->lp));
+  TSM_TRY(run->plan.prepare(c, p->gammas, p->n_gamma, p->moms, p->n_q));
+  run->E = run->plan.entries(c.lat.L[3]);
+  run->n_hp = (int)(p->hp_end - p->hp_begin);
+  run->n_lp = (int)(p->lp_end - p->lp_begin);
+  run->sp_lp = solution_prec(p->lp);
+  run->sp_hp = solution_prec(p->hp);
+  run->fp64_path = (p->lp.prec == TSM_F64 && p->hp.prec == TSM_F64);
+  run->ns = make_noise(p->seed, p->noise);
+  run->B = std::min(std::max(p->batch, 1), Ctx::kMaxBatch);
+  c.batch_cap = std::max(c.batch_cap, run->B);
+  void* vc = nullptr;
+  void* vl = nullptr;
+  TSM_TRY(c.buffer("tsm_per_corr", (size_t)std::max(run->n_hp, 1) * run->E * sizeof(double2), &vc));
+  TSM_TRY(c.buffer("tsm_per_lp", (size_t)std::max(run->n_lp, 1) * run->E * sizeof(double2), &vl));
+  run->d_corr = static_cast<double2*>(vc);
+  run->d_lp = static_cast<double2*>(vl);
+  TSM_TRY(eo_fields(c, "tsm_b_lp", run->sp_lp, &run->b_lp, c.batch_cap));
+  TSM_TRY(eo_fields(c, "tsm_s_lp", run->sp_lp, &run->s_lp, c.batch_cap));
+  TSM_TRY(eo_fields(c, "tsm_b_hp", run->sp_hp, &run->b_hp, c.batch_cap));
+  TSM_TRY(eo_fields(c, "tsm_s_hp", run->sp_hp, &run->s_hp, c.batch_cap));
+  TSM_TRY(reserve_solver(c, p->lp));
+  TSM_TRY(reserve_solver(c, p->hp));
+  TSM_TRY(reserve_contract(c));
+  return TSM_OK;
+}
+
+// all work of one TSM estimate, in stream order; eager mode also collects the
+// statistics (and verifies HP solutions if asked), capture mode records the
+// solves' state ranges for reading after the graph ran
+int record_run(Ctx& c, const tsm_params* p, TsmRun& run, tsm_loop_stats* st) {
+  const int E = run.E, B = run.B, sp_lp = run.sp_lp, sp_hp = run.sp_hp;
+  const NoiseSpec& ns = run.ns;
+  *st = tsm_loop_stats{};
+  st->lp_max_true_res = -1.0;
+  st->hp_max_true_res = (p->verify && !c.capturing) ? 0.0 : -1.0;
+  st->n_sources = run.n_hp + run.n_lp;
+  // noise of sources j0 .. j0+n-1 into a batch of fields
+  auto gen = [&](int prec, uint32_t j0, EOField f, int n) {
+    return dispatch_prec(prec, [&](auto tag) {
+      using S = decltype(tag);
+      TSM_TRY(launch_noise<S>(c, 0, ns, j0, f.e, n));
+      return launch_noise<S>(c, 1, ns, j0, f.o, n);
+    });
+  };
+  auto contract = [&](uint32_t j, EOField a, int pa, const EOField* b, int pb, double2* out) {
+    const ContractPlan& plan = run.plan;
+    if (run.fp64_path) return launch_contract<double, F64, F64>(c, plan, ns, j, a, b, out);
+    if (pa == TSM_F64 && (b == nullptr || pb == TSM_F64)) return launch_contract<float, F64, F64>(c, plan, ns, j, a, b, out);
+    if (pa == TSM_F64) return launch_contract<float, F64, F32>(c, plan, ns, j, a, b, out);
+    if (b == nullptr || pb == TSM_F32) return launch_contract<float, F32, F32>(c, plan, ns, j, a, b, out);
+    return launch_contract<float, F32, F64>(c, plan, ns, j, a, b, out);
+  };
+  // state slots: fixed in eager mode, one fresh range per solve under capture
+  auto slots = [&](int n, std::vector<std::pair<int, int>>& log) {
+    if (!c.capturing) return 0;
+    const int s0 = c.next_state;
+    c.next_state += n;
+    log.push_back({s0, n});
+    return s0;
+  };
+  std::vector<SolveResult> r_lp(B), r_hp(B);
+  // HP set: the LP map and the HP solve of every source, then L(s_HP - s_LP)
+  for (uint32_t j0 = p->hp_begin; j0 < p->hp_end; j0 += B) {
+    const int n = (int)std::min<uint32_t>(B, p->hp_end - j0);
+    TSM_TRY(gen(sp_lp, j0, run.b_lp, n));
+    TSM_TRY(solve_batch(c, p->lp, slots(n, c.cap_lp), n, run.b_lp, run.s_lp, r_lp.data()));
+    if (sp_hp != sp_lp) TSM_TRY(gen(sp_hp, j0, run.b_hp, n));
+    EOField bh = (sp_hp != sp_lp) ? run.b_hp : run.b_lp;
+    TSM_TRY(solve_batch(c, p->hp, slots(n, c.cap_hp), n, bh, run.s_hp, r_hp.data()));
+    for (int r = 0; r < n; ++r) {
+      if (!c.capturing) {
+        if (r_lp[r].status != TSM_OK || r_hp[r].status != TSM_OK) return bad(TSM_ERR_NONFINITE, "NaN/Inf in a solve");
+        if (p->verify) {
+          double tr = 0.0;
+          TSM_TRY(true_residual(c, sp_hp, eo_at(bh, sp_hp, c.g.Vh, r), eo_at(run.s_hp, sp_hp, c.g.Vh, r), &tr));
+          st->hp_max_true_res = std::max(st->hp_max_true_res, tr);
+        }
+        st->lp_iters += r_lp[r].iters;
+        st->hp_iters += r_hp[r].iters;
+        if (!r_hp[r].converged) st->hp_not_converged++;
+      }
+      const EOField sl = eo_at(run.s_lp, sp_lp, c.g.Vh, r);
+      TSM_TRY(contract(j0 + r, eo_at(run.s_hp, sp_hp, c.g.Vh, r), sp_hp, &sl, sp_lp,
+                       run.d_corr + (size_t)(j0 + r - p->hp_begin) * E));
+    }
+  }
+  // LP set: the same LP map, L(s_LP)
+  for (uint32_t j0 = p->lp_begin; j0 < p->lp_end; j0 += B) {
+    const int n = (int)std::min<uint32_t>(B, p->lp_end - j0);
+    TSM_TRY(gen(sp_lp, j0, run.b_lp, n));
+    TSM_TRY(solve_batch(c, p->lp, slots(n, c.cap_lp), n, run.b_lp, run.s_lp, r_lp.data()));
+    for (int r = 0; r < n; ++r) {
+      if (!c.capturing) {
+        if (r_lp[r].status != TSM_OK) return bad(TSM_ERR_NONFINITE, "NaN/Inf in a solve");
+        st->lp_iters += r_lp[r].iters;
+      }
+      TSM_TRY(contract(j0 + r, eo_at(run.s_lp, sp_lp, c.g.Vh, r), sp_lp, nullptr, sp_lp,
+                       run.d_lp + (size_t)(j0 + r - p->lp_begin) * E));
+    }
+  }
+  return TSM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -201,13 +327,14 @@ int tsm_create(int device, void* cuda_stream, tsm_ctx** out) {
   if (rc == TSM_OK && cudaMalloc(&c.states, Ctx::kMaxStates * sizeof(CGState)) != cudaSuccess) rc = TSM_ERR_CUDA;
   if (rc == TSM_OK && cudaMallocHost(&c.h_states, Ctx::kMaxStates * sizeof(CGState)) != cudaSuccess)
     rc = TSM_ERR_CUDA;
-  if (rc == TSM_OK && cudaMalloc(&c.red.counter, Ctx::kMaxStates * sizeof(unsigned int)) != cudaSuccess)
+  if (rc == TSM_OK && cudaMalloc(&c.red.counter, Ctx::kMaxBatch * sizeof(unsigned int)) != cudaSuccess)
     rc = TSM_ERR_CUDA;
-  if (rc == TSM_OK && cudaMemset(c.red.counter, 0, Ctx::kMaxStates * sizeof(unsigned int)) != cudaSuccess)
+  if (rc == TSM_OK && cudaMemset(c.red.counter, 0, Ctx::kMaxBatch * sizeof(unsigned int)) != cudaSuccess)
     rc = TSM_ERR_CUDA;
-  if (rc == TSM_OK && cudaMalloc(&c.d_lists, 3 * Ctx::kMaxStates * sizeof(int)) != cudaSuccess) rc = TSM_ERR_CUDA;
-  if (rc == TSM_OK && cudaMallocHost(&c.h_lists, 3 * Ctx::kMaxStates * sizeof(int)) != cudaSuccess)
+  if (rc == TSM_OK && cudaMalloc(&c.d_lists, 3 * Ctx::kMaxBatch * sizeof(int)) != cudaSuccess) rc = TSM_ERR_CUDA;
+  if (rc == TSM_OK && cudaMallocHost(&c.h_lists, 3 * Ctx::kMaxBatch * sizeof(int)) != cudaSuccess)
     rc = TSM_ERR_CUDA;
+  if (rc == TSM_OK && cudaMalloc(&c.d_guard, Ctx::kMaxGuards * sizeof(int)) != cudaSuccess) rc = TSM_ERR_CUDA;
   if (rc == TSM_OK && cudaMemset(c.states, 0, Ctx::kMaxStates * sizeof(CGState)) != cudaSuccess) rc = TSM_ERR_CUDA;
   if (rc != TSM_OK) {
     set_error("tsm_create: device allocation failed");
@@ -267,7 +394,7 @@ int tsm_load_gauge(tsm_ctx* h, const tm_lattice* lat, const double* U, int on_de
     if (c.red.partials) cudaFree(c.red.partials);
     c.red_cap = vh / 64 + 64;
     c.red.stride = (int)c.red_cap;
-    TSM_CUDA(cudaMalloc(&c.red.partials, Ctx::kMaxStates * c.red_cap * sizeof(double)));
+    TSM_CUDA(cudaMalloc(&c.red.partials, Ctx::kMaxBatch * c.red_cap * sizeof(double)));
     c.batch_cap = 1;
   }
   const double* dU = nullptr;
@@ -430,109 +557,164 @@ int tsm_loops(tsm_ctx* h, const tsm_params* p, double* loops, double* err, doubl
               double* per_corr, double* per_lp, int on_device, tsm_loop_stats* stats) {
   if (h == nullptr || p == nullptr) return bad(TSM_ERR_ARG, "null argument");
   Ctx& c = h->c;
-  if (!c.has_gauge) return bad(TSM_ERR_NO_GAUGE, "no gauge field loaded");
-  if (p->noise != 4 && p->noise != 2) return bad(TSM_ERR_ARG, "noise kind must be 4 or 2");
-  if (p->hp_end < p->hp_begin || p->lp_end < p->lp_begin) return bad(TSM_ERR_ARG, "empty-reversed source range");
-  if (p->batch < 1) return bad(TSM_ERR_ARG, "batch must be >= 1");
-  TSM_TRY(check_stop(&p->hp));
-  TSM_TRY(check_stop(&p->lp));
   TSM_TRY(select_device(c));
-  ContractPlan plan;
-  TSM_TRY(plan.prepare(c, p->gammas, p->n_gamma, p->moms, p->n_q));
-  const int T = c.lat.L[3];
-  const int E = plan.entries(T);
-  const int n_hp = (int)(p->hp_end - p->hp_begin), n_lp = (int)(p->lp_end - p->lp_begin);
-  const int sp_lp = solution_prec(p->lp), sp_hp = solution_prec(p->hp);
-  const bool fp64_path = (p->lp.prec == TSM_F64 && p->hp.prec == TSM_F64);
-  void* vc = nullptr;
-  void* vl = nullptr;
-  TSM_TRY(c.buffer("tsm_per_corr", (size_t)std::max(n_hp, 1) * E * sizeof(double2), &vc));
-  TSM_TRY(c.buffer("tsm_per_lp", (size_t)std::max(n_lp, 1) * E * sizeof(double2), &vl));
-  double2* d_corr = static_cast<double2*>(vc);
-  double2* d_lp = static_cast<double2*>(vl);
-  const int B = std::min(std::max(p->batch, 1), Ctx::kMaxBatch);
-  c.batch_cap = std::max(c.batch_cap, B);
-  EOField b_lp, s_lp, b_hp, s_hp;
-  TSM_TRY(eo_fields(c, "tsm_b_lp", sp_lp, &b_lp, c.batch_cap));
-  TSM_TRY(eo_fields(c, "tsm_s_lp", sp_lp, &s_lp, c.batch_cap));
-  TSM_TRY(eo_fields(c, "tsm_b_hp", sp_hp, &b_hp, c.batch_cap));
-  TSM_TRY(eo_fields(c, "tsm_s_hp", sp_hp, &s_hp, c.batch_cap));
-  const NoiseSpec ns = make_noise(p->seed, p->noise);
+  TsmRun run;
+  TSM_TRY(prepare_run(c, p, &run));
   tsm_loop_stats st{};
-  st.lp_max_true_res = -1.0;
-  st.hp_max_true_res = p->verify ? 0.0 : -1.0;
-  // noise of sources j0 .. j0+n-1 into a batch of fields
-  auto gen = [&](int prec, uint32_t j0, EOField f, int n) {
-    return dispatch_prec(prec, [&](auto tag) {
-      using S = decltype(tag);
-      TSM_TRY(launch_noise<S>(c, 0, ns, j0, f.e, n));
-      return launch_noise<S>(c, 1, ns, j0, f.o, n);
-    });
-  };
-  auto contract = [&](uint32_t j, EOField a, int pa, const EOField* b, int pb, double2* out) {
-    if (fp64_path) return launch_contract<double, F64, F64>(c, plan, ns, j, a, b, out);
-    if (pa == TSM_F64 && (b == nullptr || pb == TSM_F64)) return launch_contract<float, F64, F64>(c, plan, ns, j, a, b, out);
-    if (pa == TSM_F64) return launch_contract<float, F64, F32>(c, plan, ns, j, a, b, out);
-    if (b == nullptr || pb == TSM_F32) return launch_contract<float, F32, F32>(c, plan, ns, j, a, b, out);
-    return launch_contract<float, F32, F64>(c, plan, ns, j, a, b, out);
-  };
-  std::vector<SolveResult> r_lp(B), r_hp(B);
-  // HP set: the LP map and the HP solve of every source, then L(s_HP - s_LP)
-  for (uint32_t j0 = p->hp_begin; j0 < p->hp_end; j0 += B) {
-    const int n = (int)std::min<uint32_t>(B, p->hp_end - j0);
-    TSM_TRY(gen(sp_lp, j0, b_lp, n));
-    TSM_TRY(solve_batch(c, p->lp, 0, n, b_lp, s_lp, r_lp.data()));
-    if (sp_hp != sp_lp) TSM_TRY(gen(sp_hp, j0, b_hp, n));
-    EOField bh = (sp_hp != sp_lp) ? b_hp : b_lp;
-    TSM_TRY(solve_batch(c, p->hp, 0, n, bh, s_hp, r_hp.data()));
-    for (int r = 0; r < n; ++r) {
-      if (r_lp[r].status != TSM_OK || r_hp[r].status != TSM_OK) return bad(TSM_ERR_NONFINITE, "NaN/Inf in a solve");
-      if (p->verify) {
-        double tr = 0.0;
-        TSM_TRY(true_residual(c, sp_hp, eo_at(bh, sp_hp, c.g.Vh, r), eo_at(s_hp, sp_hp, c.g.Vh, r), &tr));
-        st.hp_max_true_res = std::max(st.hp_max_true_res, tr);
-      }
-      st.lp_iters += r_lp[r].iters;
-      st.hp_iters += r_hp[r].iters;
-      if (!r_hp[r].converged) st.hp_not_converged++;
-      const EOField sl = eo_at(s_lp, sp_lp, c.g.Vh, r);
-      TSM_TRY(contract(j0 + r, eo_at(s_hp, sp_hp, c.g.Vh, r), sp_hp, &sl, sp_lp,
-                       d_corr + (size_t)(j0 + r - p->hp_begin) * E));
-    }
-  }
-  // LP set: the same LP map, L(s_LP)
-  for (uint32_t j0 = p->lp_begin; j0 < p->lp_end; j0 += B) {
-    const int n = (int)std::min<uint32_t>(B, p->lp_end - j0);
-    TSM_TRY(gen(sp_lp, j0, b_lp, n));
-    TSM_TRY(solve_batch(c, p->lp, 0, n, b_lp, s_lp, r_lp.data()));
-    for (int r = 0; r < n; ++r) {
-      if (r_lp[r].status != TSM_OK) return bad(TSM_ERR_NONFINITE, "NaN/Inf in a solve");
-      st.lp_iters += r_lp[r].iters;
-      TSM_TRY(contract(j0 + r, eo_at(s_lp, sp_lp, c.g.Vh, r), sp_lp, nullptr, sp_lp,
-                       d_lp + (size_t)(j0 + r - p->lp_begin) * E));
-    }
-  }
-  st.n_sources = n_hp + n_lp;
+  TSM_TRY(record_run(c, p, run, &st));
   // Eq. 2.4 combine
+  const int E = run.E, n_hp = run.n_hp, n_lp = run.n_lp;
   double *d_est = nullptr, *d_err = nullptr, *d_lpm = nullptr, *d_cm = nullptr;
   const size_t cb = (size_t)E * sizeof(double2), rb = (size_t)E * sizeof(double);
   if (loops) TSM_TRY(stage_out_ptr(c, "out_est", loops, cb, on_device, &d_est));
   if (err) TSM_TRY(stage_out_ptr(c, "out_err", err, rb, on_device, &d_err));
   if (lp_mean) TSM_TRY(stage_out_ptr(c, "out_lpm", lp_mean, cb, on_device, &d_lpm));
   if (corr_mean) TSM_TRY(stage_out_ptr(c, "out_cm", corr_mean, cb, on_device, &d_cm));
-  TSM_TRY(launch_combine(c, d_corr, n_hp, d_lp, n_lp, E, reinterpret_cast<double2*>(d_est), d_err,
+  TSM_TRY(launch_combine(c, run.d_corr, n_hp, run.d_lp, n_lp, E, reinterpret_cast<double2*>(d_est), d_err,
                          reinterpret_cast<double2*>(d_lpm), reinterpret_cast<double2*>(d_cm)));
   if (loops) TSM_TRY(stage_out_finish(c, loops, d_est, cb, on_device));
   if (err) TSM_TRY(stage_out_finish(c, err, d_err, rb, on_device));
   if (lp_mean) TSM_TRY(stage_out_finish(c, lp_mean, d_lpm, cb, on_device));
   if (corr_mean) TSM_TRY(stage_out_finish(c, corr_mean, d_cm, cb, on_device));
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (per_corr && n_hp > 0) TSM_CUDA(cudaMemcpyAsync(per_corr, d_corr, (size_t)n_hp * cb, k, c.stream));
-  if (per_lp && n_lp > 0) TSM_CUDA(cudaMemcpyAsync(per_lp, d_lp, (size_t)n_lp * cb, k, c.stream));
+  if (per_corr && n_hp > 0) TSM_CUDA(cudaMemcpyAsync(per_corr, run.d_corr, (size_t)n_hp * cb, k, c.stream));
+  if (per_lp && n_lp > 0) TSM_CUDA(cudaMemcpyAsync(per_lp, run.d_lp, (size_t)n_lp * cb, k, c.stream));
   TSM_CUDA(cudaStreamSynchronize(c.stream));
   TSM_TRY(c.harvest_events());
   if (stats) *stats = st;
   return TSM_OK;
+}
+
+int tsm_loops_graph(tsm_ctx** ctxs, const tsm_params* params, int n, double** loops, double** err,
+                    double** per_corr, double** per_lp, tsm_loop_stats* stats) {
+  if (ctxs == nullptr || params == nullptr || n < 1) return bad(TSM_ERR_ARG, "null argument or n < 1");
+  for (int i = 0; i < n; ++i) {
+    if (ctxs[i] == nullptr) return bad(TSM_ERR_ARG, "null context");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return bad(TSM_ERR_ARG, "a context appears twice");
+    if (ctxs[i]->c.device != ctxs[0]->c.device) return bad(TSM_ERR_ARG, "contexts on different devices");
+  }
+  Ctx& c0 = ctxs[0]->c;
+  TSM_TRY(select_device(c0));
+  std::vector<TsmRun> runs(n);
+  for (int i = 0; i < n; ++i) TSM_TRY(prepare_run(ctxs[i]->c, params + i, &runs[i]));
+  for (int i = 0; i < n; ++i) TSM_CUDA(cudaStreamSynchronize(ctxs[i]->c.stream));
+  // private streams for the capture (one branch per context + one for loop bodies)
+  std::vector<cudaStream_t> own(2 * n + 1, nullptr);
+  std::vector<cudaStream_t> saved(n);
+  std::vector<cudaEvent_t> evs(n + 1, nullptr);
+  int rc = TSM_OK;
+  auto cleanup = [&]() {
+    for (int i = 0; i < n; ++i) {
+      Ctx& c = ctxs[i]->c;
+      if (own[1 + 2 * i]) c.stream = saved[i];
+      c.capturing = false;
+      c.body_stream = nullptr;
+    }
+    for (auto s : own)
+      if (s) cudaStreamDestroy(s);
+    for (auto e : evs)
+      if (e) cudaEventDestroy(e);
+  };
+  for (size_t k = 0; k < own.size() && rc == TSM_OK; ++k)
+    if (cudaStreamCreateWithFlags(&own[k], cudaStreamNonBlocking) != cudaSuccess) rc = TSM_ERR_CUDA;
+  for (size_t k = 0; k < evs.size() && rc == TSM_OK; ++k)
+    if (cudaEventCreateWithFlags(&evs[k], cudaEventDisableTiming) != cudaSuccess) rc = TSM_ERR_CUDA;
+  if (rc != TSM_OK) {
+    cleanup();
+    return bad(rc, "stream/event creation failed");
+  }
+  cudaStream_t origin = own[0];
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed) != cudaSuccess) rc = TSM_ERR_CUDA;
+  if (rc == TSM_OK && cudaEventRecord(evs[n], origin) != cudaSuccess) rc = TSM_ERR_CUDA;
+  std::vector<tsm_loop_stats> st(n);
+  for (int i = 0; i < n && rc == TSM_OK; ++i) {
+    Ctx& c = ctxs[i]->c;
+    saved[i] = c.stream;
+    c.stream = own[1 + 2 * i];
+    c.body_stream = own[2 + 2 * i];
+    c.capturing = true;
+    c.next_state = 0;
+    c.next_guard = 0;
+    c.cap_lp.clear();
+    c.cap_hp.clear();
+    if (cudaStreamWaitEvent(c.stream, evs[n], 0) != cudaSuccess) rc = TSM_ERR_CUDA;
+    if (rc == TSM_OK) rc = record_run(c, params + i, runs[i], &st[i]);
+    if (rc == TSM_OK) {
+      const int E = runs[i].E;
+      rc = launch_combine(c, runs[i].d_corr, runs[i].n_hp, runs[i].d_lp, runs[i].n_lp, E,
+                          loops ? reinterpret_cast<double2*>(loops[i]) : nullptr, err ? err[i] : nullptr, nullptr,
+                          nullptr);
+    }
+    const size_t cb = (size_t)runs[i].E * sizeof(double2);
+    if (rc == TSM_OK && per_corr && per_corr[i] && runs[i].n_hp > 0 &&
+        cudaMemcpyAsync(per_corr[i], runs[i].d_corr, runs[i].n_hp * cb, cudaMemcpyDeviceToDevice, c.stream) !=
+            cudaSuccess)
+      rc = TSM_ERR_CUDA;
+    if (rc == TSM_OK && per_lp && per_lp[i] && runs[i].n_lp > 0 &&
+        cudaMemcpyAsync(per_lp[i], runs[i].d_lp, runs[i].n_lp * cb, cudaMemcpyDeviceToDevice, c.stream) !=
+            cudaSuccess)
+      rc = TSM_ERR_CUDA;
+    if (rc == TSM_OK && cudaEventRecord(evs[i], c.stream) != cudaSuccess) rc = TSM_ERR_CUDA;
+    if (rc == TSM_OK && cudaStreamWaitEvent(origin, evs[i], 0) != cudaSuccess) rc = TSM_ERR_CUDA;
+  }
+  const cudaError_t ec = cudaStreamEndCapture(origin, &graph);
+  if (rc == TSM_OK && ec != cudaSuccess) {
+    set_error("graph capture failed: %s", cudaGetErrorString(ec));
+    rc = TSM_ERR_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (rc == TSM_OK) {
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    if (ei != cudaSuccess) {
+      set_error("graph instantiation failed: %s", cudaGetErrorString(ei));
+      rc = TSM_ERR_CUDA;
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    ctxs[i]->c.capturing = false;
+    ctxs[i]->c.stream = saved[i];
+  }
+  if (rc == TSM_OK) {
+    // launched on the first context's stream; completes before the call returns
+    if (cudaGraphLaunch(exec, c0.stream) != cudaSuccess || cudaStreamSynchronize(c0.stream) != cudaSuccess) {
+      set_error("graph launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+      rc = TSM_ERR_CUDA;
+    }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (rc == TSM_OK) {
+    for (int i = 0; i < n; ++i) {
+      Ctx& c = ctxs[i]->c;
+      const int used = c.next_state;
+      if (used > 0 &&
+          cudaMemcpy(c.h_states, c.states, used * sizeof(CGState), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        rc = TSM_ERR_CUDA;
+        break;
+      }
+      for (auto& r : c.cap_lp)
+        for (int k = 0; k < r.second; ++k) {
+          const CGState& q = c.h_states[r.first + k];
+          st[i].lp_iters += q.iter;
+          if (q.status != 0) rc = TSM_ERR_NONFINITE;
+        }
+      for (auto& r : c.cap_hp)
+        for (int k = 0; k < r.second; ++k) {
+          const CGState& q = c.h_states[r.first + k];
+          st[i].hp_iters += q.iter;
+          if (q.status != 0) rc = TSM_ERR_NONFINITE;
+          const bool met = q.rr0 == 0.0 || (q.tol <= 0.0 ? q.iter >= q.max_iter
+                                                         : !(std::sqrt(q.rr) >= q.tol * std::sqrt(q.rr0)));
+          if (!met) st[i].hp_not_converged++;
+        }
+      if (stats) stats[i] = st[i];
+    }
+  }
+  cleanup();
+  if (rc == TSM_ERR_NONFINITE) set_error("NaN/Inf in a solve");
+  return rc;
 }
 
 int tsm_combine(tsm_ctx* h, const double* per_corr, int n_hp, const double* per_lp, int n_lp, int n_entries,

@@ -103,6 +103,8 @@ void Ctx::free_all() {
   if (states) cudaFree(states);
   if (h_states) cudaFreeHost(h_states);
   if (d_lists) cudaFree(d_lists);
+  if (d_guard) cudaFree(d_guard);
+  d_guard = nullptr;
   if (h_lists) cudaFreeHost(h_lists);
   states = nullptr;
   h_states = nullptr;

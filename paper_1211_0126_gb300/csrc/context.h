@@ -61,11 +61,20 @@ struct Ctx {
   size_t red_cap = 0;
   CGState* states = nullptr;    // device, kMaxStates
   CGState* h_states = nullptr;  // pinned mirror
-  static constexpr int kMaxStates = 256;   // last 4 reserved for auxiliary reductions
+  static constexpr int kMaxStates = 2048;  // last 4 reserved for auxiliary reductions
   static constexpr int kMaxBatch = 64;     // right-hand sides per batched solve
-  int* d_lists = nullptr;       // device: 3 lists of kMaxStates right-hand-side indices
+  static constexpr int kMaxGuards = 256;   // while-loop iteration guards of one captured graph
+  int* d_lists = nullptr;       // device: 3 lists of kMaxBatch right-hand-side indices
   int* h_lists = nullptr;       // pinned staging of the lists
+  int* d_guard = nullptr;       // device iteration counters of captured while-loops
   int batch_cap = 1;            // batch width the solver workspace is laid out for
+  // graph capture: solves become graph while-loops on `stream`, their bodies
+  // are captured on `body_stream`, states are taken from `next_state` onwards
+  bool capturing = false;
+  cudaStream_t body_stream = nullptr;
+  int next_state = 0;
+  int next_guard = 0;
+  std::vector<std::pair<int, int>> cap_lp, cap_hp;   // (first state, count) of captured solves
   // instrumentation
   bool profile = false;
   struct EvRec {

@@ -182,6 +182,14 @@ template int launch_contract<double, F64, F32>(Ctx&, const ContractPlan&, const 
 template int launch_contract<float, F32, F64>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
                                               const EOField*, double2*);
 
+int reserve_contract(Ctx& c) {
+  constexpr int NT = ContractNT<double>::value;   // the smaller block: the most partials
+  const int vs2 = c.lat.L[0] * c.lat.L[1] * c.lat.L[2] / 2;
+  const int nbx = (vs2 + NT - 1) / NT;
+  void* part = nullptr;
+  return c.buffer("contract_partial", (size_t)c.lat.L[3] * 2 * nbx * CT_MAXG * CT_MAXQ * sizeof(double2), &part);
+}
+
 int launch_combine(Ctx& c, const double2* corr, int n_hp, const double2* lp, int n_lp, int E, double2* est,
                    double* err, double2* lp_mean, double2* corr_mean) {
   if (E <= 0) return TSM_OK;

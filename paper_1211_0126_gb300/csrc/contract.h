@@ -24,6 +24,9 @@ template <class R, class SA, class SB>
 int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint32_t source, EOField a,
                     const EOField* b, double2* out);
 
+// allocate the block-partial buffer of the largest contraction launch
+int reserve_contract(Ctx& c);
+
 int launch_combine(Ctx& c, const double2* corr, int n_hp, const double2* lp, int n_lp, int E, double2* est,
                    double* err, double2* lp_mean, double2* corr_mean);
 

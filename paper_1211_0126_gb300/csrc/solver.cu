@@ -46,9 +46,9 @@ static int read_states(Ctx& c, int s0, int n, std::vector<CGState>& out) {
 
 // copy a host list of right-hand-side indices to device list `which` (0..2)
 static int upload_list(Ctx& c, int which, const std::vector<int>& list, const int** dev) {
-  int* h = c.h_lists + which * Ctx::kMaxStates;
+  int* h = c.h_lists + which * Ctx::kMaxBatch;
   for (size_t k = 0; k < list.size(); ++k) h[k] = list[k];
-  int* d = c.d_lists + which * Ctx::kMaxStates;
+  int* d = c.d_lists + which * Ctx::kMaxBatch;
   if (!list.empty())
     TSM_CUDA(cudaMemcpyAsync(d, h, list.size() * sizeof(int), cudaMemcpyHostToDevice, c.stream));
   *dev = d;
@@ -108,6 +108,67 @@ static int normal_residual_f64(Ctx& c, PField x, PField b, PField r, CGState* st
   return launch_hop<F64>(c, h, 1, HOP_CENTER | HOP_NORM | HOP_BASE, -1, n);
 }
 
+// Graph while-loop over one batched solve: the condition starts at 1 (the body
+// runs at least once), and while_cond_kernel clears it once no source of the
+// batch is iterating (or after a guard of max_iter + 8 rounds).
+static __global__ void while_cond_kernel(const CGState* st, int n, cudaGraphConditionalHandle h, int* guard,
+                                         int max_rounds) {
+  if (threadIdx.x != 0) return;
+  bool any = false;
+  for (int k = 0; k < n; ++k)
+    if (!st[k].done && st[k].status == 0) any = true;
+  const int g = ++(*guard);
+  if (!any || g >= max_rounds) cudaGraphSetConditional(h, 0);
+}
+
+template <class Body>
+static int capture_while(Ctx& c, CGState* st, int n, int max_iter, Body&& body) {
+  if (c.next_guard >= Ctx::kMaxGuards) {
+    set_error("more than %d solves in one captured graph", Ctx::kMaxGuards);
+    return TSM_ERR_TOO_LARGE;
+  }
+  int* guard = c.d_guard + c.next_guard++;
+  TSM_CUDA(cudaMemsetAsync(guard, 0, sizeof(int), c.stream));
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  TSM_CUDA(cudaStreamGetCaptureInfo(c.stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) {
+    set_error("graph mode without an active stream capture");
+    return TSM_ERR_ARG;
+  }
+  cudaGraphConditionalHandle h;
+  TSM_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  TSM_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+  TSM_CUDA(cudaStreamUpdateCaptureDependencies(c.stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+  TSM_CUDA(cudaStreamBeginCaptureToGraph(c.body_stream, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  cudaStream_t outer = c.stream;
+  c.stream = c.body_stream;
+  int rc = body();
+  if (rc == TSM_OK) {
+    while_cond_kernel<<<1, 32, 0, c.stream>>>(st, n, h, guard, max_iter + 8);
+    c.launches++;
+    rc = check_launch(c, "while_cond_kernel");
+  }
+  c.stream = outer;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c.body_stream, &captured);
+  if (rc != TSM_OK) return rc;
+  if (e != cudaSuccess) {
+    set_error("capture of a while-loop body failed: %s", cudaGetErrorString(e));
+    return TSM_ERR_CUDA;
+  }
+  return TSM_OK;
+}
+
 // S: sloppy storage (links, p, t, w); SA: storage of r and x; SP: source /
 // solution storage (also used for bhat and the initial Dhat^dag bhat);
 // REL: FP32 iterations with an FP64 solution and FP64 residual replacement.
@@ -137,7 +198,7 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
   }
   // r0 = Dhat^dag bhat, <r0, r0> initialises the states
   const double delta = (stop.reliable_delta > 0.0) ? stop.reliable_delta : 0.1;
-  state_init_kernel<<<1, Ctx::kMaxStates, 0, c.stream>>>(st, nrhs, stop.rel_tol, stop.max_iter, REL ? 1 : 0,
+  state_init_kernel<<<1, Ctx::kMaxBatch, 0, c.stream>>>(st, nrhs, stop.rel_tol, stop.max_iter, REL ? 1 : 0,
                                                          delta * delta);
   c.launches++;
   TSM_TRY(check_launch(c, "state_init_kernel"));
@@ -240,15 +301,21 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
                                                                         c.sstride, dact, st);
       c.launches++;
       TSM_TRY(check_launch(c, "replace_residual_kernel"));
-      rel_finish_kernel<<<1, Ctx::kMaxStates, 0, c.stream>>>(st, dact, n);
+      rel_finish_kernel<<<1, Ctx::kMaxBatch, 0, c.stream>>>(st, dact, n);
       c.launches++;
       TSM_TRY(check_launch(c, "rel_finish_kernel"));
     }
     return TSM_OK;
   };
   std::vector<CGState> hs;
-  TSM_TRY(read_states(c, s0, nrhs, hs));
-  auto iterating = [&](int i) { return !hs[i].done && hs[i].status == 0; };
+  if (c.capturing) {
+    // graph mode: the iterations become a graph while-loop whose condition a
+    // device kernel clears once every source has met its stopping rule
+    TSM_TRY(capture_while(c, st, nrhs, stop.max_iter, [&]() { return iteration(nullptr, nrhs, false); }));
+  } else {
+    TSM_TRY(read_states(c, s0, nrhs, hs));
+  }
+  auto iterating = [&](int i) { return !c.capturing && !hs[i].done && hs[i].status == 0; };
   const int chunk = 8;
   long long launched = 0;   // guards the host loop against states that stop advancing
   for (;;) {
@@ -290,6 +357,7 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
     h.out = s.o.as<SP>();
     TSM_TRY(launch_hop<SP>(c, h, 0, HOP_CENTER, -1, nrhs));
   }
+  if (c.capturing) return TSM_OK;   // results are read from the states after the graph ran
   for (int i = 0; i < nrhs; ++i) {
     const CGState& q = hs[i];
     SolveResult& o = res[i];
@@ -300,6 +368,25 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
     else if (stop.rel_tol <= 0.0) o.converged = q.iter >= stop.max_iter;
     else o.converged = !(std::sqrt(q.rr) >= stop.rel_tol * std::sqrt(q.rr0));
   }
+  return TSM_OK;
+}
+
+// allocate every field cg_solve uses for this tier (batch width c.batch_cap),
+// so that a later solve makes no allocation (required under stream capture)
+int reserve_solver(Ctx& c, const tm_stop& stop) {
+  int pS, pA, pP;
+  switch (stop.prec) {
+    case TSM_F64: pS = pA = pP = TSM_F64; break;
+    case TSM_F32: pS = pA = TSM_F32; pP = stop.reliable ? TSM_F64 : TSM_F32; break;
+    default: pS = stop.prec; pA = pP = TSM_F32; break;
+  }
+  const int nb = c.batch_cap;
+  PField f;
+  for (const char* name : {"cg_tmp_o", "cg_bhat", "cg_w0", "cg_t0", "cg_r0"}) TSM_TRY(c.field(name, pP, &f, nb));
+  for (const char* name : {"cg_p", "cg_t", "cg_w"}) TSM_TRY(c.field(name, pS, &f, nb));
+  for (const char* name : {"cg_r", "cg_x"}) TSM_TRY(c.field(name, pA, &f, nb));
+  if (stop.prec == TSM_F32 && stop.reliable)
+    for (const char* name : {"cg_x64", "cg_r64", "rel_t", "rel_w"}) TSM_TRY(c.field(name, TSM_F64, &f, nb));
   return TSM_OK;
 }
 

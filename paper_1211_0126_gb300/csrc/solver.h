@@ -22,6 +22,9 @@ int solution_prec(const tm_stop& stop);
 // res receives nrhs results.
 int solve_batch(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EOField s, SolveResult* res);
 
+// Allocate the solver workspace of a tier for c.batch_cap sources in advance.
+int reserve_solver(Ctx& c, const tm_stop& stop);
+
 // ||b - D_tm s|| / ||b|| in FP64 (fields of tier prec).
 int true_residual(Ctx& c, int prec, EOField b, EOField s, double* out);
 

@@ -72,6 +72,8 @@ _SIGS = {
                                    ctypes.c_int]),
     "tsm_contract_noalloc": (ctypes.c_int, [ctypes.POINTER(TmLattice), ctypes.c_uint64, ctypes.c_int,
                                             ctypes.c_uint32, _P, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
+    "tsm_loops_graph": (ctypes.c_int, [_P, ctypes.POINTER(TsmParams), ctypes.c_int, _P, _P, _P, _P,
+                                       ctypes.POINTER(TsmLoopStats)]),
     "tsm_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "tsm_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
     "tsm_launch_count": (ctypes.c_longlong, [_P]),
@@ -273,6 +275,33 @@ def tsm_loops(h, p, loops=None, err=None, lp_mean=None, corr_mean=None, per_corr
     stats = TsmLoopStats()
     _check(library().tsm_loops(h, ctypes.byref(p), *[q for q, _ in ptrs], dev, ctypes.byref(stats)), "tsm_loops")
     return stats
+
+
+def tsm_loops_graph(handles, plist, loops=None, err=None, per_corr=None, per_lp=None):
+    """One CUDA graph over several contexts; outputs are lists of torch CUDA
+    tensors (or None) per context.  Returns the list of TsmLoopStats."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value for h in handles])
+    ps = (TsmParams * n)(*plist)
+
+    def ptr_array(arrs):
+        if arrs is None:
+            return None
+        vals = []
+        for a in arrs:
+            if a is None:
+                vals.append(None)
+                continue
+            p, dev = _ptr(a, True)
+            if dev != 1:
+                raise ValueError("tsm_loops_graph outputs must be device tensors")
+            vals.append(p.value)
+        return (ctypes.c_void_p * n)(*vals)
+
+    stats = (TsmLoopStats * n)()
+    _check(library().tsm_loops_graph(hs, ps, n, ptr_array(loops), ptr_array(err), ptr_array(per_corr),
+                                     ptr_array(per_lp), stats), "tsm_loops_graph")
+    return list(stats)
 
 
 def tsm_combine(h, per_corr, per_lp, n_entries, loops=None, err=None, lp_mean=None, corr_mean=None):

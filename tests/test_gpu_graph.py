@@ -1,0 +1,69 @@
+"""One captured CUDA graph over three lattices (tsm_loops_graph).
+
+Each lattice has its own context; every batched CG solve runs as a graph
+while-loop (device-side stopping rule, converged sources skipped) and the
+three lattices are parallel branches of one graph.  The results must be
+bit-identical to the eager tsm_loops of each context with the same
+parameters (same kernels, same per-source arithmetic and reduction order).
+"""
+import numpy as np
+import pytest
+
+from paper_1211_0126_gb300 import synthetic as S
+from paper_1211_0126_gb300 import tsm
+
+pytestmark = pytest.mark.gpu
+
+KAPPA, MU = 0.1245, 0.005
+LATTICES = [(4, 4, 4, 4), (6, 4, 4, 6), (8, 4, 4, 8)]
+GAM = list(range(16))
+MOMS = S.default_momenta(7)
+
+
+@pytest.mark.parametrize("tier", ["mixed", "fp64"])
+def test_graph_over_three_lattices_bit_identical(libtsm, tier):
+    import torch
+    if tier == "mixed":
+        hp = tsm.stop(1e-10, 3000, tsm.TSM_F32, reliable=True, reliable_delta=1e-3)
+        lp = tsm.stop(5e-3, 60, tsm.TSM_F16)
+    else:
+        hp = tsm.stop(1e-12, 3000, tsm.TSM_F64)
+        lp = tsm.stop(1e-2, 60, tsm.TSM_F64)
+    n_hp, n_lp, batch = 4, 21, 8
+    ctxs = [tsm.Context(0) for _ in LATTICES]
+    try:
+        eager, plist, outs = [], [], []
+        for k, (ctx, dims) in enumerate(zip(ctxs, LATTICES)):
+            ctx.load_gauge(S.gauge_field(dims, 0.25, 40 + k), dims, KAPPA, MU)
+            eager.append(ctx.loops(500 + k, 4, n_hp, n_lp, hp, lp, GAM, MOMS, per_source=True, batch=batch,
+                                   verify=False))
+            plist.append(tsm.params(500 + k, 4, (0, n_hp), (n_hp, n_hp + n_lp), hp, lp, GAM, MOMS,
+                                    batch=batch))
+            shape = (len(GAM), len(MOMS), dims[3])
+            outs.append({
+                "loops": torch.zeros(shape, dtype=torch.complex128, device="cuda"),
+                "err": torch.zeros(shape, dtype=torch.float64, device="cuda"),
+                "per_corr": torch.zeros((n_hp,) + shape, dtype=torch.complex128, device="cuda"),
+                "per_lp": torch.zeros((n_lp,) + shape, dtype=torch.complex128, device="cuda"),
+            })
+        stats = tsm.tsm_loops_graph([c.h for c in ctxs], plist,
+                                    loops=[o["loops"] for o in outs], err=[o["err"] for o in outs],
+                                    per_corr=[o["per_corr"] for o in outs], per_lp=[o["per_lp"] for o in outs])
+        torch.cuda.synchronize()
+        for k in range(len(LATTICES)):
+            for key in ("loops", "err", "per_corr", "per_lp"):
+                got = outs[k][key].cpu().numpy()
+                assert np.array_equal(got, eager[k][key]), (k, key)
+            assert stats[k].lp_iters == eager[k]["stats"]["lp_iters"]
+            assert stats[k].hp_iters == eager[k]["stats"]["hp_iters"]
+            assert stats[k].hp_not_converged == 0
+        # the graph can be built and run again (fresh seeds) on the same contexts
+        plist2 = [tsm.params(900 + k, 4, (0, n_hp), (n_hp, n_hp + n_lp), hp, lp, GAM, MOMS, batch=batch)
+                  for k in range(len(LATTICES))]
+        tsm.tsm_loops_graph([c.h for c in ctxs], plist2, loops=[o["loops"] for o in outs])
+        torch.cuda.synchronize()
+        ref = ctxs[1].loops(901, 4, n_hp, n_lp, hp, lp, GAM, MOMS, batch=batch, verify=False)
+        assert np.array_equal(outs[1]["loops"].cpu().numpy(), ref["loops"])
+    finally:
+        for c in ctxs:
+            c.close()
