@@ -36,7 +36,7 @@ DIMS = (24, 24, 24, 48)
 EPS, KAPPA, MU, GAUGE_SEED = 0.25, 0.1245, 0.005, 3
 N_HP, N_LP = 8, 256
 HP_TOL, LP_TOL, LP_MAXIT, HP_MAXIT = 1e-10, 5e-3, 60, 20000
-RELIABLE_DELTA = 1e-3        # FP64 residual replacement whenever ||r|| fell by 1000x
+RELIABLE_DELTA = 1e-4        # FP64 residual replacement whenever ||r|| fell by 10^4
 TIERS = {0: "f64", 1: "f32", 2: "bf16", 3: "f16"}
 KINDS = ("K1_hop", "K2_hop_xpay_norm", "K3_hop_dag", "K4_hop_dag_cg_update")
 N_GAMMA, N_Q = 16, 7
@@ -52,6 +52,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / equal-error / cpu-baseline legs")
     ap.add_argument("--batch", type=int, default=32, help="sources solved together (multi-RHS kernels)")
+    ap.add_argument("--reliable-delta", type=float, default=None, help="override the HP reliable-update delta")
+    ap.add_argument("--mode", default="eager", choices=["eager", "graph"],
+                    help="eager: host-driven chunked CG loops; graph: one captured CUDA graph per step "
+                         "(device-side loops, LP set beside the HP set)")
+    ap.add_argument("--workload", default="tsm24", choices=["tsm24", "three-lattice"],
+                    help="tsm24: the headline 24^3x48 TSM step; three-lattice: 8^3x16 + 12^3x24 + 16^3x32 "
+                         "in one captured graph (batching workload, its own JSON line)")
     ap.add_argument("--dslash-only", default=None,
                     help="comma list of tiers (f64,f32,f16,bf16): only run 3 standalone H_eo launches per tier "
                          "at 24^3x48 (a small case for ncu captures of the hop kernel)")
@@ -276,7 +283,8 @@ def run_ours(args):
     ctx = tsm.Context(local, stream.cuda_stream)
     ctx.load_gauge(U, DIMS, KAPPA, MU)
     gam, moms = list(range(N_GAMMA)), S.default_momenta(N_Q)
-    hp_stop = tsm.stop(HP_TOL, HP_MAXIT, tsm.TSM_F32, reliable=True, reliable_delta=RELIABLE_DELTA)
+    rdelta = args.reliable_delta if args.reliable_delta else RELIABLE_DELTA
+    hp_stop = tsm.stop(HP_TOL, HP_MAXIT, tsm.TSM_F32, reliable=True, reliable_delta=rdelta)
     lp_stop = tsm.stop(LP_TOL, LP_MAXIT, tsm.TSM_F16)
     hp_range, lp_range = replicas.source_ranges(N_HP, N_LP, rank, world)
     E = N_GAMMA * N_Q * DIMS[3]
@@ -289,6 +297,9 @@ def run_ours(args):
 
     def step(seed, verify=False):
         p = tsm.params(seed, 4, hp_range, lp_range, hp_stop, lp_stop, gam, moms, batch=args.batch, verify=verify)
+        if args.mode == "graph" and not verify:
+            return tsm.tsm_loops_graph([ctx.h], [p], loops=[d_loops], err=[d_err], per_corr=[d_pc],
+                                       per_lp=[d_pl])[0]
         return tsm.tsm_loops(ctx.h, p, d_loops, d_err, None, None, d_pc, d_pl)
 
     warm = None
@@ -349,7 +360,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "lattice": list(DIMS), "n_hp_per_gpu": N_HP, "n_lp_per_gpu": N_LP,
-                       "batch": args.batch, "reliable_delta": RELIABLE_DELTA,
+                       "batch": args.batch, "reliable_delta": rdelta, "mode": args.mode,
                        "l2": "flushed between steps (256 MB write)",
                        "lp_iters_per_source": st.lp_iters / float(N_HP + N_LP),
                        "hp_iters_per_source": st.hp_iters / float(N_HP),
@@ -463,12 +474,79 @@ def equal_error(ctx, tsm, S, d_pc, d_pl, step_ms, stream):
     return out
 
 
+def run_three_lattice(args):
+    """Batching workload: three lattices (8^3x16, 12^3x24, 16^3x32; links
+    eps = 0.25, kappa = 0.1245, mu = 0.005), per lattice N_LP = 512 BF16 LP
+    solves at 1e-2 and N_HP = 16 FP32+FP64 HP solves at 1e-10, batch widths
+    from the autotuner, all three TSM estimates in one captured CUDA graph.
+    Reports sources/s of the graph and of the same work run eagerly."""
+    import torch
+    from paper_1211_0126_gb300 import build, tsm
+    from paper_1211_0126_gb300 import synthetic as S
+    if not os.path.exists(tsm.LIB_PATH):
+        build.build()
+    lattices = [(8, 8, 8, 16), (12, 12, 12, 24), (16, 16, 16, 32)]
+    n_hp, n_lp = 16, 512
+    hp = tsm.stop(1e-10, HP_MAXIT, tsm.TSM_F32, reliable=True, reliable_delta=RELIABLE_DELTA)
+    lp = tsm.stop(1e-2, 500, tsm.TSM_BF16)
+    gam, moms = list(range(N_GAMMA)), S.default_momenta(N_Q)
+    ctxs, widths, tune = [], [], {}
+    for k, dims in enumerate(lattices):
+        ctx = tsm.Context(0)
+        ctx.load_gauge(S.gauge_field(dims, EPS, 100 + k), dims, KAPPA, MU)
+        best, times = tsm.tsm_tune_batch(ctx.h, lp)
+        ctxs.append(ctx)
+        widths.append(best)
+        tune["x".join(map(str, dims))] = {"batch": best, "ms_per_source": dict(zip(["8", "16", "32", "64"],
+                                                                                  [float(t) for t in times]))}
+    outs = [torch.zeros((len(gam), len(moms), d[3]), dtype=torch.complex128, device="cuda") for d in lattices]
+
+    def plist(seed):
+        return [tsm.params(seed + k, 4, (0, n_hp), (n_hp, n_hp + n_lp), hp, lp, gam, moms, batch=widths[k])
+                for k in range(len(lattices))]
+
+    def graph_step(seed):
+        return tsm.tsm_loops_graph([c.h for c in ctxs], plist(seed), loops=outs)
+
+    def eager_step(seed):
+        for k, c in enumerate(ctxs):
+            tsm.tsm_loops(c.h, plist(seed)[k], outs[k])
+
+    res = {}
+    for name, fn in (("graph", graph_step), ("eager", eager_step)):
+        for w in range(args.warmup):
+            fn(1000 + w)
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(args.steps):
+            t0 = time.perf_counter()
+            fn(2000 + k)
+            torch.cuda.synchronize()
+            ms.append((time.perf_counter() - t0) * 1e3)
+        res[name] = {"ms_per_step": float(np.mean(ms)),
+                     "sources_per_s": 3 * (n_hp + n_lp) / (float(np.mean(ms)) * 1e-3)}
+    st = graph_step(3000)
+    line = {"metric": "TSM sources/sec, three lattices in one captured graph", "value": res["graph"]["sources_per_s"],
+            "unit": "sources/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["graph"]["ms_per_step"], "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "three-lattice 8^3x16+12^3x24+16^3x32, per lattice hp16(f32+f64rel,1e-10) "
+                                   "lp512(bf16,1e-2)", "autotune": tune,
+                       "lp_iters_per_source": [s.lp_iters / float(n_hp + n_lp) for s in st],
+                       "hp_iters_per_source": [s.hp_iters / float(n_hp) for s in st]},
+            "eager": res["eager"], "graph_speedup": res["eager"]["ms_per_step"] / res["graph"]["ms_per_step"]}
+    print(json.dumps(line), flush=True)
+    for c in ctxs:
+        c.close()
+
+
 def main():
     args = parse()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.dslash_only:
         run_dslash_only(args.dslash_only)
+    elif args.workload == "three-lattice":
+        run_three_lattice(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -215,6 +215,14 @@ int tsm_loops(tsm_ctx* ctx, const tsm_params* p,
 int tsm_loops_graph(tsm_ctx** ctxs, const tsm_params* params, int n, double** loops, double** err,
                     double** per_corr, double** per_lp, tsm_loop_stats* stats);
 
+/* Autotuner of the multi-RHS batch width: for the loaded lattice and the
+ * stopping rule / tier `stop`, times one batched solve of noise sources (a
+ * scratch seed; nothing else is changed) for every width in {8, 16, 32, 64}
+ * and writes the width with the lowest time per source to *best.  Results
+ * are cached per context, lattice and tier.  times_ms (may be NULL) receives
+ * the 4 measured times per source in milliseconds. */
+int tsm_tune_batch(tsm_ctx* ctx, const tm_stop* stop, int* best, double* times_ms);
+
 /* Combine per-source loops gathered from several processes into the estimate
  * of Eq. 2.4.  Runs the same device kernel, in the same summation order, as
  * the final step of tsm_loops, so any split of the source ranges gives

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI (include/tsm.h).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -178,9 +179,11 @@ struct TsmRun {
   double2* d_corr = nullptr;
   double2* d_lp = nullptr;
   EOField b_lp, s_lp, b_hp, s_hp;
+  bool branch = false;   // LP set recorded as a second graph branch
+  EOField b_lp1, s_lp1;  // its source / solution batches
 };
 
-int prepare_run(Ctx& c, const tsm_params* p, TsmRun* run) {
+int prepare_run(Ctx& c, const tsm_params* p, TsmRun* run, bool branch = false) {
   if (!c.has_gauge) return bad(TSM_ERR_NO_GAUGE, "no gauge field loaded");
   if (p->noise != 4 && p->noise != 2) return bad(TSM_ERR_ARG, "noise kind must be 4 or 2");
   if (p->hp_end < p->hp_begin || p->lp_end < p->lp_begin) return bad(TSM_ERR_ARG, "empty-reversed source range");
@@ -210,6 +213,27 @@ int prepare_run(Ctx& c, const tsm_params* p, TsmRun* run) {
   TSM_TRY(reserve_solver(c, p->lp));
   TSM_TRY(reserve_solver(c, p->hp));
   TSM_TRY(reserve_contract(c));
+  run->branch = branch && run->n_hp > 0 && run->n_lp > 0;
+  if (run->branch) {
+    // the LP-set branch gets its own workspace and reduction slots
+    c.ws_prefix = "branch1/";
+    int rc = eo_fields(c, "tsm_b_lp", run->sp_lp, &run->b_lp1, c.batch_cap);
+    if (rc == TSM_OK) rc = eo_fields(c, "tsm_s_lp", run->sp_lp, &run->s_lp1, c.batch_cap);
+    if (rc == TSM_OK) rc = reserve_solver(c, p->lp);
+    if (rc == TSM_OK) rc = reserve_contract(c);
+    c.ws_prefix.clear();
+    TSM_TRY(rc);
+    if (c.red_branch.partials == nullptr || c.red_branch_cap != c.red_cap) {
+      if (c.red_branch.partials) cudaFree(c.red_branch.partials);
+      if (c.red_branch.counter) cudaFree(c.red_branch.counter);
+      c.red_branch = RedSlot{};
+      TSM_CUDA(cudaMalloc(&c.red_branch.partials, Ctx::kMaxBatch * c.red_cap * sizeof(double)));
+      TSM_CUDA(cudaMalloc(&c.red_branch.counter, Ctx::kMaxBatch * sizeof(unsigned int)));
+      TSM_CUDA(cudaMemset(c.red_branch.counter, 0, Ctx::kMaxBatch * sizeof(unsigned int)));
+      c.red_branch.stride = (int)c.red_cap;
+      c.red_branch_cap = c.red_cap;
+    }
+  }
   return TSM_OK;
 }
 
@@ -248,6 +272,35 @@ int record_run(Ctx& c, const tsm_params* p, TsmRun& run, tsm_loop_stats* st) {
     return s0;
   };
   std::vector<SolveResult> r_lp(B), r_hp(B);
+  const bool hp_first = !(c.capturing && run.branch);
+  if (!hp_first) {
+    // graph branch: the LP set runs beside the HP set (the FP64-heavy HP
+    // solves and the 16-bit LP solves load different units of the GPU)
+    TSM_CUDA(cudaEventRecord(c.fork_ev, c.stream));
+    TSM_CUDA(cudaStreamWaitEvent(c.branch_stream, c.fork_ev, 0));
+    cudaStream_t main_stream = c.stream;
+    const RedSlot main_red = c.red;
+    c.stream = c.branch_stream;
+    c.red = c.red_branch;
+    c.ws_prefix = "branch1/";
+    std::vector<SolveResult> r_lp1(B);
+    std::swap(r_lp, r_lp1);
+    int rc = TSM_OK;
+    for (uint32_t j0 = p->lp_begin; j0 < p->lp_end && rc == TSM_OK; j0 += B) {
+      const int n = (int)std::min<uint32_t>(B, p->lp_end - j0);
+      rc = gen(sp_lp, j0, run.b_lp1, n);
+      if (rc == TSM_OK) rc = solve_batch(c, p->lp, slots(n, c.cap_lp), n, run.b_lp1, run.s_lp1, r_lp.data());
+      for (int r = 0; r < n && rc == TSM_OK; ++r)
+        rc = contract(j0 + r, eo_at(run.s_lp1, sp_lp, c.g.Vh, r), sp_lp, nullptr, sp_lp,
+                      run.d_lp + (size_t)(j0 + r - p->lp_begin) * E);
+    }
+    std::swap(r_lp, r_lp1);
+    if (rc == TSM_OK && cudaEventRecord(c.join_ev, c.stream) != cudaSuccess) rc = TSM_ERR_CUDA;
+    c.stream = main_stream;
+    c.red = main_red;
+    c.ws_prefix.clear();
+    TSM_TRY(rc);
+  }
   // HP set: the LP map and the HP solve of every source, then L(s_HP - s_LP)
   for (uint32_t j0 = p->hp_begin; j0 < p->hp_end; j0 += B) {
     const int n = (int)std::min<uint32_t>(B, p->hp_end - j0);
@@ -274,20 +327,27 @@ int record_run(Ctx& c, const tsm_params* p, TsmRun& run, tsm_loop_stats* st) {
     }
   }
   // LP set: the same LP map, L(s_LP)
-  for (uint32_t j0 = p->lp_begin; j0 < p->lp_end; j0 += B) {
-    const int n = (int)std::min<uint32_t>(B, p->lp_end - j0);
-    TSM_TRY(gen(sp_lp, j0, run.b_lp, n));
-    TSM_TRY(solve_batch(c, p->lp, slots(n, c.cap_lp), n, run.b_lp, run.s_lp, r_lp.data()));
-    for (int r = 0; r < n; ++r) {
-      if (!c.capturing) {
-        if (r_lp[r].status != TSM_OK) return bad(TSM_ERR_NONFINITE, "NaN/Inf in a solve");
-        st->lp_iters += r_lp[r].iters;
+  auto lp_set = [&](EOField bl, EOField sl) -> int {
+    for (uint32_t j0 = p->lp_begin; j0 < p->lp_end; j0 += B) {
+      const int n = (int)std::min<uint32_t>(B, p->lp_end - j0);
+      TSM_TRY(gen(sp_lp, j0, bl, n));
+      TSM_TRY(solve_batch(c, p->lp, slots(n, c.cap_lp), n, bl, sl, r_lp.data()));
+      for (int r = 0; r < n; ++r) {
+        if (!c.capturing) {
+          if (r_lp[r].status != TSM_OK) return bad(TSM_ERR_NONFINITE, "NaN/Inf in a solve");
+          st->lp_iters += r_lp[r].iters;
+        }
+        TSM_TRY(contract(j0 + r, eo_at(sl, sp_lp, c.g.Vh, r), sp_lp, nullptr, sp_lp,
+                         run.d_lp + (size_t)(j0 + r - p->lp_begin) * E));
       }
-      TSM_TRY(contract(j0 + r, eo_at(run.s_lp, sp_lp, c.g.Vh, r), sp_lp, nullptr, sp_lp,
-                       run.d_lp + (size_t)(j0 + r - p->lp_begin) * E));
     }
+    return TSM_OK;
+  };
+  if (!hp_first) {
+    TSM_CUDA(cudaStreamWaitEvent(c.stream, c.join_ev, 0));   // join the LP-set branch
+    return TSM_OK;
   }
-  return TSM_OK;
+  return lp_set(run.b_lp, run.s_lp);
 }
 
 }  // namespace
@@ -597,19 +657,24 @@ int tsm_loops_graph(tsm_ctx** ctxs, const tsm_params* params, int n, double** lo
   Ctx& c0 = ctxs[0]->c;
   TSM_TRY(select_device(c0));
   std::vector<TsmRun> runs(n);
-  for (int i = 0; i < n; ++i) TSM_TRY(prepare_run(ctxs[i]->c, params + i, &runs[i]));
+  for (int i = 0; i < n; ++i) TSM_TRY(prepare_run(ctxs[i]->c, params + i, &runs[i], /*branch=*/true));
   for (int i = 0; i < n; ++i) TSM_CUDA(cudaStreamSynchronize(ctxs[i]->c.stream));
   // private streams for the capture (one branch per context + one for loop bodies)
-  std::vector<cudaStream_t> own(2 * n + 1, nullptr);
+  // own[0]: origin; per context i: own[1+3i] main branch, own[2+3i] loop
+  // bodies, own[3+3i] LP-set branch; evs[n]: fork of the origin, evs[n+1+2i],
+  // evs[n+2+2i]: fork / join of the LP-set branch of context i
+  std::vector<cudaStream_t> own(3 * n + 1, nullptr);
   std::vector<cudaStream_t> saved(n);
-  std::vector<cudaEvent_t> evs(n + 1, nullptr);
+  std::vector<cudaEvent_t> evs(3 * n + 1, nullptr);
   int rc = TSM_OK;
   auto cleanup = [&]() {
     for (int i = 0; i < n; ++i) {
       Ctx& c = ctxs[i]->c;
-      if (own[1 + 2 * i]) c.stream = saved[i];
+      if (own[1 + 3 * i]) c.stream = saved[i];
       c.capturing = false;
       c.body_stream = nullptr;
+      c.branch_stream = nullptr;
+      c.fork_ev = c.join_ev = nullptr;
     }
     for (auto s : own)
       if (s) cudaStreamDestroy(s);
@@ -632,8 +697,11 @@ int tsm_loops_graph(tsm_ctx** ctxs, const tsm_params* params, int n, double** lo
   for (int i = 0; i < n && rc == TSM_OK; ++i) {
     Ctx& c = ctxs[i]->c;
     saved[i] = c.stream;
-    c.stream = own[1 + 2 * i];
-    c.body_stream = own[2 + 2 * i];
+    c.stream = own[1 + 3 * i];
+    c.body_stream = own[2 + 3 * i];
+    c.branch_stream = own[3 + 3 * i];
+    c.fork_ev = evs[n + 1 + 2 * i];
+    c.join_ev = evs[n + 2 + 2 * i];
     c.capturing = true;
     c.next_state = 0;
     c.next_guard = 0;
@@ -740,6 +808,67 @@ int tsm_combine(tsm_ctx* h, const double* per_corr, int n_hp, const double* per_
   if (lp_mean) TSM_TRY(stage_out_finish(c, lp_mean, d_lpm, cb, on_device));
   if (corr_mean) TSM_TRY(stage_out_finish(c, corr_mean, d_cm, cb, on_device));
   TSM_CUDA(cudaStreamSynchronize(c.stream));
+  return TSM_OK;
+}
+
+int tsm_tune_batch(tsm_ctx* h, const tm_stop* stop, int* best, double* times_ms) {
+  if (h == nullptr || best == nullptr) return bad(TSM_ERR_ARG, "null argument");
+  TSM_TRY(check_stop(stop));
+  Ctx& c = h->c;
+  if (!c.has_gauge) return bad(TSM_ERR_NO_GAUGE, "no gauge field loaded");
+  TSM_TRY(select_device(c));
+  char key[160];
+  snprintf(key, sizeof(key), "%dx%dx%dx%d/p%d/r%d/t%g/m%d", c.lat.L[0], c.lat.L[1], c.lat.L[2], c.lat.L[3],
+           stop->prec, stop->reliable, stop->rel_tol, stop->max_iter);
+  const int cand[4] = {8, 16, 32, 64};
+  auto it = c.tuned_batch.find(key);
+  if (it != c.tuned_batch.end() && times_ms == nullptr) {
+    *best = it->second;
+    return TSM_OK;
+  }
+  const int sp = solution_prec(*stop);
+  c.batch_cap = std::max(c.batch_cap, cand[3]);
+  EOField fb, fs;
+  TSM_TRY(eo_fields(c, "tune_b", sp, &fb, c.batch_cap));
+  TSM_TRY(eo_fields(c, "tune_s", sp, &fs, c.batch_cap));
+  TSM_TRY(reserve_solver(c, *stop));
+  const NoiseSpec ns = make_noise(0x7475ull, 4);   // scratch sources, not part of any estimate
+  cudaEvent_t e0, e1;
+  TSM_CUDA(cudaEventCreate(&e0));
+  TSM_CUDA(cudaEventCreate(&e1));
+  std::vector<SolveResult> res(cand[3]);
+  double best_t = 1e300;
+  int best_w = cand[0];
+  int rc = TSM_OK;
+  for (int k = 0; k < 4 && rc == TSM_OK; ++k) {
+    const int w = cand[k];
+    rc = dispatch_prec(sp, [&](auto tag) {
+      using S = decltype(tag);
+      TSM_TRY(launch_noise<S>(c, 0, ns, 0, fb.e, w));
+      return launch_noise<S>(c, 1, ns, 0, fb.o, w);
+    });
+    if (rc != TSM_OK) break;
+    // one untimed solve to settle caches and clocks, then one timed
+    rc = solve_batch(c, *stop, 0, w, fb, fs, res.data());
+    if (rc != TSM_OK) break;
+    if (cudaEventRecord(e0, c.stream) != cudaSuccess) rc = TSM_ERR_CUDA;
+    if (rc == TSM_OK) rc = solve_batch(c, *stop, 0, w, fb, fs, res.data());
+    if (rc == TSM_OK && cudaEventRecord(e1, c.stream) != cudaSuccess) rc = TSM_ERR_CUDA;
+    if (rc == TSM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = TSM_ERR_CUDA;
+    float ms = 0.f;
+    if (rc == TSM_OK) cudaEventElapsedTime(&ms, e0, e1);
+    const double per = ms / w;
+    if (times_ms) times_ms[k] = per;
+    if (per < best_t) {
+      best_t = per;
+      best_w = w;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != TSM_OK) return rc;
+  c.tuned_batch[key] = best_w;
+  *best = best_w;
   return TSM_OK;
 }
 

@@ -51,11 +51,16 @@ int check_launch(Ctx& c, const char* what) {
   return TSM_OK;
 }
 
-int Ctx::buffer(const std::string& name, size_t bytes, void** out) {
+int Ctx::buffer(const std::string& base_name, size_t bytes, void** out) {
+  const std::string name = ws_prefix + base_name;
   auto it = ws.find(name);
   if (it != ws.end() && it->second.second >= bytes) {
     *out = it->second.first;
     return TSM_OK;
+  }
+  if (capturing) {
+    set_error("workspace '%s' was not reserved before graph capture", name.c_str());
+    return TSM_ERR_ARG;
   }
   if (it != ws.end()) {
     TSM_CUDA(cudaStreamSynchronize(stream));
@@ -99,6 +104,9 @@ void Ctx::free_all() {
   }
   if (red.partials) cudaFree(red.partials);
   if (red.counter) cudaFree(red.counter);
+  if (red_branch.partials) cudaFree(red_branch.partials);
+  if (red_branch.counter) cudaFree(red_branch.counter);
+  red_branch = RedSlot{};
   red = RedSlot{};
   if (states) cudaFree(states);
   if (h_states) cudaFreeHost(h_states);

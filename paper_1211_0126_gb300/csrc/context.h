@@ -72,9 +72,17 @@ struct Ctx {
   // are captured on `body_stream`, states are taken from `next_state` onwards
   bool capturing = false;
   cudaStream_t body_stream = nullptr;
+  // second branch of a captured run (the LP set beside the HP set): its own
+  // stream, workspace (names prefixed by ws_prefix) and reduction slots
+  cudaStream_t branch_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  std::string ws_prefix;
+  RedSlot red_branch{};
+  size_t red_branch_cap = 0;
   int next_state = 0;
   int next_guard = 0;
   std::vector<std::pair<int, int>> cap_lp, cap_hp;   // (first state, count) of captured solves
+  std::map<std::string, int> tuned_batch;            // autotuner cache: lattice + tier -> batch width
   // instrumentation
   bool profile = false;
   struct EvRec {

@@ -74,6 +74,7 @@ _SIGS = {
                                             ctypes.c_uint32, _P, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
     "tsm_loops_graph": (ctypes.c_int, [_P, ctypes.POINTER(TsmParams), ctypes.c_int, _P, _P, _P, _P,
                                        ctypes.POINTER(TsmLoopStats)]),
+    "tsm_tune_batch": (ctypes.c_int, [_P, ctypes.POINTER(TmStop), ctypes.POINTER(ctypes.c_int), _P]),
     "tsm_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "tsm_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
     "tsm_launch_count": (ctypes.c_longlong, [_P]),
@@ -312,6 +313,16 @@ def tsm_combine(h, per_corr, per_lp, n_entries, loops=None, err=None, lp_mean=No
     dev = _same_side(*[d for _, d in ins + outs])
     return _check(library().tsm_combine(h, ins[0][0], n_hp, ins[1][0], n_lp, int(n_entries),
                                         *[q for q, _ in outs], dev), "tsm_combine")
+
+
+def tsm_tune_batch(h, stp):
+    """Autotuned multi-RHS batch width for the loaded lattice and tier:
+    returns (best width, per-source ms for widths 8, 16, 32, 64)."""
+    best = ctypes.c_int(0)
+    times = np.zeros(4)
+    _check(library().tsm_tune_batch(h, ctypes.byref(stp), ctypes.byref(best), ctypes.c_void_p(times.ctypes.data)),
+           "tsm_tune_batch")
+    return best.value, times
 
 
 def tsm_profile(h, enable):

@@ -67,3 +67,34 @@ def test_graph_over_three_lattices_bit_identical(libtsm, tier):
     finally:
         for c in ctxs:
             c.close()
+
+
+def test_autotuner_and_config_sizes_graph_matches_eager(libtsm):
+    """The three lattices of the batching workload (8^3x16, 12^3x24, 16^3x32,
+    links eps = 0.25, kappa = 0.1245, mu = 0.005, BF16 LP at 1e-2, FP32+FP64
+    HP at 1e-10) with autotuned batch widths: one graph equals the eager runs
+    bit for bit (fewer sources than the benchmark to keep the test short)."""
+    import torch
+    lattices = [(8, 8, 8, 16), (12, 12, 12, 24), (16, 16, 16, 32)]
+    hp = tsm.stop(1e-10, 3000, tsm.TSM_F32, reliable=True, reliable_delta=1e-3)
+    lp = tsm.stop(1e-2, 200, tsm.TSM_BF16)
+    n_hp, n_lp = 4, 40
+    ctxs = [tsm.Context(0) for _ in lattices]
+    try:
+        plist, outs, eager = [], [], []
+        for k, (ctx, dims) in enumerate(zip(ctxs, lattices)):
+            ctx.load_gauge(S.gauge_field(dims, 0.25, 60 + k), dims, KAPPA, MU)
+            best, times = tsm.tsm_tune_batch(ctx.h, lp)
+            assert best in (8, 16, 32, 64) and np.all(times > 0)
+            assert times[[8, 16, 32, 64].index(best)] == times.min()
+            eager.append(ctx.loops(700 + k, 4, n_hp, n_lp, hp, lp, GAM, MOMS, per_source=True, batch=best,
+                                   verify=False))
+            plist.append(tsm.params(700 + k, 4, (0, n_hp), (n_hp, n_hp + n_lp), hp, lp, GAM, MOMS, batch=best))
+            outs.append(torch.zeros((n_lp, len(GAM), len(MOMS), dims[3]), dtype=torch.complex128, device="cuda"))
+        tsm.tsm_loops_graph([c.h for c in ctxs], plist, per_lp=outs)
+        torch.cuda.synchronize()
+        for k in range(len(lattices)):
+            assert np.array_equal(outs[k].cpu().numpy(), eager[k]["per_lp"]), k
+    finally:
+        for c in ctxs:
+            c.close()
