@@ -223,6 +223,15 @@ int tsm_loops_graph(tsm_ctx** ctxs, const tsm_params* params, int n, double** lo
  * the 4 measured times per source in milliseconds. */
 int tsm_tune_batch(tsm_ctx* ctx, const tm_stop* stop, int* best, double* times_ms);
 
+/* Tensor-core GEMM of the learned preconditioner's channel mixing (the dense
+ * contraction of the parallel-transport layers; the paper has no network --
+ * this is the project's learned LP preconditioner):
+ *   C[M][N] (FP32) = A[M][K] (BF16) * B[N][K]^T (BF16)  (+ C when beta = 1),
+ * all row-major DEVICE pointers, K % 8 == 0, computed with tcgen05.mma
+ * (accumulator in tensor memory), ordered on cuda_stream and completed on
+ * return.  TSM_ERR_TIMEOUT if a bounded tensor-core wait ran out. */
+int tsm_umma_gemm(const void* A, const void* B, float* C, int M, int N, int K, int beta, void* cuda_stream);
+
 /* Combine per-source loops gathered from several processes into the estimate
  * of Eq. 2.4.  Runs the same device kernel, in the same summation order, as
  * the final step of tsm_loops, so any split of the source ranges gives

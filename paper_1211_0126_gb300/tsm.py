@@ -75,6 +75,7 @@ _SIGS = {
     "tsm_loops_graph": (ctypes.c_int, [_P, ctypes.POINTER(TsmParams), ctypes.c_int, _P, _P, _P, _P,
                                        ctypes.POINTER(TsmLoopStats)]),
     "tsm_tune_batch": (ctypes.c_int, [_P, ctypes.POINTER(TmStop), ctypes.POINTER(ctypes.c_int), _P]),
+    "tsm_umma_gemm": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "tsm_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "tsm_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
     "tsm_launch_count": (ctypes.c_longlong, [_P]),
@@ -323,6 +324,22 @@ def tsm_tune_batch(h, stp):
     _check(library().tsm_tune_batch(h, ctypes.byref(stp), ctypes.byref(best), ctypes.c_void_p(times.ctypes.data)),
            "tsm_tune_batch")
     return best.value, times
+
+
+def tsm_umma_gemm(A, B, C, beta=0, stream=None):
+    """C = A @ B^T (+ C) on the tensor cores: A (M, K), B (N, K) torch bfloat16
+    CUDA tensors, C (M, N) torch float32 CUDA tensor."""
+    import torch
+    for t, dt in ((A, torch.bfloat16), (B, torch.bfloat16), (C, torch.float32)):
+        if not (t.is_cuda and t.is_contiguous() and t.dtype == dt):
+            raise ValueError("tsm_umma_gemm wants contiguous CUDA tensors (bf16, bf16, fp32)")
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K or tuple(C.shape) != (M, N):
+        raise ValueError("shape mismatch")
+    return _check(library().tsm_umma_gemm(ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                          ctypes.c_void_p(C.data_ptr()), M, N, K, int(beta),
+                                          ctypes.c_void_p(stream or 0)), "tsm_umma_gemm")
 
 
 def tsm_profile(h, enable):
