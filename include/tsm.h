@@ -89,11 +89,22 @@ typedef struct {
   int t_antiperiodic;  /* 1: fermion field antiperiodic in t (hops across t = T-1 <-> 0 get -1) */
 } tm_lattice;
 
-/* Stopping rule of one solve (Sec. 2.2: "a large residual or equivalently a
- * fixed number of iterations").  The solve is CG on
- * Dhat^dag Dhat x = Dhat^dag bhat with zero start; it stops after the first
+/* Stopping rule of one solve (Sec. 2.2 truncates a solve either at a loose
+ * residual or at a fixed iteration count; both are offered).  The solve is CG
+ * on Dhat^dag Dhat x = Dhat^dag bhat with zero start; it stops after the first
  * iteration k with ||r_k|| / ||Dhat^dag bhat|| < rel_tol (not squared), or
- * after max_iter iterations.  rel_tol = 0 gives a fixed iteration count. */
+ * after max_iter iterations.  rel_tol = 0 gives a fixed iteration count.
+ *
+ * precond = 1 replaces CG by flexible GMRES on Dhat x = bhat with the
+ * learned network attached to the context (tsm_set_precond) as right
+ * preconditioner (the paper has no such solver: this is the project's
+ * learned LP path).  Its rule is ||bhat - Dhat x|| / ||bhat|| < rel_tol (the
+ * residual of the Schur system itself, a different norm from CG's) or
+ * max_iter inner steps (each = one network application and one Dhat), with
+ * restarts every `restart` steps (0 -> 16, at most 64).  Its vectors are
+ * FP32 (tiers TSM_F32 without reliable updates, TSM_BF16, TSM_F16 only); a
+ * breakdown hands the source to plain CG of the same tier.  Eager only: not
+ * under tsm_loops_graph. */
 typedef struct {
   double rel_tol;
   int max_iter;
@@ -101,6 +112,8 @@ typedef struct {
   int reliable;        /* TSM_F32 only: FP64 solution and FP64 residual recomputation
                           whenever ||r|| fell by reliable_delta since the last one */
   double reliable_delta; /* 0 -> 0.1 */
+  int precond;         /* 0: CG (default); 1: flexible GMRES with the learned preconditioner */
+  int restart;         /* flexible GMRES cycle length (0 -> 16) */
 } tm_stop;
 
 /* Per-call statistics of tsm_loops. */
@@ -231,6 +244,60 @@ int tsm_tune_batch(tsm_ctx* ctx, const tm_stop* stop, int* best, double* times_m
  * (accumulator in tensor memory), ordered on cuda_stream and completed on
  * return.  TSM_ERR_TIMEOUT if a bounded tensor-core wait ran out. */
 int tsm_umma_gemm(const void* A, const void* B, float* C, int M, int N, int K, int beta, void* cuda_stream);
+
+/* ---- learned LP preconditioner (the paper has no network; this is the
+ * project's extension of the LP solves of Sec. 2.2: because the HP - LP
+ * correction of Eq. 2.4 removes any LP bias, it may change the variance per
+ * unit cost only, never the expectation, provided HP-set and LP-set sources
+ * see the same LP solver, which tsm_loops guarantees).
+ *
+ * Network: n_layers parallel-transport layers, C_0 = C_L = 1 channel (a
+ * spinor field), C_l complex channels in between.  Layer l maps psi (C_in
+ * channels) to
+ *   y_{c'}(x)_{s'a} = sum_{p=0..8} sum_{c,s} W[c'*4+s'][(p*C_in+c)*4+s] (T_p psi_c)(x)_{sa}
+ * with T_0 = 1, T_{2mu+1} psi(x) = U_mu(x) psi(x+mu), T_{2mu+2} psi(x) =
+ * U_mu(x-mu)^dag psi(x-mu) (time-boundary sign as in D_tm): gauge covariant,
+ * linear, no activation.  W is complex [4 C_out][36 C_in] (host: interleaved
+ * re, im doubles).  The transports run in FP32 (FP32 links of the context),
+ * the channel mixing as BF16 x BF16 -> FP32 tensor-core GEMMs.  Gradients use
+ * G = dL/dRe + i dL/dIm of a real loss L. */
+typedef struct tsm_net tsm_net;
+
+/* Create a network on `device` with channels[0 .. n_layers] (first and last
+ * 1, others in [1, 64]); weights start near the identity map (channel c'
+ * copies channel c' mod C_in on path 0, the last layer averages) plus complex
+ * Gaussian noise of standard deviation init_scale / sqrt(36 C_in) from a
+ * seeded splitmix64 stream. */
+int tsm_net_create(int device, int n_layers, const int* channels, uint64_t seed, double init_scale,
+                   tsm_net** out);
+int tsm_net_destroy(tsm_net* net);
+/* Host copies of one layer's complex weights [4 C_out][36 C_in]. */
+int tsm_net_set_weights(tsm_net* net, int layer, const double* W);
+int tsm_net_get_weights(tsm_net* net, int layer, double* W);
+/* y = net(x) for nb samples on ctx's gauge field; x [nb][C_0][V][4][3],
+ * y [nb][C_L][V][4][3] complex (canonical site order), host or device. */
+int tsm_net_forward(tsm_net* net, tsm_ctx* ctx, int nb, const double* x, double* y, int on_device);
+/* Given the output gradient gy (layout of y), the input gradient gx (layout
+ * of x; may be NULL) and the weight gradients gw (all layers' [4 C_out][36 C_in]
+ * complex arrays one after another; may be NULL).  Host pointers. */
+int tsm_net_gradient(tsm_net* net, tsm_ctx* ctx, int nb, const double* x, const double* gy, double* gx,
+                     double* gw);
+/* Make n training pairs (r, Dhat^-1 r) on ctx's gauge field: r = Z4 noise of
+ * `seed` (sources 0 .. n-1) on the even sites, Dhat^-1 r by batched FP32 CG
+ * (stop: TSM_F32, no reliable updates).  *group receives the pair group id.
+ * The pairs stay in device memory (2 x 96 V bytes each) until the network is
+ * destroyed; the context must outlive the network's use of them. */
+int tsm_net_add_pairs(tsm_net* net, tsm_ctx* ctx, int n, uint64_t seed, const tm_stop* stop, int* group);
+/* Adam (lr; betas 0.9, 0.999) on the mean over a minibatch of the relative
+ * loss |net(r) - t|^2 / |t|^2 over even sites; step k uses groups[k mod
+ * n_groups] and `batch` consecutive pairs of it.  loss (may be NULL) receives
+ * the minibatch mean loss of every step. */
+int tsm_net_train(tsm_net* net, const int* groups, int n_groups, int steps, int batch, double lr, double* loss);
+/* Mean relative loss over all pairs of a group, without training. */
+int tsm_net_loss(tsm_net* net, int group, double* loss);
+/* Attach (net) or detach (NULL) the preconditioner used by solves with
+ * tm_stop.precond = 1 on this context.  Not owned by the context. */
+int tsm_set_precond(tsm_ctx* ctx, tsm_net* net);
 
 /* Combine per-source loops gathered from several processes into the estimate
  * of Eq. 2.4.  Runs the same device kernel, in the same summation order, as

@@ -85,6 +85,8 @@ int check_stop(const tm_stop* s) {
   if (s == nullptr) return bad(TSM_ERR_ARG, "null tm_stop");
   if (s->prec < TSM_F64 || s->prec > TSM_F16) return bad(TSM_ERR_ARG, "tm_stop.prec out of range");
   if (s->max_iter < 0 || !(s->rel_tol >= 0.0)) return bad(TSM_ERR_ARG, "tm_stop: max_iter < 0 or rel_tol < 0");
+  if (s->precond != 0 && s->precond != 1) return bad(TSM_ERR_ARG, "tm_stop.precond must be 0 or 1");
+  if (s->restart < 0) return bad(TSM_ERR_ARG, "tm_stop.restart < 0");
   return TSM_OK;
 }
 

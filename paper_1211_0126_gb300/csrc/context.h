@@ -47,8 +47,11 @@ struct EOField {
 
 enum HopKind { PK_HOP = 0, PK_HOP_XPAY = 1, PK_HOP_DAG = 2, PK_HOP_UPDATE = 3 };
 
+struct Net;
+
 struct Ctx {
   int device = 0;
+  Net* net = nullptr;    // learned preconditioner used by solves with tm_stop.precond (not owned)
   cudaStream_t stream = nullptr;
   bool has_gauge = false;
   tm_lattice lat{};

@@ -28,6 +28,7 @@
 
 #include "fields.cuh"
 #include "solver.h"
+#include "net.h"
 
 namespace tsm {
 
@@ -391,6 +392,7 @@ int reserve_solver(Ctx& c, const tm_stop& stop) {
 }
 
 int solve_batch(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EOField s, SolveResult* res) {
+  if (stop.precond) return fgmres_batch(c, stop, nrhs, b, s, res);
   if (nrhs < 1 || nrhs > c.batch_cap || s0 < 0 || s0 + nrhs > Ctx::kMaxStates - 4) {
     set_error("batch of %d right-hand sides at state %d exceeds the capacity (%d)", nrhs, s0, c.batch_cap);
     return TSM_ERR_TOO_LARGE;

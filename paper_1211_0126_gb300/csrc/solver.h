@@ -10,6 +10,8 @@ struct SolveResult {
   int status = TSM_OK;     // TSM_OK or TSM_ERR_NONFINITE
   int converged = 0;       // stopping rule met (fixed-count rule: max_iter reached)
   double rel_res = 0.0;    // final ||r|| / ||Dhat^dag bhat|| as tracked by the solver
+                           // (flexible GMRES: the true ||bhat - Dhat x|| / ||bhat||)
+  int fallback = 0;        // flexible GMRES broke down and plain CG produced the solution
 };
 
 // Storage tier of a solve's source and solution fields: FP64 for the FP64

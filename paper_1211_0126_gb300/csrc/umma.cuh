@@ -95,11 +95,15 @@ __device__ __forceinline__ void stage_tile(const __nv_bfloat16* __restrict__ g, 
 // BN = tile width (multiple of 16, <= 192: the static shared memory holds
 // both stages within 48 KB); K need not be a multiple of 64
 // (zero-filled) but the rows of A and B must start 16-byte aligned (K % 8 == 0).
+//
+// Split-K: blockIdx.z covers K range [z * kchunk, (z + 1) * kchunk) and writes
+// its partial product to C + z * czstride (reduced afterwards by the caller).
 template <int BN>
 __global__ void __launch_bounds__(UMMA_THREADS) umma_gemm_kernel(const __nv_bfloat16* __restrict__ A,
                                                                  const __nv_bfloat16* __restrict__ B,
                                                                  float* __restrict__ C, int M, int N, int K,
-                                                                 int ldc, int beta, int* __restrict__ error) {
+                                                                 int ldc, int beta, int* __restrict__ error,
+                                                                 int lda, int ldb, int kchunk, long long czstride) {
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 192, "BN must be a multiple of 16 in [16, 192]");
   constexpr int TMEM_COLS = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
   __shared__ __align__(1024) uint8_t sA[UMMA_BM * UMMA_BK * 2];
@@ -124,11 +128,15 @@ __global__ void __launch_bounds__(UMMA_THREADS) umma_gemm_kernel(const __nv_bflo
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
   constexpr uint32_t idesc = umma_idesc_bf16(UMMA_BM, BN);
-  const int ktiles = (K + UMMA_BK - 1) / UMMA_BK;
+  // this CTA's K range (split-K along blockIdx.z)
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  const int ktiles = kend > kbeg ? (kend - kbeg + UMMA_BK - 1) / UMMA_BK : 0;
+  C += (size_t)blockIdx.z * (size_t)czstride;
   uint32_t phase = 0;
   for (int kt = 0; kt < ktiles; ++kt) {
-    stage_tile<UMMA_BM>(A, K, m0, M, kt * UMMA_BK, K, sA);
-    stage_tile<BN>(B, K, n0, N, kt * UMMA_BK, K, sB);
+    stage_tile<UMMA_BM>(A, lda, m0, M, kbeg + kt * UMMA_BK, kend, sA);
+    stage_tile<BN>(B, ldb, n0, N, kbeg + kt * UMMA_BK, kend, sB);
     // generic-proxy writes of shared memory -> visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -157,8 +165,9 @@ __global__ void __launch_bounds__(UMMA_THREADS) umma_gemm_kernel(const __nv_bflo
     if (timed_out) break;
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!timed_out && ktiles > 0) {
-    // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31
+  if (!timed_out) {
+    // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31 (an empty
+    // split-K range contributes zeros)
     const int row = m0 + warp * 32 + lane;
     for (int c0 = 0; c0 < BN; c0 += 8) {
       uint32_t v[8];
@@ -168,6 +177,10 @@ __global__ void __launch_bounds__(UMMA_THREADS) umma_gemm_kernel(const __nv_bflo
           : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (ktiles == 0) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = 0u;
+      }
       if (row < M) {
 #pragma unroll
         for (int e = 0; e < 8; ++e) {

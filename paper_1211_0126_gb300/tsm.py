@@ -36,7 +36,8 @@ class TmLattice(ctypes.Structure):
 
 class TmStop(ctypes.Structure):
     _fields_ = [("rel_tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("prec", ctypes.c_int),
-                ("reliable", ctypes.c_int), ("reliable_delta", ctypes.c_double)]
+                ("reliable", ctypes.c_int), ("reliable_delta", ctypes.c_double), ("precond", ctypes.c_int),
+                ("restart", ctypes.c_int)]
 
 
 class TsmLoopStats(ctypes.Structure):
@@ -76,6 +77,18 @@ _SIGS = {
                                        ctypes.POINTER(TsmLoopStats)]),
     "tsm_tune_batch": (ctypes.c_int, [_P, ctypes.POINTER(TmStop), ctypes.POINTER(ctypes.c_int), _P]),
     "tsm_umma_gemm": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "tsm_net_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint64, ctypes.c_double,
+                                      ctypes.POINTER(_P)]),
+    "tsm_net_destroy": (ctypes.c_int, [_P]),
+    "tsm_net_set_weights": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "tsm_net_get_weights": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "tsm_net_forward": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, ctypes.c_int]),
+    "tsm_net_gradient": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P, _P]),
+    "tsm_net_add_pairs": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(TmStop),
+                                         ctypes.POINTER(ctypes.c_int)]),
+    "tsm_net_train": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P]),
+    "tsm_net_loss": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "tsm_set_precond": (ctypes.c_int, [_P, _P]),
     "tsm_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "tsm_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
     "tsm_launch_count": (ctypes.c_longlong, [_P]),
@@ -185,8 +198,9 @@ def lattice(dims, kappa, mu, antiperiodic_t=True):
     return lat
 
 
-def stop(rel_tol, max_iter, prec=TSM_F64, reliable=False, reliable_delta=0.0):
-    return TmStop(float(rel_tol), int(max_iter), int(prec), 1 if reliable else 0, float(reliable_delta))
+def stop(rel_tol, max_iter, prec=TSM_F64, reliable=False, reliable_delta=0.0, precond=False, restart=0):
+    return TmStop(float(rel_tol), int(max_iter), int(prec), 1 if reliable else 0, float(reliable_delta),
+                  1 if precond else 0, int(restart))
 
 
 def tsm_load_gauge(h, lat, U):
@@ -342,6 +356,69 @@ def tsm_umma_gemm(A, B, C, beta=0, stream=None):
                                           ctypes.c_void_p(stream or 0)), "tsm_umma_gemm")
 
 
+def tsm_net_create(channels, seed=0, init_scale=0.1, device=0):
+    """Network with channels[0..L] (first and last 1); returns its handle."""
+    ch = np.ascontiguousarray(channels, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(library().tsm_net_create(int(device), len(ch) - 1, ctypes.c_void_p(ch.ctypes.data),
+                                    ctypes.c_uint64(seed), float(init_scale), ctypes.byref(h)), "tsm_net_create")
+    return h
+
+
+def tsm_net_destroy(n):
+    _check(library().tsm_net_destroy(n), "tsm_net_destroy")
+
+
+def tsm_net_set_weights(n, layer, W):
+    W = np.ascontiguousarray(W, dtype=np.complex128)
+    _check(library().tsm_net_set_weights(n, int(layer), ctypes.c_void_p(W.ctypes.data)), "tsm_net_set_weights")
+
+
+def tsm_net_get_weights(n, layer, shape):
+    W = np.zeros(shape, dtype=np.complex128)
+    _check(library().tsm_net_get_weights(n, int(layer), ctypes.c_void_p(W.ctypes.data)), "tsm_net_get_weights")
+    return W
+
+
+def tsm_net_forward(n, h, nb, x, y):
+    px, dx = _ptr(x)
+    py, dy = _ptr(y, True)
+    _check(library().tsm_net_forward(n, h, int(nb), px, py, _same_side(dx, dy)), "tsm_net_forward")
+
+
+def tsm_net_gradient(n, h, nb, x, gy, gx, gw):
+    px, _ = _ptr(x)
+    pg, _ = _ptr(gy)
+    pgx, _ = _ptr(gx, True)
+    pgw, _ = _ptr(gw, True)
+    _check(library().tsm_net_gradient(n, h, int(nb), px, pg, pgx, pgw), "tsm_net_gradient")
+
+
+def tsm_net_add_pairs(n, h, count, seed, stp):
+    g = ctypes.c_int(-1)
+    _check(library().tsm_net_add_pairs(n, h, int(count), ctypes.c_uint64(seed), ctypes.byref(stp), ctypes.byref(g)),
+           "tsm_net_add_pairs")
+    return g.value
+
+
+def tsm_net_train(n, groups, steps, batch, lr):
+    gr = np.ascontiguousarray(groups, dtype=np.int32)
+    loss = np.zeros(max(int(steps), 1))
+    _check(library().tsm_net_train(n, ctypes.c_void_p(gr.ctypes.data), len(gr), int(steps), int(batch), float(lr),
+                                   ctypes.c_void_p(loss.ctypes.data)), "tsm_net_train")
+    return loss[:int(steps)]
+
+
+def tsm_net_loss(n, group):
+    v = ctypes.c_double(0.0)
+    _check(library().tsm_net_loss(n, int(group), ctypes.byref(v)), "tsm_net_loss")
+    return v.value
+
+
+def tsm_set_precond(h, n):
+    _check(library().tsm_set_precond(h, n), "tsm_set_precond")
+
+
 def tsm_profile(h, enable):
     return _check(library().tsm_profile(h, 1 if enable else 0), "tsm_profile")
 
@@ -458,3 +535,64 @@ class Context:
 
     def launch_count(self):
         return tsm_launch_count(self.h)
+
+    def set_precond(self, net):
+        tsm_set_precond(self.h, None if net is None else net.h)
+
+
+class Network:
+    """Owning wrapper around a tsm_net (the learned LP preconditioner)."""
+
+    def __init__(self, channels, seed=0, init_scale=0.1, device=0):
+        self.channels = [int(c) for c in channels]
+        self.h = tsm_net_create(self.channels, seed, init_scale, device)
+
+    def close(self):
+        if self.h is not None:
+            tsm_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape(self, layer):
+        return (4 * self.channels[layer + 1], 36 * self.channels[layer])
+
+    def set_weights(self, layer, W):
+        tsm_net_set_weights(self.h, layer, W)
+
+    def get_weights(self, layer):
+        return tsm_net_get_weights(self.h, layer, self.shape(layer))
+
+    def forward(self, ctx, x):
+        """x [nb, C0, T, Z, Y, X, 4, 3] complex -> [nb, CL, ...]."""
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        y = np.zeros((x.shape[0], self.channels[-1]) + x.shape[2:], dtype=np.complex128)
+        tsm_net_forward(self.h, ctx.h, x.shape[0], x, y)
+        return y
+
+    def gradient(self, ctx, x, gy):
+        """(gx, [gW per layer]) for output gradient gy (G = dL/dRe + i dL/dIm)."""
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        gy = np.ascontiguousarray(gy, dtype=np.complex128)
+        gx = np.zeros_like(x)
+        sizes = [int(np.prod(self.shape(l))) for l in range(len(self.channels) - 1)]
+        gw = np.zeros(sum(sizes), dtype=np.complex128)
+        tsm_net_gradient(self.h, ctx.h, x.shape[0], x, gy, gx, gw)
+        out, off = [], 0
+        for l, sz in enumerate(sizes):
+            out.append(gw[off:off + sz].reshape(self.shape(l)))
+            off += sz
+        return gx, out
+
+    def add_pairs(self, ctx, count, seed, stp):
+        return tsm_net_add_pairs(self.h, ctx.h, count, seed, stp)
+
+    def train(self, groups, steps, batch, lr):
+        return tsm_net_train(self.h, groups, steps, batch, lr)
+
+    def loss(self, group):
+        return tsm_net_loss(self.h, group)

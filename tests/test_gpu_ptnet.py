@@ -1,0 +1,189 @@
+"""The learned LP preconditioner on the GPU against the oracle.
+
+* Forward of a parallel-transport network (FP32 transports, BF16 x BF16 -> FP32
+  channel mixing on the tensor cores) against oracle.ptnet in FP64.  Bound:
+  normwise relative error below 4 L u, u = 2^-9 the BF16 unit roundoff (per
+  layer one rounding of the gathered input and one of the weights, each
+  bounded by u, summed with random signs; L layers compound).
+* Input and weight gradients against the oracle's analytic backward, within
+  8 L u (the backward rounds the output gradient as well).
+* Training pairs and loss: the network's mean relative loss on its pairs
+  equals the oracle's on (Z4 noise on even sites from the oracle's Philox,
+  Dhat^-1 r by the oracle's CG), within the forward bound.
+* Training lowers the loss on a held-out gauge field.
+* Flexible GMRES with the network solves D_tm s = eta (dense inverse as judge),
+  honours the fixed-step rule, and hands a broken network (NaN weights planted
+  on the host) to plain CG.
+* tsm_loops with learned LP solves agrees with the FP64 path within the
+  stochastic error (the HP - LP correction keeps the estimate unbiased).
+"""
+import numpy as np
+import pytest
+
+from oracle import dirac, philox, ptnet, solver
+from paper_1211_0126_gb300 import synthetic as S
+from paper_1211_0126_gb300 import tsm
+
+pytestmark = pytest.mark.gpu
+
+U_BF16 = 2.0 ** -9
+KAPPA, MU = 0.124, 0.01
+DIMS = (6, 4, 2, 4)          # V = 192: 3V = 576 GEMM rows = 4.5 tiles of 128
+
+
+def _rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+def _oracle_weights(net):
+    return [net.get_weights(l) for l in range(len(net.channels) - 1)]
+
+
+@pytest.mark.parametrize("channels", [[1, 3, 2, 1], [1, 12, 12, 12, 1]])
+def test_forward_matches_oracle(ctx, channels):
+    U = S.gauge_field(DIMS, 0.3, 3)
+    ctx.load_gauge(U, DIMS, KAPPA, MU)
+    net = tsm.Network(channels, seed=1, init_scale=1.0)
+    Ws = _oracle_weights(net)
+    x = S.random_spinor(DIMS, 5, batch=(2, 1))
+    y = net.forward(ctx, x)
+    L = len(channels) - 1
+    for b in range(2):
+        want = ptnet.net_forward(U, Ws, x[b], DIMS)[-1]
+        assert _rel(y[b], want) < 4 * L * U_BF16
+
+
+def test_weights_round_trip(ctx):
+    net = tsm.Network([1, 2, 1], seed=2)
+    rng = np.random.default_rng(3)
+    W = rng.standard_normal(net.shape(0)) + 1j * rng.standard_normal(net.shape(0))
+    net.set_weights(0, W)
+    got = net.get_weights(0)
+    assert np.array_equal(got.real, W.real.astype(np.float32).astype(np.float64))
+    assert np.array_equal(got.imag, W.imag.astype(np.float32).astype(np.float64))
+
+
+def test_gradients_match_oracle(ctx):
+    U = S.gauge_field(DIMS, 0.3, 4)
+    ctx.load_gauge(U, DIMS, KAPPA, MU)
+    channels = [1, 4, 3, 1]
+    L = len(channels) - 1
+    net = tsm.Network(channels, seed=6, init_scale=1.0)
+    Ws = _oracle_weights(net)
+    x = S.random_spinor(DIMS, 7, batch=(2, 1))
+    gy = S.random_spinor(DIMS, 8, batch=(2, 1))
+    gx, gW = net.gradient(ctx, x, gy)
+    want_w = [np.zeros_like(w) for w in Ws]
+    for b in range(2):
+        acts = ptnet.net_forward(U, Ws, x[b], DIMS)
+        g = gy[b]
+        for l in range(L - 1, -1, -1):
+            g, gl = ptnet.layer_backward(U, Ws[l], acts[l], g, DIMS)
+            want_w[l] += gl
+        assert _rel(gx[b], g) < 8 * L * U_BF16
+    for l in range(L):
+        assert _rel(gW[l], want_w[l]) < 8 * L * U_BF16, l
+
+
+def test_pairs_and_loss_match_oracle(ctx):
+    dims = (4, 4, 4, 4)
+    U = S.gauge_field(dims, 0.3, 9)
+    ctx.load_gauge(U, dims, KAPPA, MU)
+    net = tsm.Network([1, 4, 1], seed=10, init_scale=0.5)
+    n, seed = 6, 321
+    g = net.add_pairs(ctx, n, seed, tsm.stop(1e-7, 4000, tsm.TSM_F32))
+    got = net.loss(g)
+    Ws = _oracle_weights(net)
+    e = dirac.even_mask(dims)
+    want = []
+    for j in range(n):
+        r = e * philox.noise(seed, j, dims, 4)
+        t, _, res = solver.cgnr(U, r, dims, KAPPA, MU, 1e-11, 5000)
+        y = ptnet.net_forward(U, Ws, r[None], dims)[-1]
+        want.append(ptnet.relative_loss(y, t, e)[0])
+    want = float(np.mean(want))
+    # |dL| <= 2 sqrt(L) |dy| / |t| with |dy| <= 4 L u |y| (L = 2 layers here)
+    assert abs(got - want) <= 0.05 * want
+
+
+def test_training_lowers_heldout_loss(libtsm):
+    dims = (4, 4, 4, 4)
+    stp = tsm.stop(1e-6, 4000, tsm.TSM_F32)
+    with tsm.Context(0) as train, tsm.Context(0) as held:
+        train.load_gauge(S.gauge_field(dims, 0.3, 11), dims, KAPPA, MU)
+        held.load_gauge(S.gauge_field(dims, 0.3, 12), dims, KAPPA, MU)
+        net = tsm.Network([1, 4, 4, 1], seed=13, init_scale=0.1)
+        gt = net.add_pairs(train, 32, 1, stp)
+        gh = net.add_pairs(held, 16, 2, stp)
+        before = net.loss(gh)
+        hist = net.train([gt], steps=120, batch=4, lr=3e-3)
+        after = net.loss(gh)
+        net.close()
+    assert np.isfinite(hist).all()
+    assert hist[-8:].mean() < hist[:8].mean()
+    assert after < 0.8 * before, (before, after)
+
+
+@pytest.fixture()
+def solve_setup(ctx):
+    dims = (4, 4, 4, 4)
+    U = S.gauge_field(dims, 0.3, 14)
+    ctx.load_gauge(U, dims, KAPPA, MU)
+    eta = philox.noise(77, 0, dims, 4)
+    exact = np.linalg.solve(dirac.dense_dtm(U, dims, KAPPA, MU), eta.ravel()).reshape(eta.shape)
+    net = tsm.Network([1, 4, 1], seed=15, init_scale=0.1)
+    ctx.set_precond(net)
+    yield eta, exact, net
+    ctx.set_precond(None)
+    net.close()
+
+
+def test_fgmres_solves_system(ctx, solve_setup):
+    eta, exact, net = solve_setup
+    s, iters, tres, st = ctx.solve(eta, tsm.stop(1e-6, 600, tsm.TSM_F32, precond=True, restart=12))
+    assert st == 0
+    assert tres[0] < 5e-6
+    assert _rel(s, exact) < 1e-3
+    assert 0 < iters[0] < 600
+
+
+def test_fgmres_fixed_steps(ctx, solve_setup):
+    eta, exact, net = solve_setup
+    for k in (1, 7, 20):
+        s, iters, tres, st = ctx.solve(eta, tsm.stop(0.0, k, tsm.TSM_F16, precond=True, restart=8))
+        assert iters[0] == k
+    # more steps, smaller residual
+    _, _, t7, _ = ctx.solve(eta, tsm.stop(0.0, 7, tsm.TSM_F32, precond=True, restart=8))
+    _, _, t20, _ = ctx.solve(eta, tsm.stop(0.0, 20, tsm.TSM_F32, precond=True, restart=8))
+    assert t20[0] < t7[0]
+
+
+def test_fgmres_falls_back_to_cg(ctx, solve_setup):
+    eta, exact, net = solve_setup
+    W = net.get_weights(0)
+    W[0, 0] = np.nan
+    net.set_weights(0, W)
+    s, iters, tres, st = ctx.solve(eta, tsm.stop(1e-6, 3000, tsm.TSM_F32, precond=True))
+    assert np.isfinite(s).all()
+    assert tres[0] < 1e-4
+    assert _rel(s, exact) < 1e-3
+
+
+def test_learned_tsm_unbiased(ctx):
+    dims = (4, 4, 4, 4)
+    U = S.gauge_field(dims, 0.3, 1)
+    ctx.load_gauge(U, dims, KAPPA, MU)
+    net = tsm.Network([1, 4, 1], seed=16, init_scale=0.1)
+    g = net.add_pairs(ctx, 16, 99, tsm.stop(1e-6, 4000, tsm.TSM_F32))
+    net.train([g], steps=40, batch=4, lr=3e-3)
+    ctx.set_precond(net)
+    gam, moms = list(range(16)), S.default_momenta(4)
+    hp = tsm.stop(1e-10, 5000, tsm.TSM_F32, reliable=True)
+    got = ctx.loops(11, 4, 8, 64, hp, tsm.stop(1e-2, 200, tsm.TSM_F16, precond=True, restart=8), gam, moms)
+    ref = ctx.loops(11, 4, 8, 64, tsm.stop(1e-12, 5000, tsm.TSM_F64), tsm.stop(1e-2, 5000, tsm.TSM_F64),
+                    gam, moms)
+    ctx.set_precond(None)
+    net.close()
+    assert got["stats"]["hp_not_converged"] == 0
+    z = np.abs(got["loops"] - ref["loops"]) / np.sqrt(got["err"] ** 2 + ref["err"] ** 2 + 1e-300)
+    assert np.median(z) < 1.0 and z.max() < 5.0
