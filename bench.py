@@ -56,9 +56,12 @@ def parse():
     ap.add_argument("--mode", default="eager", choices=["eager", "graph"],
                     help="eager: host-driven chunked CG loops; graph: one captured CUDA graph per step "
                          "(device-side loops, LP set beside the HP set)")
-    ap.add_argument("--workload", default="tsm24", choices=["tsm24", "three-lattice"],
+    ap.add_argument("--workload", default="tsm24", choices=["tsm24", "three-lattice", "learned"],
                     help="tsm24: the headline 24^3x48 TSM step; three-lattice: 8^3x16 + 12^3x24 + 16^3x32 "
-                         "in one captured graph (batching workload, its own JSON line)")
+                         "in one captured graph (batching workload, its own JSON line); learned: the learned "
+                         "LP preconditioner at 16^3x32 (training + held-out evaluation, its own JSON line)")
+    ap.add_argument("--train-steps", type=int, default=400, help="learned workload: Adam steps")
+    ap.add_argument("--pairs-per-field", type=int, default=500, help="learned workload: pairs per training field")
     ap.add_argument("--dslash-only", default=None,
                     help="comma list of tiers (f64,f32,f16,bf16): only run 3 standalone H_eo launches per tier "
                          "at 24^3x48 (a small case for ncu captures of the hop kernel)")
@@ -539,6 +542,103 @@ def run_three_lattice(args):
         c.close()
 
 
+def run_learned(args):
+    """Learned-preconditioner workload: 16^3x32, links eps = 0.25 (seeds 201-204
+    train, 205-206 held out), kappa = 0.1245, mu = 0.005.  A 4-layer
+    parallel-transport network (channels 1-12-12-12-1, BF16 channel mixing on
+    the tensor cores) is trained with Adam on 4 x pairs-per-field (r, Dhat^-1 r)
+    pairs from FP32 CG solves (1e-6) and evaluated on the held-out fields:
+    relative loss; flexible GMRES with the trained and with the untrained
+    (near-identity) network against CG at the LP tolerance 1e-2; and the TSM
+    estimate with N_HP = 16, N_LP = 1024 using learned LP solves against plain
+    BF16 CG LP solves, compared at equal loop error (time x variance)."""
+    import torch
+    from paper_1211_0126_gb300 import build, tsm
+    from paper_1211_0126_gb300 import synthetic as S
+    if not os.path.exists(tsm.LIB_PATH):
+        build.build()
+    dims = (16, 16, 16, 32)
+    channels = [1, 12, 12, 12, 1]
+    gam, moms = list(range(N_GAMMA)), S.default_momenta(N_Q)
+    pair_stop = tsm.stop(1e-6, 4000, tsm.TSM_F32)
+    lp_cg = tsm.stop(1e-2, 500, tsm.TSM_BF16)
+    lp_fg = tsm.stop(1e-2, 500, tsm.TSM_BF16, precond=True, restart=16)
+    hp = tsm.stop(1e-10, HP_MAXIT, tsm.TSM_F32, reliable=True, reliable_delta=RELIABLE_DELTA)
+    ctxs = []
+    for seed in range(201, 207):
+        c = tsm.Context(0)
+        c.load_gauge(S.gauge_field(dims, EPS, seed), dims, KAPPA, MU)
+        ctxs.append(c)
+    train, held = ctxs[:4], ctxs[4:]
+    net = tsm.Network(channels, seed=7, init_scale=0.1)
+    untrained = tsm.Network(channels, seed=7, init_scale=0.1)
+    t0 = time.perf_counter()
+    g_train = [net.add_pairs(c, args.pairs_per_field, 300 + k, pair_stop) for k, c in enumerate(train)]
+    g_held = [net.add_pairs(c, 32, 400 + k, pair_stop) for k, c in enumerate(held)]
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    loss0 = [net.loss(g) for g in g_held]
+    t0 = time.perf_counter()
+    hist = net.train(g_train, args.train_steps, 4, 2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    loss1 = [net.loss(g) for g in g_held]
+
+    def solve_stats(c, stp, model, n=16):
+        c.set_precond(model)
+        b = np.stack([c.noise(900, j) for j in range(n)])
+        c.solve(b[:2], stp)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, it, tr, _ = c.solve(b, stp)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t) * 1e3 / n
+        c.set_precond(None)
+        return {"iters": float(np.mean(it)), "true_res": float(np.mean(tr)), "ms_per_solve": ms}
+
+    solves = {"cg_bf16": [solve_stats(c, lp_cg, None) for c in held],
+              "fgmres_trained": [solve_stats(c, lp_fg, net) for c in held],
+              "fgmres_untrained": [solve_stats(c, lp_fg, untrained) for c in held]}
+    tsm_cmp = []
+    for k, c in enumerate(held):
+        row = {}
+        for name, lp, model in (("plain_cg", lp_cg, None), ("learned", lp_fg, net)):
+            c.set_precond(model)
+            c.loops(50 + k, 4, 2, 8, hp, lp, gam, moms, batch=32)     # warm-up
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            out = c.loops(60 + k, 4, 16, 1024, hp, lp, gam, moms, batch=32)
+            torch.cuda.synchronize()
+            row[name] = {"s": time.perf_counter() - t, "err2": out["err"] ** 2,
+                         "lp_iters_per_source": out["stats"]["lp_iters"] / 1040.0}
+            c.set_precond(None)
+        ok = row["plain_cg"]["err2"] > 0
+        var = row["learned"]["err2"][ok] / row["plain_cg"]["err2"][ok]
+        ratio = var * row["learned"]["s"] / row["plain_cg"]["s"]
+        tsm_cmp.append({"plain_cg_s": row["plain_cg"]["s"], "learned_s": row["learned"]["s"],
+                        "plain_lp_iters": row["plain_cg"]["lp_iters_per_source"],
+                        "learned_lp_iters": row["learned"]["lp_iters_per_source"],
+                        "median_var_ratio": float(np.median(var)),
+                        "median_cost_at_equal_error_ratio": float(np.median(ratio))})
+    gain = float(np.mean([r["median_cost_at_equal_error_ratio"] for r in tsm_cmp]))
+    line = {"metric": "learned LP preconditioner: TSM cost at equal loop error, learned / plain CG",
+            "value": gain, "unit": "ratio (<1: learned cheaper)", "n_gpus": 1, "higher_is_better": False,
+            "data": "synthetic",
+            "config": {"workload": "learned-16^3x32-eps0.25-k0.1245-mu0.005 net1-12-12-12-1 "
+                                   "train 4 fields x %d pairs, held-out 2 fields; TSM hp16 lp1024 at 1e-2"
+                                   % args.pairs_per_field,
+                       "train_steps": args.train_steps, "batch": 4, "lr": 2e-3},
+            "pairs_s": t_pairs, "train_s": t_train, "train_ms_per_step": t_train * 1e3 / max(args.train_steps, 1),
+            "train_loss_first_last": [float(np.mean(hist[:10])), float(np.mean(hist[-10:]))],
+            "heldout_loss_before_after": [float(np.mean(loss0)), float(np.mean(loss1))],
+            "solves_at_1e-2": solves, "tsm_equal_error": tsm_cmp}
+    print(json.dumps(line), flush=True)
+    net.close()
+    untrained.close()
+    for c in ctxs:
+        c.close()
+
+
 def main():
     args = parse()
     if args.warmup < 3:
@@ -547,6 +647,8 @@ def main():
         run_dslash_only(args.dslash_only)
     elif args.workload == "three-lattice":
         run_three_lattice(args)
+    elif args.workload == "learned":
+        run_learned(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
