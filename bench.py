@@ -36,7 +36,7 @@ DIMS = (24, 24, 24, 48)
 EPS, KAPPA, MU, GAUGE_SEED = 0.25, 0.1245, 0.005, 3
 N_HP, N_LP = 8, 256
 HP_TOL, LP_TOL, LP_MAXIT, HP_MAXIT = 1e-10, 5e-3, 60, 20000
-RELIABLE_DELTA = 1e-4        # FP64 residual replacement whenever ||r|| fell by 10^4
+RELIABLE_DELTA = 1e-5        # FP64 residual replacement whenever ||r|| fell by 10^5
 TIERS = {0: "f64", 1: "f32", 2: "bf16", 3: "f16"}
 KINDS = ("K1_hop", "K2_hop_xpay_norm", "K3_hop_dag", "K4_hop_dag_cg_update")
 N_GAMMA, N_Q = 16, 7
@@ -62,10 +62,72 @@ def parse():
                          "LP preconditioner at 16^3x32 (training + held-out evaluation, its own JSON line)")
     ap.add_argument("--train-steps", type=int, default=400, help="learned workload: Adam steps")
     ap.add_argument("--pairs-per-field", type=int, default=500, help="learned workload: pairs per training field")
+    ap.add_argument("--net-only", action="store_true",
+                    help="only run 3 forward passes of the learned preconditioner's network (channels "
+                         "1-12-12-12-1) at 16^3x32, timed with CUDA events (a small case for ncu captures of "
+                         "the transport and tensor-core GEMM kernels)")
+    ap.add_argument("--lp-only", action="store_true",
+                    help="only run one batched LP solve (32 Z4 sources, FP16 storage, 5e-3 or 60 iterations) at "
+                         "16^3x32 (a small case for ncu captures of the batched K1-K4 kernels; its fields exceed "
+                         "L2)")
     ap.add_argument("--dslash-only", default=None,
                     help="comma list of tiers (f64,f32,f16,bf16): only run 3 standalone H_eo launches per tier "
                          "at 24^3x48 (a small case for ncu captures of the hop kernel)")
     return ap.parse_args()
+
+
+def run_net_only():
+    import torch
+    from paper_1211_0126_gb300 import build, tsm
+    from paper_1211_0126_gb300 import synthetic as S
+    if not os.path.exists(tsm.LIB_PATH):
+        build.build()
+    dims = (16, 16, 16, 32)
+    V = int(np.prod(dims))
+    stream = torch.cuda.current_stream()
+    ctx = tsm.Context(0, stream.cuda_stream)
+    ctx.load_gauge(S.gauge_field(dims, EPS, 201), dims, KAPPA, MU)
+    net = tsm.Network([1, 12, 12, 12, 1], seed=7, init_scale=0.1)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn(1, 1, V * 12, dtype=torch.complex128, device="cuda", generator=g)
+    y = torch.zeros_like(x)
+    tsm.tsm_net_forward(net.h, ctx.h, 1, x, y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        tsm.tsm_net_forward(net.h, ctx.h, 1, x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    print(json.dumps({"net_only": {"lattice": list(dims), "channels": [1, 12, 12, 12, 1],
+                                   "ms_per_forward": e0.elapsed_time(e1) / 3}}), flush=True)
+    net.close()
+    ctx.close()
+
+
+def run_lp_only():
+    import torch
+    from paper_1211_0126_gb300 import build, tsm
+    from paper_1211_0126_gb300 import synthetic as S
+    if not os.path.exists(tsm.LIB_PATH):
+        build.build()
+    dims = (16, 16, 16, 32)
+    stream = torch.cuda.current_stream()
+    ctx = tsm.Context(0, stream.cuda_stream)
+    ctx.load_gauge(S.gauge_field(dims, EPS, GAUGE_SEED), dims, KAPPA, MU)
+    V = int(np.prod(dims))
+    b = torch.zeros(32, V * 12, dtype=torch.complex128, device="cuda")
+    for j in range(32):
+        tsm.tsm_noise(ctx.h, 77, 4, j, b[j])
+    s = torch.zeros_like(b)
+    lp = tsm.stop(LP_TOL, LP_MAXIT, tsm.TSM_F16)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, iters, _ = tsm.tm_solve_batch(ctx.h, b, s, lp, 32)
+    torch.cuda.synchronize()
+    print(json.dumps({"lp_only": {"lattice": list(dims), "batch": 32, "iters_mean": float(np.mean(iters)),
+                                  "ms": (time.perf_counter() - t0) * 1e3}}), flush=True)
+    ctx.close()
 
 
 def run_dslash_only(tiers):
@@ -363,7 +425,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "lattice": list(DIMS), "n_hp_per_gpu": N_HP, "n_lp_per_gpu": N_LP,
-                       "batch": args.batch, "reliable_delta": rdelta, "mode": args.mode,
+                       "batch": args.batch, "reliable_delta": rdelta,
+                       "mode": args.mode,
                        "l2": "flushed between steps (256 MB write)",
                        "lp_iters_per_source": st.lp_iters / float(N_HP + N_LP),
                        "hp_iters_per_source": st.hp_iters / float(N_HP),
@@ -643,7 +706,11 @@ def main():
     args = parse()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.dslash_only:
+    if args.net_only:
+        run_net_only()
+    elif args.lp_only:
+        run_lp_only()
+    elif args.dslash_only:
         run_dslash_only(args.dslash_only)
     elif args.workload == "three-lattice":
         run_three_lattice(args)

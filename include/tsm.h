@@ -236,6 +236,7 @@ int tsm_loops_graph(tsm_ctx** ctxs, const tsm_params* params, int n, double** lo
  * the 4 measured times per source in milliseconds. */
 int tsm_tune_batch(tsm_ctx* ctx, const tm_stop* stop, int* best, double* times_ms);
 
+
 /* Tensor-core GEMM of the learned preconditioner's channel mixing (the dense
  * contraction of the parallel-transport layers; the paper has no network --
  * this is the project's learned LP preconditioner):
@@ -244,6 +245,15 @@ int tsm_tune_batch(tsm_ctx* ctx, const tm_stop* stop, int* best, double* times_m
  * (accumulator in tensor memory), ordered on cuda_stream and completed on
  * return.  TSM_ERR_TIMEOUT if a bounded tensor-core wait ran out. */
 int tsm_umma_gemm(const void* A, const void* B, float* C, int M, int N, int K, int beta, void* cuda_stream);
+
+/* The same GEMM with leading dimensions (elements; lda, ldb >= K and
+ * multiples of 8, ldc >= N) and split-K: with splits > 1 the K range is cut
+ * into at most `splits` chunks of a multiple of 64 columns and chunk z writes
+ * its partial product to C + z * M * ldc (the caller sums the partials);
+ * *used_splits (may be NULL) receives the number of partials written.
+ * TSM_ERR_ARG for bad sizes, TSM_ERR_TIMEOUT as above. */
+int tsm_umma_gemm_ex(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M, int N, int K,
+                     int beta, int splits, int* used_splits, void* cuda_stream);
 
 /* ---- learned LP preconditioner (the paper has no network; this is the
  * project's extension of the LP solves of Sec. 2.2: because the HP - LP

@@ -15,40 +15,58 @@
 
 namespace tsm {
 
+namespace {
+
+template <int BN>
+int umma_launch(cudaStream_t stream, dim3 grid, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int M,
+                int N, int K, int ldc, int beta, int* error, int lda, int ldb, int kchunk, long long czs) {
+  const int smem = umma_smem_bytes<BN>();
+  if (cudaFuncSetAttribute(umma_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return TSM_ERR_CUDA;
+  umma_gemm_kernel<BN><<<grid, UMMA_THREADS, smem, stream>>>(A, B, C, M, N, K, ldc, beta, error, lda, ldb, kchunk,
+                                                             czs);
+  return cudaGetLastError() == cudaSuccess ? TSM_OK : TSM_ERR_CUDA;
+}
+
+}  // namespace
+
 // C (FP32) = A (BF16, rows of length lda) * B (BF16, rows of length ldb)^T over
 // K columns (+ C if beta).  splits > 1: split-K, partial z written to
-// C + z * M * ldc (the caller reduces).
+// C + z * M * ldc (the caller reduces); *used_splits receives the number of
+// partials written (never more than requested).  N is covered by
+// ceil(N / 256) tiles of equal width (a multiple of 16).
 int launch_umma_gemm_ex(cudaStream_t stream, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
                         float* C, int ldc, int M, int N, int K, int beta, int splits, int* error, int* used_splits) {
   if (used_splits) *used_splits = 0;
   if (M <= 0 || N <= 0) return TSM_OK;
-  if (K <= 0 || (lda % 8) != 0 || (ldb % 8) != 0) {
-    set_error("umma gemm needs K > 0 and row lengths that are multiples of 8 (K %d, lda %d, ldb %d)", K, lda, ldb);
+  if (K <= 0 || (K % 8) != 0 || (lda % 8) != 0 || (ldb % 8) != 0 || lda < K || ldb < K) {
+    set_error("umma gemm needs K > 0 and K, lda >= K, ldb >= K multiples of 8 (K %d, lda %d, ldb %d)", K, lda, ldb);
     return TSM_ERR_ARG;
   }
   if (splits < 1) splits = 1;
   int kchunk = (K + splits - 1) / splits;
   kchunk = (kchunk + UMMA_BK - 1) / UMMA_BK * UMMA_BK;   // whole stages per split, 16-byte aligned starts
-  splits = (K + kchunk - 1) / kchunk;   // never more than requested
+  splits = (K + kchunk - 1) / kchunk;                    // never more than requested
   if (used_splits) *used_splits = splits;
   const long long czs = (long long)M * ldc;
   const int gm = (M + UMMA_BM - 1) / UMMA_BM;
-#define TSM_UMMA_CASE(BN)                                                                                   \
-  if (N <= BN) {                                                                                            \
-    umma_gemm_kernel<BN><<<dim3(gm, 1, splits), UMMA_THREADS, 0, stream>>>(A, B, C, M, N, K, ldc, beta, error, \
-                                                                          lda, ldb, kchunk, czs);           \
-    return cudaGetLastError() == cudaSuccess ? TSM_OK : TSM_ERR_CUDA;                                       \
-  }
+  const int gn = (N + 255) / 256;
+  const int w = (N + gn - 1) / gn;
+  const dim3 grid(gm, gn, splits);
+#define TSM_UMMA_CASE(BN) \
+  if (w <= BN) return umma_launch<BN>(stream, grid, A, B, C, M, N, K, ldc, beta, error, lda, ldb, kchunk, czs);
   TSM_UMMA_CASE(16)
   TSM_UMMA_CASE(32)
+  TSM_UMMA_CASE(48)
   TSM_UMMA_CASE(64)
   TSM_UMMA_CASE(96)
   TSM_UMMA_CASE(128)
+  TSM_UMMA_CASE(160)
   TSM_UMMA_CASE(192)
+  TSM_UMMA_CASE(224)
+  TSM_UMMA_CASE(256)
 #undef TSM_UMMA_CASE
-  umma_gemm_kernel<128><<<dim3(gm, (N + 127) / 128, splits), UMMA_THREADS, 0, stream>>>(
-      A, B, C, M, N, K, ldc, beta, error, lda, ldb, kchunk, czs);
-  return cudaGetLastError() == cudaSuccess ? TSM_OK : TSM_ERR_CUDA;
+  return TSM_ERR_ARG;
 }
 
 int launch_umma_gemm(cudaStream_t stream, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int M, int N,
@@ -108,6 +126,10 @@ int Net::cmax() const {
 
 int Net::reserve(int V, int nb) {
   if (V == ws_V && nb <= ws_nb) return TSM_OK;
+  if ((long long)V * PT_PATHS * cmax() >= (1ll << 31) || (long long)nb * 3 * V * 8 * cmax() >= (1ll << 40)) {
+    set_error("lattice too large for the network kernels (V * 9 * C must stay below 2^31)");
+    return TSM_ERR_TOO_LARGE;
+  }
   const int L = (int)layers.size();
   for (float*& a : acts) dfree(a);
   dfree(Z);
@@ -186,7 +208,7 @@ int Net::backward(Ctx& c, const float* X0, int nb, const float* dY, float* dX0) 
                                                                                                           Zt);
     TSM_TRY(check_net_launch(c, "pt_transpose_kernel"));
     // dB^T = Z^T dY, split over the rows (sites x colours)
-    const int tiles = grid1(K2, UMMA_BM) * (N2 <= 192 ? 1 : grid1(N2, 128));
+    const int tiles = grid1(K2, UMMA_BM) * grid1(N2, 256);
     int splits = std::max(1, std::min(2 * 152 / tiles, grid1(M, 4 * UMMA_BK)));
     const size_t need = (size_t)splits * K2 * N2;
     if (need > part_cap) {
@@ -314,27 +336,35 @@ int zero_grads(Net& n, cudaStream_t s) {
 
 }  // namespace
 
-extern "C" int tsm_umma_gemm(const void* A, const void* B, float* C, int M, int N, int K, int beta,
-                             void* cuda_stream) {
+extern "C" int tsm_umma_gemm_ex(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M, int N,
+                                int K, int beta, int splits, int* used_splits, void* cuda_stream) {
   if (A == nullptr || B == nullptr || C == nullptr) return nbad(TSM_ERR_ARG, "tsm_umma_gemm: null argument");
+  if (ldc < N) return nbad(TSM_ERR_ARG, "tsm_umma_gemm: ldc < N");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   int* err = nullptr;
   TSM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&err), sizeof(int), s));
   TSM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-  int rc = launch_umma_gemm(s, static_cast<const __nv_bfloat16*>(A), static_cast<const __nv_bfloat16*>(B), C, M, N, K,
-                            N, beta, err);
+  int used = 0;
+  int rc = launch_umma_gemm_ex(s, static_cast<const __nv_bfloat16*>(A), lda, static_cast<const __nv_bfloat16*>(B), ldb,
+                               C, ldc, M, N, K, beta, splits, err, &used);
   int herr = 0;
   if (rc == TSM_OK) {
     TSM_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     TSM_CUDA(cudaStreamSynchronize(s));
   }
   cudaFreeAsync(err, s);
+  if (used_splits) *used_splits = used;
   if (rc != TSM_OK) {
-    set_error("tsm_umma_gemm: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    if (rc == TSM_ERR_CUDA) set_error("tsm_umma_gemm: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return rc;
   }
   if (herr) return nbad(TSM_ERR_TIMEOUT, "tsm_umma_gemm: a tensor-core wait timed out");
   return TSM_OK;
+}
+
+extern "C" int tsm_umma_gemm(const void* A, const void* B, float* C, int M, int N, int K, int beta,
+                             void* cuda_stream) {
+  return tsm_umma_gemm_ex(A, K, B, K, C, N, M, N, K, beta, 1, nullptr, cuda_stream);
 }
 
 extern "C" int tsm_net_create(int device, int n_layers, const int* channels, uint64_t seed, double init_scale,

@@ -10,8 +10,11 @@
 // Activation rows m = 3 * site + colour (lexicographic full-lattice site);
 // an activation with C channels has 8C FP32 columns: real parts
 // (c * 4 + s) in [0, 4C), imaginary parts at 4C + (c * 4 + s).  The gathered
-// matrix Z has 2K BF16 columns, K = 36 C: real parts (p * C + c) * 4 + s,
-// imaginary parts K + (p * C + c) * 4 + s.
+// matrix Z has 72 C BF16 columns: for each (path p, channel c), j = p * C + c,
+// the 16-byte group 8 j .. 8 j + 7 holds the real parts of spins 0..3 and
+// then their imaginary parts (one core-matrix row of the tensor-core layout).
+// The block weight matrix B [8 C_out][72 C_in] matches: row n < 4 C_out gives
+// the real part of output component n, row 4 C_out + n its imaginary part.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -43,34 +46,6 @@ __device__ __forceinline__ int lex_of(const Geom& g, const int c[4]) {
   return ((c[3] * g.L[2] + c[2]) * g.L[1] + c[1]) * g.L[0] + c[0];
 }
 
-// the three rows of U_mu at full-lattice site lex
-__device__ __forceinline__ void net_link(const NetGeom& ng, int lex, const int c[4], int mu, cx<float> r[9]) {
-  const int parity = (c[0] + c[1] + c[2] + c[3]) & 1;
-  const float4* base = ng.links + (size_t)parity * 4 * F32::LN * ng.lstride;
-  load_link<F32>(base, ng.lstride, mu, lex >> 1, r);
-  third_row(r, r + 6);
-}
-
-// neighbour of path p (1..8) of site c: returns its lex index and coords in cn,
-// the boundary sign, and whether the hop is forward
-__device__ __forceinline__ int path_neighbour(const Geom& g, const int c[4], int p, int cn[4], float* sign,
-                                              bool* fwd) {
-  const int mu = (p - 1) >> 1;
-  *fwd = ((p - 1) & 1) == 0;
-  cn[0] = c[0];
-  cn[1] = c[1];
-  cn[2] = c[2];
-  cn[3] = c[3];
-  if (*fwd) {
-    cn[mu] = (c[mu] + 1 == g.L[mu]) ? 0 : c[mu] + 1;
-    *sign = (mu == 3 && g.apbc && c[3] == g.L[3] - 1) ? -1.f : 1.f;
-  } else {
-    cn[mu] = (c[mu] == 0) ? g.L[mu] - 1 : c[mu] - 1;
-    *sign = (mu == 3 && g.apbc && c[3] == 0) ? -1.f : 1.f;
-  }
-  return lex_of(g, cn);
-}
-
 // one channel's 4 x 3 complex components at site `lex` of an activation
 __device__ __forceinline__ void load_channel(const float* __restrict__ X, int C, int lex, int ch, cx<float> v[4][3]) {
   const int w = 8 * C;
@@ -86,129 +61,168 @@ __device__ __forceinline__ void load_channel(const float* __restrict__ X, int C,
   }
 }
 
-// forward gather: Z rows 3x + a, columns of path p and channel c
-// (blockIdx.y = sample of a batch; samples are consecutive 3V-row blocks)
+// neighbour of site (x0..x3) along path p = 1..8 (scalar coordinates, no
+// runtime-indexed arrays): its lex index, parity, boundary sign, direction
+struct PathHop {
+  int src, src_parity, mu;
+  float sign;
+  bool fwd;
+};
+
+__device__ __forceinline__ PathHop path_hop(const Geom& g, int x0, int x1, int x2, int x3, int p) {
+  PathHop h;
+  h.mu = (p - 1) >> 1;
+  h.fwd = ((p - 1) & 1) == 0;
+  h.sign = 1.f;
+  int y0 = x0, y1 = x1, y2 = x2, y3 = x3;
+  switch (h.mu) {
+    case 0: y0 = h.fwd ? (x0 + 1 == g.L[0] ? 0 : x0 + 1) : (x0 == 0 ? g.L[0] - 1 : x0 - 1); break;
+    case 1: y1 = h.fwd ? (x1 + 1 == g.L[1] ? 0 : x1 + 1) : (x1 == 0 ? g.L[1] - 1 : x1 - 1); break;
+    case 2: y2 = h.fwd ? (x2 + 1 == g.L[2] ? 0 : x2 + 1) : (x2 == 0 ? g.L[2] - 1 : x2 - 1); break;
+    default:
+      y3 = h.fwd ? (x3 + 1 == g.L[3] ? 0 : x3 + 1) : (x3 == 0 ? g.L[3] - 1 : x3 - 1);
+      if (g.apbc && (h.fwd ? x3 == g.L[3] - 1 : x3 == 0)) h.sign = -1.f;
+      break;
+  }
+  h.src = ((y3 * g.L[2] + y2) * g.L[1] + y1) * g.L[0] + y0;
+  h.src_parity = (y0 + y1 + y2 + y3) & 1;
+  return h;
+}
+
+// the three rows of U_mu at the site with lex index `lex` and parity `par`
+__device__ __forceinline__ void net_link_at(const NetGeom& ng, int lex, int par, int mu, cx<float> r[9]) {
+  const float4* base = ng.links + (size_t)par * 4 * F32::LN * ng.lstride;
+  load_link<F32>(base, ng.lstride, mu, lex >> 1, r);
+  third_row(r, r + 6);
+}
+
+// effective transport matrix of a hop: w = sign * U (forward) or sign * U^dag
+// (backward), so that the transported colour vector is w v in both cases
+__device__ __forceinline__ void effective_link(const cx<float> u[9], bool fwd, float sign, cx<float> w[9]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const cx<float> e = fwd ? u[3 * a + b] : cconj(u[3 * b + a]);
+      w[3 * a + b] = sign * e;
+    }
+}
+
+// forward gather: Z rows 3x + a, the column group of path p and channel c.
+// One thread per (site, path, channel), channel fastest, so a warp writes
+// contiguous 16-byte groups of each row.  blockIdx.y = sample of a batch
+// (consecutive 3V-row blocks).
 __global__ void __launch_bounds__(NET_NT) pt_gather_kernel(NetGeom ng, const float* __restrict__ X, int C,
                                                           __nv_bfloat16* __restrict__ Z) {
-  const long long tid = (long long)blockIdx.x * NET_NT + threadIdx.x;
-  if (tid >= (long long)ng.g.V * PT_PATHS * C) return;
+  const int tid = blockIdx.x * NET_NT + threadIdx.x;   // V * 9 * C < 2^31 (checked by the host)
+  if (tid >= ng.g.V * PT_PATHS * C) return;
   X += (size_t)blockIdx.y * 3 * ng.g.V * 8 * C;
   Z += (size_t)blockIdx.y * 3 * ng.g.V * 72 * C;
-  const int ch = (int)(tid % C);
-  const int p = (int)((tid / C) % PT_PATHS);
-  const int x = (int)(tid / ((long long)C * PT_PATHS));
-  int c[4];
-  lex_coords(ng.g, x, c);
+  const int xp = tid / C;
+  const int ch = tid - xp * C;
+  const int x = xp / PT_PATHS;
+  const int p = xp - x * PT_PATHS;
+  const Geom& g = ng.g;
+  int r = x;
+  const int x0 = r % g.L[0];
+  r /= g.L[0];
+  const int x1 = r % g.L[1];
+  r /= g.L[1];
+  const int x2 = r % g.L[2];
+  const int x3 = r / g.L[2];
   cx<float> v[4][3], out[4][3];
   if (p == 0) {
     load_channel(X, C, x, ch, out);
   } else {
-    int cn[4];
-    float sign;
-    bool fwd;
-    const int src = path_neighbour(ng.g, c, p, cn, &sign, &fwd);
-    load_channel(X, C, src, ch, v);
-    cx<float> u[9];
-    const int mu = (p - 1) >> 1;
-    if (fwd) net_link(ng, x, c, mu, u);     // U_mu(x)
-    else net_link(ng, src, cn, mu, u);      // U_mu(x - mu), used as U^dag
+    const PathHop h = path_hop(g, x0, x1, x2, x3, p);
+    load_channel(X, C, h.src, ch, v);
+    cx<float> u[9], w[9];
+    if (h.fwd) net_link_at(ng, x, (x0 + x1 + x2 + x3) & 1, h.mu, u);   // U_mu(x)
+    else net_link_at(ng, h.src, h.src_parity, h.mu, u);                // U_mu(x - mu), applied as U^dag
+    effective_link(u, h.fwd, h.sign, w);
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
+    for (int s2 = 0; s2 < 4; ++s2)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        cx<float> acc = {0.f, 0.f};
-#pragma unroll
-        for (int b = 0; b < 3; ++b) acc = acc + (fwd ? u[3 * a + b] * v[s][b] : cjmul(u[3 * b + a], v[s][b]));
-        out[s][a] = sign * acc;
-      }
+      for (int a = 0; a < 3; ++a) out[s2][a] = w[3 * a] * v[s2][0] + w[3 * a + 1] * v[s2][1] + w[3 * a + 2] * v[s2][2];
   }
-  const int K = 36 * C;
-  const int k = (p * C + ch) * 4;
+  const int j8 = (p * C + ch) * 8;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    __nv_bfloat16* row = Z + (size_t)(3 * x + a) * (2 * K);
     __nv_bfloat162 r01 = __floats2bfloat162_rn(out[0][a].re, out[1][a].re);
     __nv_bfloat162 r23 = __floats2bfloat162_rn(out[2][a].re, out[3][a].re);
     __nv_bfloat162 i01 = __floats2bfloat162_rn(out[0][a].im, out[1][a].im);
     __nv_bfloat162 i23 = __floats2bfloat162_rn(out[2][a].im, out[3][a].im);
-    uint2 rr, ii;
-    rr.x = *reinterpret_cast<uint32_t*>(&r01);
-    rr.y = *reinterpret_cast<uint32_t*>(&r23);
-    ii.x = *reinterpret_cast<uint32_t*>(&i01);
-    ii.y = *reinterpret_cast<uint32_t*>(&i23);
-    *reinterpret_cast<uint2*>(row + k) = rr;
-    *reinterpret_cast<uint2*>(row + K + k) = ii;
+    uint4 q;
+    q.x = *reinterpret_cast<uint32_t*>(&r01);
+    q.y = *reinterpret_cast<uint32_t*>(&r23);
+    q.z = *reinterpret_cast<uint32_t*>(&i01);
+    q.w = *reinterpret_cast<uint32_t*>(&i23);
+    *reinterpret_cast<uint4*>(Z + (size_t)(3 * x + a) * (72 * C) + j8) = q;
   }
 }
 
-// backward gather (adjoint transports): dX(y)_c = sum_p (T_p^dag dZ_{p,c})(y)
+// backward gather (adjoint transports): dX(y)_c = sum_p (T_p^dag dZ_{p,c})(y).
+// T_p^dag is the transport of the opposite hop of the same direction
+// (T_{2mu+1}^dag = T_{2mu+2} and back, same boundary sign), so the neighbour
+// and link come from path_hop of the swapped path.
 __global__ void __launch_bounds__(NET_NT) pt_gather_adjoint_kernel(NetGeom ng, const float* __restrict__ dZ, int C,
                                                                   float* __restrict__ dX) {
-  const long long tid = (long long)blockIdx.x * NET_NT + threadIdx.x;
-  if (tid >= (long long)ng.g.V * C) return;
+  const int tid = blockIdx.x * NET_NT + threadIdx.x;
+  if (tid >= ng.g.V * C) return;
   dZ += (size_t)blockIdx.y * 3 * ng.g.V * 72 * C;
   dX += (size_t)blockIdx.y * 3 * ng.g.V * 8 * C;
-  const int ch = (int)(tid % C);
-  const int y = (int)(tid / C);
+  const int y = tid / C;
+  const int ch = tid - y * C;
   const int K = 36 * C;
-  int c[4];
-  lex_coords(ng.g, y, c);
+  const Geom& g = ng.g;
+  int r = y;
+  const int x0 = r % g.L[0];
+  r /= g.L[0];
+  const int x1 = r % g.L[1];
+  r /= g.L[1];
+  const int x2 = r % g.L[2];
+  const int x3 = r / g.L[2];
   cx<float> acc[4][3];
 #pragma unroll
-  for (int s = 0; s < 4; ++s)
+  for (int s2 = 0; s2 < 4; ++s2)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) acc[s][a] = {0.f, 0.f};
+    for (int a = 0; a < 3; ++a) acc[s2][a] = {0.f, 0.f};
   for (int p = 0; p < PT_PATHS; ++p) {
-    const int k = (p * C + ch) * 4;
+    const int j8 = (p * C + ch) * 8;
     int src = y;
-    float sign = 1.f;
-    cx<float> u[9];
-    bool have_link = false, dag = false;
+    cx<float> w[9];
     if (p > 0) {
-      const int mu = (p - 1) >> 1;
-      const bool fwd = ((p - 1) & 1) == 0;
-      int cn[4] = {c[0], c[1], c[2], c[3]};
-      if (fwd) {
-        // (T^dag h)(y) = s(y - mu) U_mu(y - mu)^dag h(y - mu)
-        cn[mu] = (c[mu] == 0) ? ng.g.L[mu] - 1 : c[mu] - 1;
-        sign = (mu == 3 && ng.g.apbc && cn[3] == ng.g.L[3] - 1) ? -1.f : 1.f;
-        src = lex_of(ng.g, cn);
-        net_link(ng, src, cn, mu, u);
-        dag = true;
-      } else {
-        // (T^dag h)(y) = s'(y + mu) U_mu(y) h(y + mu)
-        cn[mu] = (c[mu] + 1 == ng.g.L[mu]) ? 0 : c[mu] + 1;
-        sign = (mu == 3 && ng.g.apbc && cn[3] == 0) ? -1.f : 1.f;
-        src = lex_of(ng.g, cn);
-        net_link(ng, y, c, mu, u);
-        dag = false;
-      }
-      have_link = true;
+      const int q = ((p - 1) & 1) ? p - 1 : p + 1;   // the opposite hop
+      const PathHop h = path_hop(g, x0, x1, x2, x3, q);
+      src = h.src;
+      cx<float> u[9];
+      if (h.fwd) net_link_at(ng, y, (x0 + x1 + x2 + x3) & 1, h.mu, u);
+      else net_link_at(ng, src, h.src_parity, h.mu, u);
+      effective_link(u, h.fwd, h.sign, w);
     }
     cx<float> v[4][3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      const float* row = dZ + (size_t)(3 * src + b) * (2 * K);
-      const float4 re = *reinterpret_cast<const float4*>(row + k);
-      const float4 im = *reinterpret_cast<const float4*>(row + K + k);
+      const float* row = dZ + (size_t)(3 * src + b) * (2 * K) + j8;
+      const float4 re = *reinterpret_cast<const float4*>(row);
+      const float4 im = *reinterpret_cast<const float4*>(row + 4);
       v[0][b] = {re.x, im.x};
       v[1][b] = {re.y, im.y};
       v[2][b] = {re.z, im.z};
       v[3][b] = {re.w, im.w};
     }
+    if (p == 0) {
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
+      for (int s2 = 0; s2 < 4; ++s2)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (!have_link) {
-          acc[s][a] = acc[s][a] + v[s][a];
-        } else {
-          cx<float> t = {0.f, 0.f};
+        for (int a = 0; a < 3; ++a) acc[s2][a] = acc[s2][a] + v[s2][a];
+    } else {
 #pragma unroll
-          for (int b = 0; b < 3; ++b) t = t + (dag ? cjmul(u[3 * b + a], v[s][b]) : u[3 * a + b] * v[s][b]);
-          acc[s][a] = acc[s][a] + sign * t;
-        }
-      }
+      for (int s2 = 0; s2 < 4; ++s2)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          acc[s2][a] = acc[s2][a] + w[3 * a] * v[s2][0] + w[3 * a + 1] * v[s2][1] + w[3 * a + 2] * v[s2][2];
+    }
   }
   const int w = 8 * C;
 #pragma unroll
@@ -356,43 +370,48 @@ __global__ void __launch_bounds__(NET_NT) pt_act_to_canon_kernel(int V, int C, c
     }
 }
 
-// complex FP32 weights [N4][K36] (N4 = 4 C_out, K36 = 36 C_in) -> BF16 block
-// matrix B [2 N4][2 K36] = [[Wr, -Wi], [Wi, Wr]] and its transpose Bt
+// complex FP32 weights [N4][K36] (N4 = 4 C_out, K36 = 36 C_in, column
+// kk = 4 j + s) -> BF16 block matrix B [2 N4][72 C_in] in the interleaved
+// column layout of Z and its transpose Bt:
+//   B[n][8j+s] = Wr, B[n][8j+4+s] = -Wi, B[N4+n][8j+s] = Wi, B[N4+n][8j+4+s] = Wr
 __global__ void pt_pack_weights_kernel(const float* __restrict__ wr, const float* __restrict__ wi, int N4, int K36,
                                        __nv_bfloat16* __restrict__ B, __nv_bfloat16* __restrict__ Bt) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= N4 * K36) return;
-  const int n = idx / K36, k = idx % K36;
+  const int n = idx / K36, kk = idx % K36;
+  const int kr = 2 * kk - (kk & 3), ki = kr + 4;   // 8 (kk / 4) + (kk % 4) and its imaginary slot
   const float r = wr[idx], i = wi[idx];
   const int K2 = 2 * K36, N2 = 2 * N4;
   const __nv_bfloat16 br = __float2bfloat16(r), bi = __float2bfloat16(i), bmi = __float2bfloat16(-i);
-  B[(size_t)n * K2 + k] = br;
-  B[(size_t)n * K2 + K36 + k] = bmi;
-  B[(size_t)(N4 + n) * K2 + k] = bi;
-  B[(size_t)(N4 + n) * K2 + K36 + k] = br;
-  Bt[(size_t)k * N2 + n] = br;
-  Bt[(size_t)(K36 + k) * N2 + n] = bmi;
-  Bt[(size_t)k * N2 + N4 + n] = bi;
-  Bt[(size_t)(K36 + k) * N2 + N4 + n] = br;
+  B[(size_t)n * K2 + kr] = br;
+  B[(size_t)n * K2 + ki] = bmi;
+  B[(size_t)(N4 + n) * K2 + kr] = bi;
+  B[(size_t)(N4 + n) * K2 + ki] = br;
+  Bt[(size_t)kr * N2 + n] = br;
+  Bt[(size_t)ki * N2 + n] = bmi;
+  Bt[(size_t)kr * N2 + N4 + n] = bi;
+  Bt[(size_t)ki * N2 + N4 + n] = br;
 }
 
-// split-K partials of dB^T [splits][2 K36][2 N4] (dB = dL/dB of the block
-// matrix B) -> complex weight gradient (+=), G = dL/dWr + i dL/dWi:
-// dL/dWr = dB[n][k] + dB[N4+n][K36+k], dL/dWi = dB[N4+n][k] - dB[n][K36+k]
+// split-K partials of dB^T [splits][72 C_in][2 N4] (dB = dL/dB of the block
+// matrix B, interleaved columns) -> complex weight gradient (+=),
+// G = dL/dWr + i dL/dWi:
+//   dL/dWr = dB[n][8j+s] + dB[N4+n][8j+4+s],  dL/dWi = dB[N4+n][8j+s] - dB[n][8j+4+s]
 __global__ void pt_weight_grad_kernel(const float* __restrict__ part, int splits, int N4, int K36,
                                       float* __restrict__ gr, float* __restrict__ gi) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= N4 * K36) return;
-  const int n = idx / K36, k = idx % K36;
+  const int n = idx / K36, kk = idx % K36;
+  const int kr = 2 * kk - (kk & 3), ki = kr + 4;
   const int N2 = 2 * N4;
   const size_t zs = (size_t)2 * K36 * N2;
   float a = 0.f, b = 0.f, c = 0.f, d = 0.f;
   for (int z = 0; z < splits; ++z) {
     const float* P = part + z * zs;
-    a += P[(size_t)k * N2 + n];
-    b += P[(size_t)(K36 + k) * N2 + N4 + n];
-    c += P[(size_t)k * N2 + N4 + n];
-    d += P[(size_t)(K36 + k) * N2 + n];
+    a += P[(size_t)kr * N2 + n];
+    b += P[(size_t)ki * N2 + N4 + n];
+    c += P[(size_t)kr * N2 + N4 + n];
+    d += P[(size_t)ki * N2 + n];
   }
   gr[idx] += a + b;
   gi[idx] += c - d;

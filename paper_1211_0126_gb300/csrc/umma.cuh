@@ -3,14 +3,17 @@
 //   C[M x N] (FP32) = A[M x K] (BF16, row-major) * B[N x K]^T (BF16, row-major)
 //
 // used by the channel-mixing layers of the learned preconditioner.  One CTA
-// (128 threads) computes a 128 x BN tile: the operand tiles are staged in
-// shared memory in the canonical K-major layout without swizzle (8-row x
-// 16-byte core matrices, K-adjacent cores 128 B apart, 8-row groups
-// (K_TILE / 8) * 128 B apart), one elected thread issues tcgen05.mma with the
-// accumulator in tensor memory (TMEM), completion is signalled through an
-// mbarrier by tcgen05.commit, and the epilogue reads TMEM with tcgen05.ld.
-// Every wait is bounded: on timeout the CTA records an error flag, still
-// frees its TMEM and returns.
+// (128 threads) computes a 128 x BN tile of C over its K range through a
+// 3- or 4-deep ring of shared-memory stages: all threads copy operand
+// tiles with cp.async (16 bytes per copy, zero fill outside the matrices)
+// into the canonical K-major layout without swizzle (8-row x 16-byte core
+// matrices, K-adjacent cores 128 B apart, 8-row groups (UMMA_BK / 8) * 128 B
+// apart) while one thread issues tcgen05.mma on the stage that has landed,
+// with the accumulator in tensor memory (TMEM).  tcgen05.commit arrives on the
+// stage's mbarrier when its MMAs are done, which frees the stage for the copy
+// UMMA_STAGES - 1 tiles ahead.  The epilogue reads TMEM with tcgen05.ld.
+// Every wait is bounded: on timeout the CTA records an error flag, waits
+// (bounded) for its copies and MMAs in flight, frees its TMEM and returns.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -21,6 +24,14 @@ namespace tsm {
 constexpr int UMMA_BM = 128;
 constexpr int UMMA_BK = 64;              // K elements per shared-memory stage (4 MMAs of K = 16)
 constexpr int UMMA_THREADS = 128;
+constexpr int UMMA_A_BYTES = UMMA_BM * UMMA_BK * 2;
+// ring depth: 4 stages for narrow tiles, 3 for BN >= 64 so that two CTAs fit
+// in one SM's shared memory (one CTA's epilogue overlaps the other's loads)
+template <int BN> __host__ __device__ constexpr int umma_stages() { return BN >= 64 ? 3 : 4; }
+template <int BN> __host__ __device__ constexpr int umma_stage_bytes() { return UMMA_A_BYTES + BN * UMMA_BK * 2; }
+template <int BN> __host__ __device__ constexpr int umma_smem_bytes() {
+  return umma_stages<BN>() * umma_stage_bytes<BN>() + 1024;
+}
 constexpr long long UMMA_SPIN_LIMIT = 1ll << 26;   // bounded mbarrier wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -64,57 +75,56 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-// tile of R rows x UMMA_BK columns of a row-major BF16 matrix (leading
-// dimension ld, rows >= nrows / columns >= ncols zero-filled) -> canonical
-// K-major core-matrix layout in shared memory
+// cp.async of one R-row x UMMA_BK-column tile of a row-major BF16 matrix
+// (leading dimension ld; rows >= nrows and columns >= ncols are zero-filled;
+// ncols and ld multiples of 8) into the canonical K-major core-matrix layout
 template <int R>
-__device__ __forceinline__ void stage_tile(const __nv_bfloat16* __restrict__ g, int ld, int row0, int nrows, int k0,
-                                           int ncols, uint8_t* s) {
-  // R rows x 8 chunks of 16 bytes (8 BF16 each)
+__device__ __forceinline__ void copy_tile_async(const __nv_bfloat16* __restrict__ g, int ld, int row0, int nrows,
+                                                int k0, int ncols, uint32_t s) {
+#pragma unroll 2
   for (int idx = threadIdx.x; idx < R * (UMMA_BK / 8); idx += UMMA_THREADS) {
     const int r = idx / (UMMA_BK / 8), kc = idx % (UMMA_BK / 8);
     const int row = row0 + r, col = k0 + kc * 8;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (row < nrows) {
-      if (col + 8 <= ncols) {
-        v = *reinterpret_cast<const uint4*>(g + (size_t)row * ld + col);
-      } else if (col < ncols) {
-        __nv_bfloat16 tmp[8];
-        for (int e = 0; e < 8; ++e) tmp[e] = (col + e < ncols) ? g[(size_t)row * ld + col + e] : __float2bfloat16(0.f);
-        v = *reinterpret_cast<uint4*>(tmp);
-      }
-    }
-    // core matrix (r / 8, kc): 8 rows x 16 B; K-adjacent cores 128 B apart
-    const int off = ((r >> 3) * (UMMA_BK / 8) + kc) * 128 + (r & 7) * 16;
-    *reinterpret_cast<uint4*>(s + off) = v;
+    const bool in = row < nrows && col < ncols;
+    const __nv_bfloat16* src = in ? g + (size_t)row * ld + col : g;   // valid address, nothing read when !in
+    const uint32_t dst = s + ((r >> 3) * (UMMA_BK / 8) + kc) * 128 + (r & 7) * 16;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(in ? 16 : 0)
+                 : "memory");
   }
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // C = A * B^T  (A: M x K, B: N x K, row-major BF16; C: M x N FP32 row-major,
 // leading dimension ldc; beta = 0 overwrites, 1 accumulates into C).
-// BN = tile width (multiple of 16, <= 192: the static shared memory holds
-// both stages within 48 KB); K need not be a multiple of 64
-// (zero-filled) but the rows of A and B must start 16-byte aligned (K % 8 == 0).
-//
-// Split-K: blockIdx.z covers K range [z * kchunk, (z + 1) * kchunk) and writes
-// its partial product to C + z * czstride (reduced afterwards by the caller).
+// BN = tile width (multiple of 16 in [16, 256]); K, lda, ldb multiples of 8.
+// Split-K: blockIdx.z covers K range [z * kchunk, (z + 1) * kchunk) (kchunk a
+// multiple of UMMA_BK) and writes its partial product to C + z * czstride.
+// Dynamic shared memory: umma_smem_bytes<BN>().
 template <int BN>
 __global__ void __launch_bounds__(UMMA_THREADS) umma_gemm_kernel(const __nv_bfloat16* __restrict__ A,
                                                                  const __nv_bfloat16* __restrict__ B,
                                                                  float* __restrict__ C, int M, int N, int K,
                                                                  int ldc, int beta, int* __restrict__ error,
                                                                  int lda, int ldb, int kchunk, long long czstride) {
-  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 192, "BN must be a multiple of 16 in [16, 192]");
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "BN must be a multiple of 16 in [16, 256]");
   constexpr int TMEM_COLS = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
-  __shared__ __align__(1024) uint8_t sA[UMMA_BM * UMMA_BK * 2];
-  __shared__ __align__(1024) uint8_t sB[BN * UMMA_BK * 2];
-  __shared__ __align__(8) uint64_t mma_bar;
+  constexpr int SB = umma_stage_bytes<BN>();
+  constexpr int UMMA_STAGES = umma_stages<BN>();
+  extern __shared__ uint8_t umma_dyn[];
+  __shared__ __align__(8) uint64_t bar[UMMA_STAGES];
   __shared__ uint32_t tmem_slot;
   __shared__ int timed_out;
+  // 1024-byte aligned ring of stages
+  const uint32_t ring = (smem_u32(umma_dyn) + 1023u) & ~1023u;
   const int m0 = blockIdx.x * UMMA_BM, n0 = blockIdx.y * BN;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    mbar_init(&mma_bar, 1);
+#pragma unroll
+    for (int s = 0; s < UMMA_STAGES; ++s) mbar_init(&bar[s], 1);
     timed_out = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -128,21 +138,31 @@ __global__ void __launch_bounds__(UMMA_THREADS) umma_gemm_kernel(const __nv_bflo
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
   constexpr uint32_t idesc = umma_idesc_bf16(UMMA_BM, BN);
-  // this CTA's K range (split-K along blockIdx.z)
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
   const int ktiles = kend > kbeg ? (kend - kbeg + UMMA_BK - 1) / UMMA_BK : 0;
   C += (size_t)blockIdx.z * (size_t)czstride;
-  uint32_t phase = 0;
+  int last = -1;   // last tile whose MMAs were committed
+  auto load = [&](int kt, int s) {
+    const uint32_t sa = ring + s * SB;
+    copy_tile_async<UMMA_BM>(A, lda, m0, M, kbeg + kt * UMMA_BK, kend, sa);
+    copy_tile_async<BN>(B, ldb, n0, N, kbeg + kt * UMMA_BK, kend, sa + UMMA_A_BYTES);
+  };
+  // prologue: tiles 0 .. STAGES-2 in flight (one commit group per tile, empty groups keep the count)
+#pragma unroll
+  for (int s = 0; s < UMMA_STAGES - 1; ++s) {
+    if (s < ktiles) load(s, s);
+    cp_async_commit();
+  }
   for (int kt = 0; kt < ktiles; ++kt) {
-    stage_tile<UMMA_BM>(A, lda, m0, M, kbeg + kt * UMMA_BK, kend, sA);
-    stage_tile<BN>(B, ldb, n0, N, kbeg + kt * UMMA_BK, kend, sB);
+    const int s = kt % UMMA_STAGES;
+    cp_async_wait<UMMA_STAGES - 2>();   // this thread's copies of tile kt have landed
     // generic-proxy writes of shared memory -> visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      const uint32_t a0 = ring + s * SB, b0 = a0 + UMMA_A_BYTES;
 #pragma unroll
       for (int kk = 0; kk < UMMA_BK / 16; ++kk) {
         // K = 16 per MMA = two K-adjacent core matrices (256 B further per step)
@@ -155,20 +175,33 @@ __global__ void __launch_bounds__(UMMA_THREADS) umma_gemm_kernel(const __nv_bflo
             "l"(da), "l"(db), "r"(idesc), "r"(acc));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&mma_bar))
+                       smem_u32(&bar[s]))
                    : "memory");
     }
-    // wait until the MMAs of this stage have read shared memory and finished
-    if (!mbar_wait(&mma_bar, phase)) timed_out = 1;
-    phase ^= 1u;
-    __syncthreads();
-    if (timed_out) break;
+    last = kt;
+    // refill the stage of tile kt-1 with tile kt+STAGES-1 once tile kt-1's MMAs are done
+    const int nk = kt + UMMA_STAGES - 1;
+    if (nk < ktiles) {
+      const int ps = nk % UMMA_STAGES;
+      if (kt >= 1 && !mbar_wait(&bar[ps], (uint32_t)(((kt - 1) / UMMA_STAGES) & 1))) timed_out = 1;
+      __syncthreads();
+      if (timed_out) break;
+      load(nk, ps);
+    }
+    cp_async_commit();
   }
+  // all MMAs done: the commit of the last tile covers every earlier MMA
+  if (last >= 0 && !timed_out) {
+    if (!mbar_wait(&bar[last % UMMA_STAGES], (uint32_t)((last / UMMA_STAGES) & 1))) timed_out = 1;
+  }
+  cp_async_wait<0>();
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!timed_out) {
     // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31 (an empty
     // split-K range contributes zeros)
     const int row = m0 + warp * 32 + lane;
+    const bool vec = (ldc % 4) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
     for (int c0 = 0; c0 < BN; c0 += 8) {
       uint32_t v[8];
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
@@ -177,26 +210,31 @@ __global__ void __launch_bounds__(UMMA_THREADS) umma_gemm_kernel(const __nv_bflo
           : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (ktiles == 0) {
+      float f[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = 0u;
-      }
-      if (row < M) {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int col = n0 + c0 + e;
-          if (col < N) {
-            float* dst = C + (size_t)row * ldc + col;
-            const float val = __uint_as_float(v[e]);
-            *dst = beta ? *dst + val : val;
+      for (int e = 0; e < 8; ++e) f[e] = ktiles == 0 ? 0.f : __uint_as_float(v[e]);
+      const int col = n0 + c0;
+      if (row < M && col < N) {
+        float* dst = C + (size_t)row * ldc + col;
+        if (vec && col + 8 <= N) {
+          float4 lo = make_float4(f[0], f[1], f[2], f[3]), hi = make_float4(f[4], f[5], f[6], f[7]);
+          if (beta) {
+            const float4 a = *reinterpret_cast<const float4*>(dst), b = *reinterpret_cast<const float4*>(dst + 4);
+            lo = make_float4(lo.x + a.x, lo.y + a.y, lo.z + a.z, lo.w + a.w);
+            hi = make_float4(hi.x + b.x, hi.y + b.y, hi.z + b.z, hi.w + b.w);
           }
+          *reinterpret_cast<float4*>(dst) = lo;
+          *reinterpret_cast<float4*>(dst + 4) = hi;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            if (col + e < N) dst[e] = beta ? dst[e] + f[e] : f[e];
         }
       }
     }
-  }
-  if (timed_out) {
+  } else {
     // give MMAs still in flight a second bounded wait before TMEM is released
-    mbar_wait(&mma_bar, phase);
+    if (last >= 0) mbar_wait(&bar[last % UMMA_STAGES], (uint32_t)((last / UMMA_STAGES) & 1));
     if (threadIdx.x == 0 && error != nullptr) atomicExch(error, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -77,6 +77,9 @@ _SIGS = {
                                        ctypes.POINTER(TsmLoopStats)]),
     "tsm_tune_batch": (ctypes.c_int, [_P, ctypes.POINTER(TmStop), ctypes.POINTER(ctypes.c_int), _P]),
     "tsm_umma_gemm": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "tsm_umma_gemm_ex": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int), _P]),
     "tsm_net_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint64, ctypes.c_double,
                                       ctypes.POINTER(_P)]),
     "tsm_net_destroy": (ctypes.c_int, [_P]),
@@ -417,6 +420,26 @@ def tsm_net_loss(n, group):
 
 def tsm_set_precond(h, n):
     _check(library().tsm_set_precond(h, n), "tsm_set_precond")
+
+
+def tsm_umma_gemm_ex(A, B, C, splits=1, beta=0, stream=None):
+    """Split-K form: A (M, K) and B (N, K) bfloat16 (row strides may exceed K),
+    C (splits, M, N) float32 receives the partial products; returns the number
+    of partials written."""
+    import torch
+    for t, dt in ((A, torch.bfloat16), (B, torch.bfloat16), (C, torch.float32)):
+        if not (t.is_cuda and t.dtype == dt and t.stride(-1) == 1):
+            raise ValueError("tsm_umma_gemm_ex wants CUDA tensors (bf16, bf16, fp32) with unit inner stride")
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K or tuple(C.shape[-2:]) != (M, N) or not C.is_contiguous():
+        raise ValueError("shape mismatch")
+    used = ctypes.c_int(0)
+    _check(library().tsm_umma_gemm_ex(ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.c_void_p(B.data_ptr()),
+                                      B.stride(0), ctypes.c_void_p(C.data_ptr()), N, M, N, K, int(beta),
+                                      int(splits), ctypes.byref(used), ctypes.c_void_p(stream or 0)),
+           "tsm_umma_gemm_ex")
+    return used.value
 
 
 def tsm_profile(h, enable):
