@@ -20,6 +20,24 @@ counts N_HP + N_LP low-precision inversions).
 Error (reading; the paper gives none): sigma^2 = Var_corr / N_HP + Var_LP / N_LP
 with Var the unbiased sample variance of the complex per-source values,
 Var = sum |X_j - mean|^2 / (N - 1).
+
+One-end trick (Sec. 2.3, Eq. 2.5) for the isovector loop u - d of twisted
+mass, D_u = D_tm(+mu), D_d = D_tm(-mu) = gamma5 D_u^dag gamma5.  Since
+D_u - D_d = 4 i kappa mu gamma5 in this normalisation,
+
+    D_u^-1 - D_d^-1 = -4 i kappa mu D_u^-1 D_u^-dag gamma5,
+
+so with s = D_u^-1 eta and E[eta eta^dag] = 1,
+
+    Tr[P Gamma (D_u^-1 - D_d^-1)] = -4 i kappa mu E[s^dag gamma5 P Gamma s]
+
+(P: the diagonal timeslice / phase projector, which commutes with gamma5).
+The per-source value is L^1_j(Gamma, t, q) = -4 i kappa mu
+sum_{x: x_4 = t} e^{iq.x} s_j(x)^dag gamma5 Gamma s_j(x); it is quadratic in s,
+so the TSM correction is L^1(s_HP) - L^1(s_LP).  The paper writes the same
+identity for M = D / (2 kappa) in physical units (-2 i mu a M_d^-1 gamma5
+M_u^-1); the factor and sign here are those of D_tm itself, fixed by the
+dense-matrix pins in tests.
 """
 import numpy as np
 
@@ -46,6 +64,16 @@ def local_loops(eta, s, dims, gammas, moms):
     dens = np.einsum('tzyxac,gab,tzyxbc->gtzyx', np.conj(eta), G, s)
     ph = phases(dims, moms)
     return np.einsum('qtzyx,gtzyx->gqt', ph, dens)
+
+
+def one_end_loops(s, dims, kappa, mu, gammas, moms):
+    """One-end-trick value of one source s = D_u^-1 eta: [n_gamma, n_q, T] complex."""
+    G = gamma_list()[list(gammas)]
+    g5 = np.diag([1.0, 1.0, -1.0, -1.0])
+    G5 = np.einsum('ab,gbc->gac', g5, G)              # gamma5 Gamma
+    dens = np.einsum('tzyxac,gab,tzyxbc->gtzyx', np.conj(s), G5, s)
+    ph = phases(dims, moms)
+    return -4j * kappa * mu * np.einsum('qtzyx,gtzyx->gqt', ph, dens)
 
 
 def exact_loops(Dinv, dims, gammas, moms):
@@ -87,26 +115,33 @@ def tsm_combine(corr, lp):
 
 
 def tsm_loops(U, dims, kappa, mu, seed, noise_kind, n_hp, n_lp, hp_stop, lp_stop,
-              gammas, moms, antiperiodic_t=True):
+              gammas, moms, antiperiodic_t=True, estimator='standard'):
     """The whole TSM estimate, source by source, in the order of Eq. 2.4.
 
     hp_stop / lp_stop = (rel_tol, max_iter).  Source j uses eta_j from
-    oracle.philox.noise(seed, j, ...).  Returns a dict with the estimate, its
-    error, the LP-only mean over the LP set, the mean correction, the per-source
-    loops and iteration counts.
+    oracle.philox.noise(seed, j, ...).  estimator: 'standard' (eta^dag Gamma s,
+    loops of D_u^-1) or 'one_end' (Eq. 2.5, loops of D_u^-1 - D_d^-1).
+    Returns a dict with the estimate, its error, the LP-only mean over the LP
+    set, the mean correction, the per-source loops and iteration counts.
     """
+    if estimator == 'one_end':
+        def value(eta, s):
+            return one_end_loops(s, dims, kappa, mu, gammas, moms)
+    else:
+        def value(eta, s):
+            return local_loops(eta, s, dims, gammas, moms)
     corr, lp_vals, hp_iters, lp_iters = [], [], [], []
     for j in range(n_hp + n_lp):
         eta = philox.noise(seed, j, dims, noise_kind)
         s_lp, it_lp, _, _ = solver.solve_full(U, eta, dims, kappa, mu, lp_stop[0], lp_stop[1],
                                               antiperiodic_t)
         lp_iters.append(it_lp)
-        l_lp = local_loops(eta, s_lp, dims, gammas, moms)
+        l_lp = value(eta, s_lp)
         if j < n_hp:
             s_hp, it_hp, _, _ = solver.solve_full(U, eta, dims, kappa, mu, hp_stop[0], hp_stop[1],
                                                   antiperiodic_t)
             hp_iters.append(it_hp)
-            corr.append(local_loops(eta, s_hp, dims, gammas, moms) - l_lp)
+            corr.append(value(eta, s_hp) - l_lp)
         else:
             lp_vals.append(l_lp)
     shape = (len(gammas), len(moms), dims[3])
