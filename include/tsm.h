@@ -182,6 +182,18 @@ int tsm_contract(tsm_ctx* ctx, int prec, uint64_t seed, int kind, uint32_t sourc
                  const int* gammas, int n_gamma, const int* moms, int n_q,
                  double* out, int on_device);
 
+/* One-end-trick value (Sec. 2.3, Eq. 2.5) of one canonical solution
+ * s = D_u^-1 eta of the loaded (+mu) operator, for the isovector loop u - d:
+ *   out[g][q][t] = -4 i kappa mu sum_{x: x_4 = t} e^{i q.x}
+ *                  [s_a^dag gamma5 Gamma_g s_a - s_b^dag gamma5 Gamma_g s_b](x)
+ * (s_b may be NULL), from D_u^-1 - D_d^-1 = -4 i kappa mu D_u^-1 D_u^-dag gamma5
+ * for D_tm = 1 - kappa H + 2 i kappa mu gamma5 (the paper states it for
+ * M = D / (2 kappa)).  Its noise average is Tr[P Gamma (D_u^-1 - D_d^-1)].
+ * Layouts, tiers and errors as tsm_contract. */
+int tsm_contract_one_end(tsm_ctx* ctx, int prec, const double* s_a, const double* s_b,
+                         const int* gammas, int n_gamma, const int* moms, int n_q,
+                         double* out, int on_device);
+
 /* TSM parameters (Sec. 2.2, Eq. 2.4).  Sources hp_begin .. hp_end-1 form this
  * call's part of the HP set and lp_begin .. lp_end-1 its part of the LP set;
  * a single process passes hp = [0, N_HP) and lp = [N_HP, N_HP + N_LP). */
@@ -197,6 +209,10 @@ typedef struct {
   const int* moms; int n_q; /* host pointers */
   int verify;               /* 1: recompute every HP solution's true residual in FP64
                                (tsm_loop_stats.hp_max_true_res; 2 extra FP64 hops per HP source) */
+  int estimator;            /* 0: eta^dag Gamma s, loops of D_u^-1 (Sec. 2.3 first estimator);
+                               1: one-end trick, loops of D_u^-1 - D_d^-1 (Eq. 2.5, see
+                               tsm_contract_one_end); the TSM correction is then
+                               f(s_HP) - f(s_LP) of the quadratic per-source value */
 } tsm_params;
 
 /* Run the TSM over this call's source ranges.  Outputs (host or device per

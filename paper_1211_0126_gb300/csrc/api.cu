@@ -192,7 +192,9 @@ int prepare_run(Ctx& c, const tsm_params* p, TsmRun* run, bool branch = false) {
   if (p->batch < 1) return bad(TSM_ERR_ARG, "batch must be >= 1");
   TSM_TRY(check_stop(&p->hp));
   TSM_TRY(check_stop(&p->lp));
+  if (p->estimator != 0 && p->estimator != 1) return bad(TSM_ERR_ARG, "estimator must be 0 or 1");
   TSM_TRY(run->plan.prepare(c, p->gammas, p->n_gamma, p->moms, p->n_q));
+  run->plan.one_end = p->estimator;
   run->E = run->plan.entries(c.lat.L[3]);
   run->n_hp = (int)(p->hp_end - p->hp_begin);
   run->n_lp = (int)(p->lp_end - p->lp_begin);
@@ -577,9 +579,9 @@ int tsm_noise(tsm_ctx* h, uint64_t seed, int kind, uint32_t source, double* out,
   return TSM_OK;
 }
 
-int tsm_contract(tsm_ctx* h, int prec, uint64_t seed, int kind, uint32_t source, const double* s_a,
-                 const double* s_b, const int* gammas, int n_gamma, const int* moms, int n_q, double* out,
-                 int on_device) {
+static int contract_entry(tsm_ctx* h, int one_end, int prec, uint64_t seed, int kind, uint32_t source,
+                          const double* s_a, const double* s_b, const int* gammas, int n_gamma, const int* moms,
+                          int n_q, double* out, int on_device) {
   if (h == nullptr || s_a == nullptr || out == nullptr) return bad(TSM_ERR_ARG, "null argument");
   if (kind != 4 && kind != 2) return bad(TSM_ERR_ARG, "noise kind must be 4 or 2");
   if (prec != TSM_F64 && prec != TSM_F32) return bad(TSM_ERR_ARG, "contraction tier must be TSM_F64 or TSM_F32");
@@ -588,6 +590,7 @@ int tsm_contract(tsm_ctx* h, int prec, uint64_t seed, int kind, uint32_t source,
   TSM_TRY(select_device(c));
   ContractPlan plan;
   TSM_TRY(plan.prepare(c, gammas, n_gamma, moms, n_q));
+  plan.one_end = one_end;
   const size_t bytes = spinor_bytes(c);
   EOField fa, fb;
   TSM_TRY(eo_fields(c, "ct_a", TSM_F64, &fa));
@@ -613,6 +616,17 @@ int tsm_contract(tsm_ctx* h, int prec, uint64_t seed, int kind, uint32_t source,
   TSM_TRY(stage_out_finish(c, out, dout, obytes, on_device));
   TSM_CUDA(cudaStreamSynchronize(c.stream));
   return TSM_OK;
+}
+
+int tsm_contract(tsm_ctx* h, int prec, uint64_t seed, int kind, uint32_t source, const double* s_a,
+                 const double* s_b, const int* gammas, int n_gamma, const int* moms, int n_q, double* out,
+                 int on_device) {
+  return contract_entry(h, 0, prec, seed, kind, source, s_a, s_b, gammas, n_gamma, moms, n_q, out, on_device);
+}
+
+int tsm_contract_one_end(tsm_ctx* h, int prec, const double* s_a, const double* s_b, const int* gammas,
+                         int n_gamma, const int* moms, int n_q, double* out, int on_device) {
+  return contract_entry(h, 1, prec, 0, 4, 0, s_a, s_b, gammas, n_gamma, moms, n_q, out, on_device);
 }
 
 int tsm_loops(tsm_ctx* h, const tsm_params* p, double* loops, double* err, double* lp_mean, double* corr_mean,

@@ -156,8 +156,11 @@ int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint3
     args.phz = plan.phz + (size_t)q0 * c.lat.L[2];
     args.partial = static_cast<double2*>(part);
     args.nbx = nbx;
+    args.fre = 0.0;
+    args.fim = -4.0 * c.lat.kappa * c.lat.mu;
     dim3 grid(nbx, T, 2);
-    contract_kernel<R, SA, SB><<<grid, NT, 0, c.stream>>>(args);
+    if (plan.one_end) contract_kernel<R, SA, SB, true><<<grid, NT, 0, c.stream>>>(args);
+    else contract_kernel<R, SA, SB, false><<<grid, NT, 0, c.stream>>>(args);
     c.launches++;
     TSM_TRY(check_launch(c, "contract_kernel"));
     const int nred = nout * T;

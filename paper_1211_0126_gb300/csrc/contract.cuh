@@ -6,6 +6,12 @@
 // insertion has one non-zero per row, a power of i), and
 // L(g, q, t) = sum_{x: x_4 = t} e^{i q.x} G_g(x).
 // The noise is regenerated from the counter generator, never read from memory.
+//
+// One-end trick (Eq. 2.5, OE = true): S_ab = sum_c conj(s_a,c) s_b,c of the
+// solution itself, the trace taken with gamma5 Gamma (rows 2, 3 negated) and
+// the result multiplied by f = -4 i kappa mu; with a second field b the value
+// is f [s_a^dag g5 Gamma s_a - s_b^dag g5 Gamma s_b], formed without
+// cancellation as conj(d) a + conj(b) d with d = a - b.
 // Phases come from per-axis FP64 tables built on the host (no device sin/cos).
 #pragma once
 
@@ -37,6 +43,7 @@ struct ContractArgs {
   const double2* phz;   // [nq][Lz]
   double2* partial;     // [T][2][nbx][ng*nq]
   int nbx;
+  double fre, fim;      // one-end factor -4 i kappa mu (OE only)
 };
 
 template <class R>
@@ -52,7 +59,7 @@ __device__ __forceinline__ cx<R> times_ipow(cx<R> v, int p) {
 template <class R> struct ContractNT { static constexpr int value = 128; };
 template <> struct ContractNT<double> { static constexpr int value = 64; };
 
-template <class R, class SA, class SB>
+template <class R, class SA, class SB, bool OE>
 __global__ void __launch_bounds__(ContractNT<R>::value) contract_kernel(const ContractArgs<SA, SB> a) {
   constexpr int NT = ContractNT<R>::value;
   __shared__ cx<R> Gs[NT][CT_MAXG + 1];
@@ -65,36 +72,83 @@ __global__ void __launch_bounds__(ContractNT<R>::value) contract_kernel(const Co
     const int ih = t * vs2 + local;
     int c[4];
     site_coords(a.g, parity, ih, c);
-    const uint32_t lex = (uint32_t)(((c[3] * a.g.L[2] + c[2]) * a.g.L[1] + c[1]) * a.g.L[0] + c[0]);
-    cx<R> eta[12], s[12];
-    noise_site<R>(a.noise, lex, a.source, eta);
-    {
+    cx<R> S[4][4];
+    if constexpr (!OE) {
+      const uint32_t lex = (uint32_t)(((c[3] * a.g.L[2] + c[2]) * a.g.L[1] + c[1]) * a.g.L[0] + c[0]);
+      cx<R> eta[12], s[12];
+      noise_site<R>(a.noise, lex, a.source, eta);
+      {
+        cx<typename SA::real> va[12];
+        load_spinor<SA>(a.a[parity], a.sstride, ih, va);
+        if (a.b[0] != nullptr) {
+          cx<typename SB::real> vb[12];
+          load_spinor<SB>(a.b[parity], a.sstride, ih, vb);
+          using W = typename SA::real;  // subtract in the solution's own precision
+#pragma unroll
+          for (int k = 0; k < 12; ++k) {
+            const W re = va[k].re - (W)vb[k].re, im = va[k].im - (W)vb[k].im;
+            s[k] = {(R)re, (R)im};
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 12; ++k) s[k] = {(R)va[k].re, (R)va[k].im};
+        }
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          cx<R> acc = cjmul(eta[3 * x], s[3 * y]);
+          acc = acc + cjmul(eta[3 * x + 1], s[3 * y + 1]);
+          acc = acc + cjmul(eta[3 * x + 2], s[3 * y + 2]);
+          S[x][y] = acc;
+        }
+    } else {
+      cx<R> sa[12];
       cx<typename SA::real> va[12];
       load_spinor<SA>(a.a[parity], a.sstride, ih, va);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) sa[k] = {(R)va[k].re, (R)va[k].im};
       if (a.b[0] != nullptr) {
         cx<typename SB::real> vb[12];
         load_spinor<SB>(a.b[parity], a.sstride, ih, vb);
-        using W = typename SA::real;  // subtract in the solution's own precision
+        using W = typename SA::real;
+        cx<R> d[12], sb[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
           const W re = va[k].re - (W)vb[k].re, im = va[k].im - (W)vb[k].im;
-          s[k] = {(R)re, (R)im};
+          d[k] = {(R)re, (R)im};
+          sb[k] = {(R)vb[k].re, (R)vb[k].im};
         }
+        // a^dag X a - b^dag X b = d^dag X a + b^dag X d
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            cx<R> acc = {0, 0};
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc)
+              acc = acc + cjmul(d[3 * x + cc], sa[3 * y + cc]) + cjmul(sb[3 * x + cc], d[3 * y + cc]);
+            S[x][y] = acc;
+          }
       } else {
 #pragma unroll
-        for (int k = 0; k < 12; ++k) s[k] = {(R)va[k].re, (R)va[k].im};
-      }
-    }
-    cx<R> S[4][4];
+        for (int x = 0; x < 4; ++x)
 #pragma unroll
-    for (int x = 0; x < 4; ++x)
+          for (int y = 0; y < 4; ++y) {
+            cx<R> acc = cjmul(sa[3 * x], sa[3 * y]);
+            acc = acc + cjmul(sa[3 * x + 1], sa[3 * y + 1]);
+            acc = acc + cjmul(sa[3 * x + 2], sa[3 * y + 2]);
+            S[x][y] = acc;
+          }
+      }
+      // gamma5 Gamma: rows 2 and 3 of Gamma change sign in the chiral basis
 #pragma unroll
       for (int y = 0; y < 4; ++y) {
-        cx<R> acc = cjmul(eta[3 * x], s[3 * y]);
-        acc = acc + cjmul(eta[3 * x + 1], s[3 * y + 1]);
-        acc = acc + cjmul(eta[3 * x + 2], s[3 * y + 2]);
-        S[x][y] = acc;
+        S[2][y] = (R)(-1) * S[2][y];
+        S[3][y] = (R)(-1) * S[3][y];
       }
+    }
     for (int k = 0; k < ng; ++k) {
       cx<R> v = {0, 0};
 #pragma unroll
@@ -109,6 +163,7 @@ __global__ void __launch_bounds__(ContractNT<R>::value) contract_kernel(const Co
         }
         v = v + times_ipow(sv, a.gam.ph[k][row]);
       }
+      if constexpr (OE) v = cx<R>{(R)a.fre, (R)a.fim} * v;
       Gs[threadIdx.x][k] = v;
     }
     for (int q = 0; q < nq; ++q) {

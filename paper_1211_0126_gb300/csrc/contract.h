@@ -12,6 +12,7 @@ struct ContractPlan {
   const double2* phx = nullptr;   // device phase tables [n_q][Lx], [n_q][Ly], [n_q][Lz]
   const double2* phy = nullptr;
   const double2* phz = nullptr;
+  int one_end = 0;                // 1: one-end-trick values (Eq. 2.5) with factor -4 i kappa mu
   int prepare(Ctx& c, const int* gammas, int n_gamma, const int* moms, int n_q);
   int entries(int T) const { return ng * n_q * T; }
 };
@@ -19,7 +20,8 @@ struct ContractPlan {
 int make_gamma_tab(const int* gammas, int n, GammaTab* tab);
 NoiseSpec make_noise(uint64_t seed, int kind);
 
-// out[g][q][t] (device, complex) = sum_t-slice e^{iqx} eta^dag Gamma_g (a - b)
+// out[g][q][t] (device, complex) = sum_t-slice e^{iqx} eta^dag Gamma_g (a - b), or
+// with plan.one_end the one-end values f(a) - f(b), f(s) = -4 i kappa mu s^dag g5 Gamma_g s
 template <class R, class SA, class SB>
 int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint32_t source, EOField a,
                     const EOField* b, double2* out);

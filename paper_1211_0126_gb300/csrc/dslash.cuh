@@ -188,8 +188,15 @@ struct HopArgs {
 
 constexpr int HOP_NT = 128;
 
+// Blocks per SM the stencil kernels are compiled for: the 32- and 16-bit tiers
+// are bound by FP32 issue and memory latency together, and six resident blocks
+// (at most 80 registers, a few spilled words) beat five with no spills; the
+// FP64 tier keeps the compiler's choice.
+template <class S> struct HopMinBlocks { static constexpr int value = 6; };
+template <> struct HopMinBlocks<F64> { static constexpr int value = 1; };
+
 template <class S, int DAG, int MODE>
-__global__ void __launch_bounds__(HOP_NT) hop_kernel(const HopArgs<S> a) {
+__global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) hop_kernel(const HopArgs<S> a) {
   using R = typename S::real;
   const int rhs = rhs_slot(a.active);
   if (a.skip != nullptr && (a.skip_rel ? !a.skip[rhs].need_rel : a.skip[rhs].done)) return;
@@ -259,7 +266,7 @@ struct CGUpdArgs {
 };
 
 template <class S, class SA>
-__global__ void __launch_bounds__(HOP_NT) cg_update_kernel(const CGUpdArgs<S, SA> a) {
+__global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) cg_update_kernel(const CGUpdArgs<S, SA> a) {
   using R = typename S::real;
   using RA = typename SA::real;
   const int rhs = rhs_slot(a.active);

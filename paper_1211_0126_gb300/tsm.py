@@ -52,7 +52,8 @@ class TsmParams(ctypes.Structure):
                 ("lp_begin", ctypes.c_uint32), ("lp_end", ctypes.c_uint32),
                 ("hp", TmStop), ("lp", TmStop), ("batch", ctypes.c_int),
                 ("gammas", ctypes.POINTER(ctypes.c_int)), ("n_gamma", ctypes.c_int),
-                ("moms", ctypes.POINTER(ctypes.c_int)), ("n_q", ctypes.c_int), ("verify", ctypes.c_int)]
+                ("moms", ctypes.POINTER(ctypes.c_int)), ("n_q", ctypes.c_int), ("verify", ctypes.c_int),
+                ("estimator", ctypes.c_int)]
 
 
 # exported symbol -> (restype, argtypes)
@@ -67,6 +68,8 @@ _SIGS = {
     "tsm_noise": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, _P, ctypes.c_int]),
     "tsm_contract": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, _P, _P,
                                     _P, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int]),
+    "tsm_contract_one_end": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, ctypes.c_int, _P,
+                                            ctypes.c_int]),
     "tsm_loops": (ctypes.c_int, [_P, ctypes.POINTER(TsmParams), _P, _P, _P, _P, _P, _P, ctypes.c_int,
                                  ctypes.POINTER(TsmLoopStats)]),
     "tsm_combine": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
@@ -252,6 +255,16 @@ def tsm_contract(h, prec, seed, kind, source, s_a, s_b, gammas, moms, out):
                   "tsm_contract")
 
 
+def tsm_contract_one_end(h, prec, s_a, s_b, gammas, moms, out):
+    g, gp = _int_array(gammas, "gammas")
+    m, mp = _int_array(moms, "moms")
+    pa, da = _ptr(s_a)
+    pb, db = _ptr(s_b)
+    po, do = _ptr(out, True)
+    return _check(library().tsm_contract_one_end(h, int(prec), pa, pb, gp, len(g), mp, len(m) // 3, po,
+                                                 _same_side(da, db, do)), "tsm_contract_one_end")
+
+
 def tsm_contract_noalloc(lat, seed, kind, source, s_dev, gammas, moms, out_dev, stream=None):
     """Contraction that allocates nothing (for callers that cannot allocate
     device memory); s_dev and out_dev are torch CUDA tensors (complex128).
@@ -267,7 +280,8 @@ def tsm_contract_noalloc(lat, seed, kind, source, s_dev, gammas, moms, out_dev, 
                                                  ctypes.c_void_p(stream or 0)), "tsm_contract_noalloc")
 
 
-def params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batch=1, verify=False):
+def params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batch=1, verify=False,
+           estimator=0):
     """TsmParams; keeps the integer arrays alive on the returned object."""
     p = TsmParams()
     p.seed = int(seed)
@@ -285,6 +299,7 @@ def params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batc
     p.moms = m.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
     p.n_q = len(m) // 3
     p.verify = 1 if verify else 0
+    p.estimator = int(estimator)
     return p
 
 
@@ -522,10 +537,10 @@ class Context:
         return out
 
     def loops(self, seed, noise, n_hp, n_lp, hp_stop, lp_stop, gammas, moms, hp_range=None, lp_range=None,
-              per_source=False, batch=1, verify=True):
+              per_source=False, batch=1, verify=True, estimator=0):
         hp_range = hp_range or (0, n_hp)
         lp_range = lp_range or (n_hp, n_hp + n_lp)
-        p = params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batch, verify)
+        p = params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batch, verify, estimator)
         shape = (len(gammas), len(moms), self.dims[3])
         out = {k: np.zeros(shape, dtype=np.complex128) for k in ("loops", "lp_mean", "corr_mean")}
         out["err"] = np.zeros(shape, dtype=np.float64)
@@ -537,6 +552,14 @@ class Context:
         out["stats"] = {f: getattr(stats, f) for f, _ in TsmLoopStats._fields_}
         if per_source:
             out["per_corr"], out["per_lp"] = pc, pl
+        return out
+
+    def contract_one_end(self, s_a, gammas, moms, s_b=None, prec=TSM_F64):
+        s_a = np.ascontiguousarray(s_a, dtype=np.complex128)
+        if s_b is not None:
+            s_b = np.ascontiguousarray(s_b, dtype=np.complex128)
+        out = np.zeros((len(gammas), len(moms), self.dims[3]), dtype=np.complex128)
+        tsm_contract_one_end(self.h, prec, s_a, s_b, gammas, moms, out)
         return out
 
     def combine(self, per_corr, per_lp):
