@@ -38,6 +38,17 @@ so the TSM correction is L^1(s_HP) - L^1(s_LP).  The paper writes the same
 identity for M = D / (2 kappa) in physical units (-2 i mu a M_d^-1 gamma5
 M_u^-1); the factor and sign here are those of D_tm itself, fixed by the
 dense-matrix pins in tests.
+
+Generalised one-end trick (Eq. 2.6) for the isoscalar loop u + d: with the
+Wilson operator D_W = 1 - kappa H, D_u + D_d = 2 D_W, hence
+D_u^-1 + D_d^-1 = 2 D_d^-1 D_W D_u^-1 = 2 gamma5 D_u^-dag gamma5 D_W D_u^-1,
+and because D_u D_u^dag = gamma5 D_u^dag D_u gamma5 for twisted mass,
+
+    Tr[P Gamma (D_u^-1 + D_d^-1)] = 2 E[s^dag gamma5 P Gamma gamma5 D_W s].
+
+Per-source value L^2_j = 2 sum_{x: x_4 = t} e^{iq.x} s_j(x)^dag gamma5 Gamma
+gamma5 (D_W s_j)(x): one extra application of the Wilson hop per source; no
+mu suppression, so it is noisier than Eq. 2.5 (as the paper notes).
 """
 import numpy as np
 
@@ -74,6 +85,17 @@ def one_end_loops(s, dims, kappa, mu, gammas, moms):
     dens = np.einsum('tzyxac,gab,tzyxbc->gtzyx', np.conj(s), G5, s)
     ph = phases(dims, moms)
     return -4j * kappa * mu * np.einsum('qtzyx,gtzyx->gqt', ph, dens)
+
+
+def gen_one_end_loops(U, s, dims, kappa, gammas, moms, antiperiodic_t=True):
+    """Generalised one-end-trick value of one source s = D_u^-1 eta (Eq. 2.6)."""
+    G = gamma_list()[list(gammas)]
+    g5 = np.diag([1.0, 1.0, -1.0, -1.0])
+    Y = np.einsum('ab,gbc,cd->gad', g5, G, g5)           # gamma5 Gamma gamma5
+    dw = s - kappa * dirac.hop(U, s, dims, antiperiodic_t)   # D_W s
+    dens = np.einsum('tzyxac,gab,tzyxbc->gtzyx', np.conj(s), Y, dw)
+    ph = phases(dims, moms)
+    return 2.0 * np.einsum('qtzyx,gtzyx->gqt', ph, dens)
 
 
 def exact_loops(Dinv, dims, gammas, moms):
@@ -120,13 +142,17 @@ def tsm_loops(U, dims, kappa, mu, seed, noise_kind, n_hp, n_lp, hp_stop, lp_stop
 
     hp_stop / lp_stop = (rel_tol, max_iter).  Source j uses eta_j from
     oracle.philox.noise(seed, j, ...).  estimator: 'standard' (eta^dag Gamma s,
-    loops of D_u^-1) or 'one_end' (Eq. 2.5, loops of D_u^-1 - D_d^-1).
+    loops of D_u^-1), 'one_end' (Eq. 2.5, loops of D_u^-1 - D_d^-1) or
+    'gen_one_end' (Eq. 2.6, loops of D_u^-1 + D_d^-1).
     Returns a dict with the estimate, its error, the LP-only mean over the LP
     set, the mean correction, the per-source loops and iteration counts.
     """
     if estimator == 'one_end':
         def value(eta, s):
             return one_end_loops(s, dims, kappa, mu, gammas, moms)
+    elif estimator == 'gen_one_end':
+        def value(eta, s):
+            return gen_one_end_loops(U, s, dims, kappa, gammas, moms, antiperiodic_t)
     else:
         def value(eta, s):
             return local_loops(eta, s, dims, gammas, moms)

@@ -83,3 +83,44 @@ def test_tsm_one_end_against_dense():
     sig_lp = np.sqrt((np.abs(lp - lp.mean(0)) ** 2).sum(0) / (len(lp) - 1) / len(lp)) + 1e-14
     zl = np.abs(got['lp_mean'] - exact) / sig_lp
     assert zl.max() > 10.0
+
+
+# ---- generalised one-end trick (Eq. 2.6), isoscalar u + d
+
+def test_isoscalar_identity_dense():
+    dims = (2, 2, 2, 2)
+    U = S.gauge_field(dims, 0.5, 5)
+    Du = dirac.dense_dtm(U, dims, KAPPA, MU)
+    Dd = dirac.dense_dtm(U, dims, KAPPA, -MU)
+    Dw = dirac.dense_dtm(U, dims, KAPPA, 0.0)          # 1 - kappa H, assembled on its own
+    iu, idd = np.linalg.inv(Du), np.linalg.inv(Dd)
+    g5 = _gamma5_full(16)
+    rhs = 2.0 * g5 @ iu.conj().T @ g5 @ Dw @ iu
+    assert np.abs((iu + idd) - rhs).max() < 1e-12 * np.abs(iu).max()
+    # the property the stochastic form rests on
+    assert np.abs(Du @ Du.conj().T - g5 @ Du.conj().T @ Du @ g5).max() < 1e-12
+
+
+def test_gen_complete_basis_reproduces_exact_isoscalar_loop():
+    dims = (2, 2, 2, 2)
+    U = S.gauge_field(dims, 0.5, 6)
+    iu = np.linalg.inv(dirac.dense_dtm(U, dims, KAPPA, MU))
+    idd = np.linalg.inv(dirac.dense_dtm(U, dims, KAPPA, -MU))
+    exact = loops.exact_loops(iu + idd, dims, GAM, MOMS)
+    total = np.zeros_like(exact)
+    for k in range(12 * 16):
+        s = iu[:, k].reshape(dims[3], dims[2], dims[1], dims[0], 4, 3)
+        total += loops.gen_one_end_loops(U, s, dims, KAPPA, GAM, MOMS)
+    assert np.abs(total - exact).max() < 1e-11 * max(np.abs(exact).max(), 1.0)
+
+
+def test_gen_tsm_against_dense():
+    dims = (2, 2, 2, 2)
+    U = S.gauge_field(dims, 0.5, 7)
+    iu = np.linalg.inv(dirac.dense_dtm(U, dims, KAPPA, MU))
+    idd = np.linalg.inv(dirac.dense_dtm(U, dims, KAPPA, -MU))
+    exact = loops.exact_loops(iu + idd, dims, GAM, MOMS)
+    got = loops.tsm_loops(U, dims, KAPPA, MU, 13, 4, 8, 300, (1e-12, 2000), (0.0, 2), GAM, MOMS,
+                          estimator='gen_one_end')
+    z = np.abs(got['loops'] - exact) / (got['err'] + 1e-14)
+    assert np.median(z) < 1.5 and z.max() < 6.0
