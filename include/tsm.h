@@ -194,6 +194,18 @@ int tsm_contract_one_end(tsm_ctx* ctx, int prec, const double* s_a, const double
                          const int* gammas, int n_gamma, const int* moms, int n_q,
                          double* out, int on_device);
 
+/* Generalised one-end-trick value (Sec. 2.3, Eq. 2.6) of one canonical
+ * solution s = D_u^-1 eta, for the isoscalar loop u + d:
+ *   out[g][q][t] = 2 sum_{x: x_4 = t} e^{i q.x}
+ *                  [s_a^dag gamma5 Gamma_g gamma5 (D_W s_a) - (same for s_b)](x)
+ * with the Wilson operator D_W = 1 - kappa H (applied by the library), from
+ * D_u + D_d = 2 D_W and D_u D_u^dag = gamma5 D_u^dag D_u gamma5.  Its noise
+ * average is Tr[P Gamma (D_u^-1 + D_d^-1)].  Layouts, tiers, errors as
+ * tsm_contract. */
+int tsm_contract_gen_one_end(tsm_ctx* ctx, int prec, const double* s_a, const double* s_b,
+                             const int* gammas, int n_gamma, const int* moms, int n_q,
+                             double* out, int on_device);
+
 /* TSM parameters (Sec. 2.2, Eq. 2.4).  Sources hp_begin .. hp_end-1 form this
  * call's part of the HP set and lp_begin .. lp_end-1 its part of the LP set;
  * a single process passes hp = [0, N_HP) and lp = [N_HP, N_HP + N_LP). */
@@ -211,8 +223,12 @@ typedef struct {
                                (tsm_loop_stats.hp_max_true_res; 2 extra FP64 hops per HP source) */
   int estimator;            /* 0: eta^dag Gamma s, loops of D_u^-1 (Sec. 2.3 first estimator);
                                1: one-end trick, loops of D_u^-1 - D_d^-1 (Eq. 2.5, see
-                               tsm_contract_one_end); the TSM correction is then
-                               f(s_HP) - f(s_LP) of the quadratic per-source value */
+                               tsm_contract_one_end);
+                               2: generalised one-end trick, loops of D_u^-1 + D_d^-1
+                               (Eq. 2.6, see tsm_contract_gen_one_end; one Wilson
+                               application per solution; not in tsm_loops_graph).
+                               For 1 and 2 the TSM correction is f(s_HP) - f(s_LP) of
+                               the quadratic per-source value */
 } tsm_params;
 
 /* Run the TSM over this call's source ranges.  Outputs (host or device per

@@ -192,7 +192,9 @@ int prepare_run(Ctx& c, const tsm_params* p, TsmRun* run, bool branch = false) {
   if (p->batch < 1) return bad(TSM_ERR_ARG, "batch must be >= 1");
   TSM_TRY(check_stop(&p->hp));
   TSM_TRY(check_stop(&p->lp));
-  if (p->estimator != 0 && p->estimator != 1) return bad(TSM_ERR_ARG, "estimator must be 0 or 1");
+  if (p->estimator < 0 || p->estimator > 2) return bad(TSM_ERR_ARG, "estimator must be 0, 1 or 2");
+  if (p->estimator == 2 && c.capturing)
+    return bad(TSM_ERR_ARG, "the generalised one-end estimator runs eagerly (tsm_loops), not in a captured graph");
   TSM_TRY(run->plan.prepare(c, p->gammas, p->n_gamma, p->moms, p->n_q));
   run->plan.one_end = p->estimator;
   run->E = run->plan.entries(c.lat.L[3]);
@@ -261,11 +263,25 @@ int record_run(Ctx& c, const tsm_params* p, TsmRun& run, tsm_loop_stats* st) {
   };
   auto contract = [&](uint32_t j, EOField a, int pa, const EOField* b, int pb, double2* out) {
     const ContractPlan& plan = run.plan;
-    if (run.fp64_path) return launch_contract<double, F64, F64>(c, plan, ns, j, a, b, out);
-    if (pa == TSM_F64 && (b == nullptr || pb == TSM_F64)) return launch_contract<float, F64, F64>(c, plan, ns, j, a, b, out);
-    if (pa == TSM_F64) return launch_contract<float, F64, F32>(c, plan, ns, j, a, b, out);
-    if (b == nullptr || pb == TSM_F32) return launch_contract<float, F32, F32>(c, plan, ns, j, a, b, out);
-    return launch_contract<float, F32, F64>(c, plan, ns, j, a, b, out);
+    EOField wa{}, wb{};
+    const EOField *pwa = nullptr, *pwb = nullptr;
+    if (plan.one_end == CT_GEN_ONE_END) {
+      // Eq. 2.6 needs D_W of each solution: one Wilson application per field
+      TSM_TRY(eo_fields(c, "gen_wa", pa, &wa));
+      TSM_TRY(apply_wilson(c, pa, a, wa));
+      pwa = &wa;
+      if (b != nullptr) {
+        TSM_TRY(eo_fields(c, "gen_wb", pb, &wb));
+        TSM_TRY(apply_wilson(c, pb, *b, wb));
+        pwb = &wb;
+      }
+    }
+    if (run.fp64_path) return launch_contract<double, F64, F64>(c, plan, ns, j, a, b, out, pwa, pwb);
+    if (pa == TSM_F64 && (b == nullptr || pb == TSM_F64))
+      return launch_contract<float, F64, F64>(c, plan, ns, j, a, b, out, pwa, pwb);
+    if (pa == TSM_F64) return launch_contract<float, F64, F32>(c, plan, ns, j, a, b, out, pwa, pwb);
+    if (b == nullptr || pb == TSM_F32) return launch_contract<float, F32, F32>(c, plan, ns, j, a, b, out, pwa, pwb);
+    return launch_contract<float, F32, F64>(c, plan, ns, j, a, b, out, pwa, pwb);
   };
   // state slots: fixed in eager mode, one fresh range per solve under capture
   auto slots = [&](int n, std::vector<std::pair<int, int>>& log) {
@@ -607,12 +623,23 @@ static int contract_entry(tsm_ctx* h, int one_end, int prec, uint64_t seed, int 
   double* dout = nullptr;
   TSM_TRY(stage_out_ptr(c, "io_loops", out, obytes, on_device, &dout));
   const NoiseSpec ns = make_noise(seed, kind);
+  EOField wa{}, wb{};
+  if (one_end == CT_GEN_ONE_END) {
+    TSM_TRY(eo_fields(c, "gen_wa", TSM_F64, &wa));
+    TSM_TRY(apply_wilson(c, TSM_F64, fa, wa));
+    if (s_b) {
+      TSM_TRY(eo_fields(c, "gen_wb", TSM_F64, &wb));
+      TSM_TRY(apply_wilson(c, TSM_F64, fb, wb));
+    }
+  }
+  const EOField* pwa = one_end == CT_GEN_ONE_END ? &wa : nullptr;
+  const EOField* pwb = (one_end == CT_GEN_ONE_END && s_b) ? &wb : nullptr;
   if (prec == TSM_F64)
     TSM_TRY((launch_contract<double, F64, F64>(c, plan, ns, source, fa, s_b ? &fb : nullptr,
-                                               reinterpret_cast<double2*>(dout))));
+                                               reinterpret_cast<double2*>(dout), pwa, pwb)));
   else
     TSM_TRY((launch_contract<float, F64, F64>(c, plan, ns, source, fa, s_b ? &fb : nullptr,
-                                              reinterpret_cast<double2*>(dout))));
+                                              reinterpret_cast<double2*>(dout), pwa, pwb)));
   TSM_TRY(stage_out_finish(c, out, dout, obytes, on_device));
   TSM_CUDA(cudaStreamSynchronize(c.stream));
   return TSM_OK;
@@ -626,7 +653,12 @@ int tsm_contract(tsm_ctx* h, int prec, uint64_t seed, int kind, uint32_t source,
 
 int tsm_contract_one_end(tsm_ctx* h, int prec, const double* s_a, const double* s_b, const int* gammas,
                          int n_gamma, const int* moms, int n_q, double* out, int on_device) {
-  return contract_entry(h, 1, prec, 0, 4, 0, s_a, s_b, gammas, n_gamma, moms, n_q, out, on_device);
+  return contract_entry(h, CT_ONE_END, prec, 0, 4, 0, s_a, s_b, gammas, n_gamma, moms, n_q, out, on_device);
+}
+
+int tsm_contract_gen_one_end(tsm_ctx* h, int prec, const double* s_a, const double* s_b, const int* gammas,
+                             int n_gamma, const int* moms, int n_q, double* out, int on_device) {
+  return contract_entry(h, CT_GEN_ONE_END, prec, 0, 4, 0, s_a, s_b, gammas, n_gamma, moms, n_q, out, on_device);
 }
 
 int tsm_loops(tsm_ctx* h, const tsm_params* p, double* loops, double* err, double* lp_mean, double* corr_mean,

@@ -130,7 +130,11 @@ int ContractPlan::prepare(Ctx& c, const int* gammas, int n_gamma, const int* mom
 
 template <class R, class SA, class SB>
 int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint32_t source, EOField a,
-                    const EOField* b, double2* out) {
+                    const EOField* b, double2* out, const EOField* wa, const EOField* wb) {
+  if (plan.one_end == CT_GEN_ONE_END && (wa == nullptr || (b != nullptr && wb == nullptr))) {
+    set_error("generalised one-end contraction needs D_W of its fields");
+    return TSM_ERR_ARG;
+  }
   constexpr int NT = ContractNT<R>::value;
   const int vs2 = c.lat.L[0] * c.lat.L[1] * c.lat.L[2] / 2;
   const int T = c.lat.L[3];
@@ -156,11 +160,17 @@ int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint3
     args.phz = plan.phz + (size_t)q0 * c.lat.L[2];
     args.partial = static_cast<double2*>(part);
     args.nbx = nbx;
-    args.fre = 0.0;
-    args.fim = -4.0 * c.lat.kappa * c.lat.mu;
+    args.wa[0] = wa ? wa->e.as<SA>() : nullptr;
+    args.wa[1] = wa ? wa->o.as<SA>() : nullptr;
+    args.wb[0] = wb ? wb->e.as<SB>() : nullptr;
+    args.wb[1] = wb ? wb->o.as<SB>() : nullptr;
+    args.fre = plan.one_end == CT_GEN_ONE_END ? 2.0 : 0.0;
+    args.fim = plan.one_end == CT_ONE_END ? -4.0 * c.lat.kappa * c.lat.mu : 0.0;
     dim3 grid(nbx, T, 2);
-    if (plan.one_end) contract_kernel<R, SA, SB, true><<<grid, NT, 0, c.stream>>>(args);
-    else contract_kernel<R, SA, SB, false><<<grid, NT, 0, c.stream>>>(args);
+    if (plan.one_end == CT_ONE_END) contract_kernel<R, SA, SB, CT_ONE_END><<<grid, NT, 0, c.stream>>>(args);
+    else if (plan.one_end == CT_GEN_ONE_END)
+      contract_kernel<R, SA, SB, CT_GEN_ONE_END><<<grid, NT, 0, c.stream>>>(args);
+    else contract_kernel<R, SA, SB, CT_STANDARD><<<grid, NT, 0, c.stream>>>(args);
     c.launches++;
     TSM_TRY(check_launch(c, "contract_kernel"));
     const int nred = nout * T;
@@ -173,17 +183,44 @@ int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint3
 }
 
 template int launch_contract<double, F64, F64>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
-                                               const EOField*, double2*);
+                                               const EOField*, double2*, const EOField*, const EOField*);
 template int launch_contract<float, F64, F64>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
-                                              const EOField*, double2*);
+                                              const EOField*, double2*, const EOField*, const EOField*);
 template int launch_contract<float, F32, F32>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
-                                              const EOField*, double2*);
+                                              const EOField*, double2*, const EOField*, const EOField*);
 template int launch_contract<float, F64, F32>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
-                                              const EOField*, double2*);
+                                              const EOField*, double2*, const EOField*, const EOField*);
 template int launch_contract<double, F64, F32>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
-                                               const EOField*, double2*);
+                                               const EOField*, double2*, const EOField*, const EOField*);
 template int launch_contract<float, F32, F64>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
-                                              const EOField*, double2*);
+                                              const EOField*, double2*, const EOField*, const EOField*);
+
+int apply_wilson(Ctx& c, int prec, EOField in, EOField out) {
+  return dispatch_prec(prec, [&](auto tag) -> int {
+    using S = decltype(tag);
+    for (int par = 0; par < 2; ++par) {
+      HopArgs<S> h{};
+      h.g = c.g;
+      h.p_out = par;
+      h.Uout = c.links_of<S>(par);
+      h.Uin = c.links_of<S>(1 - par);
+      h.lstride = c.lstride;
+      h.sstride = c.sstride;
+      h.in = (par ? in.e : in.o).as<S>();
+      h.center = (par ? in.o : in.e).as<S>();
+      h.out = (par ? out.o : out.e).as<S>();
+      h.ac = 1.0;
+      h.ah = -c.lat.kappa;
+      h.tc = twist_one();
+      h.to = twist_one();
+      h.ts = twist_one();
+      h.red = c.red;
+      h.post = POST_NONE;
+      TSM_TRY(launch_hop<S>(c, h, 0, HOP_CENTER, -1));
+    }
+    return (int)TSM_OK;
+  });
+}
 
 int reserve_contract(Ctx& c) {
   constexpr int NT = ContractNT<double>::value;   // the smaller block: the most partials

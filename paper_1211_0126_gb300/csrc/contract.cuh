@@ -12,6 +12,11 @@
 // the result multiplied by f = -4 i kappa mu; with a second field b the value
 // is f [s_a^dag g5 Gamma s_a - s_b^dag g5 Gamma s_b], formed without
 // cancellation as conj(d) a + conj(b) d with d = a - b.
+//
+// Generalised one-end trick (Eq. 2.6, MODE 2): S_ab = sum_c conj(s_a,c)
+// (D_W s)_b,c with D_W s supplied by the caller, the trace taken with
+// gamma5 Gamma gamma5 (rows and columns 2, 3 negated) and the factor 2; with
+// a second field, minus the same for s_b.
 // Phases come from per-axis FP64 tables built on the host (no device sin/cos).
 #pragma once
 
@@ -35,6 +40,8 @@ struct ContractArgs {
   uint32_t source;
   const typename SA::schunk* a[2];   // even, odd
   const typename SB::schunk* b[2];   // may be null
+  const typename SA::schunk* wa[2];  // MODE 2: D_W a
+  const typename SB::schunk* wb[2];  // MODE 2: D_W b (when b is given)
   int sstride;
   GammaTab gam;
   int nq;
@@ -59,8 +66,11 @@ __device__ __forceinline__ cx<R> times_ipow(cx<R> v, int p) {
 template <class R> struct ContractNT { static constexpr int value = 128; };
 template <> struct ContractNT<double> { static constexpr int value = 64; };
 
-template <class R, class SA, class SB, bool OE>
+enum { CT_STANDARD = 0, CT_ONE_END = 1, CT_GEN_ONE_END = 2 };
+
+template <class R, class SA, class SB, int MODE>
 __global__ void __launch_bounds__(ContractNT<R>::value) contract_kernel(const ContractArgs<SA, SB> a) {
+  constexpr bool OE = MODE == CT_ONE_END;
   constexpr int NT = ContractNT<R>::value;
   __shared__ cx<R> Gs[NT][CT_MAXG + 1];
   __shared__ cx<R> Ps[NT][CT_MAXQ + 1];
@@ -73,7 +83,44 @@ __global__ void __launch_bounds__(ContractNT<R>::value) contract_kernel(const Co
     int c[4];
     site_coords(a.g, parity, ih, c);
     cx<R> S[4][4];
-    if constexpr (!OE) {
+    if constexpr (MODE == CT_GEN_ONE_END) {
+      cx<typename SA::real> va[12], wa[12];
+      load_spinor<SA>(a.a[parity], a.sstride, ih, va);
+      load_spinor<SA>(a.wa[parity], a.sstride, ih, wa);
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          cx<R> acc = {0, 0};
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc)
+            acc = acc + cjmul(cx<R>{(R)va[3 * x + cc].re, (R)va[3 * x + cc].im},
+                              cx<R>{(R)wa[3 * y + cc].re, (R)wa[3 * y + cc].im});
+          S[x][y] = acc;
+        }
+      if (a.b[0] != nullptr) {
+        cx<typename SB::real> vb[12], wb[12];
+        load_spinor<SB>(a.b[parity], a.sstride, ih, vb);
+        load_spinor<SB>(a.wb[parity], a.sstride, ih, wb);
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            cx<R> acc = {0, 0};
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc)
+              acc = acc + cjmul(cx<R>{(R)vb[3 * x + cc].re, (R)vb[3 * x + cc].im},
+                                cx<R>{(R)wb[3 * y + cc].re, (R)wb[3 * y + cc].im});
+            S[x][y] = S[x][y] - acc;
+          }
+      }
+      // gamma5 Gamma gamma5: rows and columns 2, 3 change sign
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+          if ((x >= 2) != (y >= 2)) S[x][y] = (R)(-1) * S[x][y];
+    } else if constexpr (!OE) {
       const uint32_t lex = (uint32_t)(((c[3] * a.g.L[2] + c[2]) * a.g.L[1] + c[1]) * a.g.L[0] + c[0]);
       cx<R> eta[12], s[12];
       noise_site<R>(a.noise, lex, a.source, eta);
@@ -163,7 +210,7 @@ __global__ void __launch_bounds__(ContractNT<R>::value) contract_kernel(const Co
         }
         v = v + times_ipow(sv, a.gam.ph[k][row]);
       }
-      if constexpr (OE) v = cx<R>{(R)a.fre, (R)a.fim} * v;
+      if constexpr (MODE != CT_STANDARD) v = cx<R>{(R)a.fre, (R)a.fim} * v;
       Gs[threadIdx.x][k] = v;
     }
     for (int q = 0; q < nq; ++q) {

@@ -12,7 +12,8 @@ struct ContractPlan {
   const double2* phx = nullptr;   // device phase tables [n_q][Lx], [n_q][Ly], [n_q][Lz]
   const double2* phy = nullptr;
   const double2* phz = nullptr;
-  int one_end = 0;                // 1: one-end-trick values (Eq. 2.5) with factor -4 i kappa mu
+  int one_end = 0;                // 1: one-end-trick values (Eq. 2.5) with factor -4 i kappa mu;
+                                  // 2: generalised one-end trick (Eq. 2.6): 2 s^dag g5 Gamma g5 D_W s
   int prepare(Ctx& c, const int* gammas, int n_gamma, const int* moms, int n_q);
   int entries(int T) const { return ng * n_q * T; }
 };
@@ -22,9 +23,13 @@ NoiseSpec make_noise(uint64_t seed, int kind);
 
 // out[g][q][t] (device, complex) = sum_t-slice e^{iqx} eta^dag Gamma_g (a - b), or
 // with plan.one_end the one-end values f(a) - f(b), f(s) = -4 i kappa mu s^dag g5 Gamma_g s
+// (plan.one_end == 2 needs wa = D_W a and, with b, wb = D_W b)
 template <class R, class SA, class SB>
 int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint32_t source, EOField a,
-                    const EOField* b, double2* out);
+                    const EOField* b, double2* out, const EOField* wa = nullptr, const EOField* wb = nullptr);
+
+// out = D_W in = in - kappa H in on both parities (fields of tier prec)
+int apply_wilson(Ctx& c, int prec, EOField in, EOField out);
 
 // allocate the block-partial buffer of the largest contraction launch
 int reserve_contract(Ctx& c);

@@ -70,6 +70,8 @@ _SIGS = {
                                     _P, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int]),
     "tsm_contract_one_end": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, ctypes.c_int, _P,
                                             ctypes.c_int]),
+    "tsm_contract_gen_one_end": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, ctypes.c_int,
+                                                _P, ctypes.c_int]),
     "tsm_loops": (ctypes.c_int, [_P, ctypes.POINTER(TsmParams), _P, _P, _P, _P, _P, _P, ctypes.c_int,
                                  ctypes.POINTER(TsmLoopStats)]),
     "tsm_combine": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
@@ -263,6 +265,16 @@ def tsm_contract_one_end(h, prec, s_a, s_b, gammas, moms, out):
     po, do = _ptr(out, True)
     return _check(library().tsm_contract_one_end(h, int(prec), pa, pb, gp, len(g), mp, len(m) // 3, po,
                                                  _same_side(da, db, do)), "tsm_contract_one_end")
+
+
+def tsm_contract_gen_one_end(h, prec, s_a, s_b, gammas, moms, out):
+    g, gp = _int_array(gammas, "gammas")
+    m, mp = _int_array(moms, "moms")
+    pa, da = _ptr(s_a)
+    pb, db = _ptr(s_b)
+    po, do = _ptr(out, True)
+    return _check(library().tsm_contract_gen_one_end(h, int(prec), pa, pb, gp, len(g), mp, len(m) // 3, po,
+                                                     _same_side(da, db, do)), "tsm_contract_gen_one_end")
 
 
 def tsm_contract_noalloc(lat, seed, kind, source, s_dev, gammas, moms, out_dev, stream=None):
@@ -560,6 +572,14 @@ class Context:
             s_b = np.ascontiguousarray(s_b, dtype=np.complex128)
         out = np.zeros((len(gammas), len(moms), self.dims[3]), dtype=np.complex128)
         tsm_contract_one_end(self.h, prec, s_a, s_b, gammas, moms, out)
+        return out
+
+    def contract_gen_one_end(self, s_a, gammas, moms, s_b=None, prec=TSM_F64):
+        s_a = np.ascontiguousarray(s_a, dtype=np.complex128)
+        if s_b is not None:
+            s_b = np.ascontiguousarray(s_b, dtype=np.complex128)
+        out = np.zeros((len(gammas), len(moms), self.dims[3]), dtype=np.complex128)
+        tsm_contract_gen_one_end(self.h, prec, s_a, s_b, gammas, moms, out)
         return out
 
     def combine(self, per_corr, per_lp):

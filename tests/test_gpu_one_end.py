@@ -72,3 +72,34 @@ def test_one_end_tsm_against_dense_and_mixed(ctx, field):
                       tsm.stop(1e-2, 60, tsm.TSM_F16), GAM, MOMS, batch=8, estimator=1)
     zm = np.abs(mixed["loops"] - ref["loops"]) / np.sqrt(mixed["err"] ** 2 + ref["err"] ** 2 + 1e-300)
     assert np.median(zm) < 1.0 and zm.max() < 5.0
+
+
+# ---- generalised one-end trick (Eq. 2.6): isoscalar u + d
+
+@pytest.mark.parametrize("prec,tol", [(tsm.TSM_F64, 1e-12), (tsm.TSM_F32, 1e-5)])
+def test_contract_gen_one_end_matches_oracle(ctx, field, prec, tol):
+    ctx.load_gauge(field, DIMS, KAPPA, MU)
+    a = S.random_spinor(DIMS, 3)
+    b = a + 0.01 * S.random_spinor(DIMS, 4)
+    want = oloops.gen_one_end_loops(field, a, DIMS, KAPPA, GAM, MOMS)
+    assert _rel(ctx.contract_gen_one_end(a, GAM, MOMS, prec=prec), want) < tol
+    want = want - oloops.gen_one_end_loops(field, b, DIMS, KAPPA, GAM, MOMS)
+    assert _rel(ctx.contract_gen_one_end(a, GAM, MOMS, s_b=b, prec=prec), want) < tol * 100
+
+
+def test_fp64_gen_one_end_tsm_matches_oracle_and_dense(ctx, field):
+    ctx.load_gauge(field, DIMS, KAPPA, MU)
+    hp, lp = (1e-12, 5000), (0.0, 5)
+    got = ctx.loops(43, 4, 4, 12, tsm.stop(*hp, tsm.TSM_F64), tsm.stop(*lp, tsm.TSM_F64), GAM, MOMS,
+                    per_source=True, estimator=2)
+    want = oloops.tsm_loops(field, DIMS, KAPPA, MU, 43, 4, 4, 12, hp, lp, GAM, MOMS, estimator='gen_one_end')
+    assert _rel(got["per_lp"], want["lp"]) < 1e-9
+    assert _rel(got["per_corr"], want["corr"]) < 1e-8
+    assert _rel(got["loops"], want["loops"]) < 1e-9
+    iu = np.linalg.inv(dirac.dense_dtm(field, DIMS, KAPPA, MU))
+    idd = np.linalg.inv(dirac.dense_dtm(field, DIMS, KAPPA, -MU))
+    exact = oloops.exact_loops(iu + idd, DIMS, GAM, MOMS)
+    est = ctx.loops(79, 4, 8, 160, tsm.stop(1e-12, 5000, tsm.TSM_F64), tsm.stop(1e-2, 5000, tsm.TSM_F64),
+                    GAM, MOMS, estimator=2)
+    z = np.abs(est["loops"] - exact) / (est["err"] + 1e-300)
+    assert np.median(z) < 1.5 and z.max() < 6.0
