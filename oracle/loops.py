@@ -49,11 +49,24 @@ and because D_u D_u^dag = gamma5 D_u^dag D_u gamma5 for twisted mass,
 Per-source value L^2_j = 2 sum_{x: x_4 = t} e^{iq.x} s_j(x)^dag gamma5 Gamma
 gamma5 (D_W s_j)(x): one extra application of the Wilson hop per source; no
 mu suppression, so it is noisier than Eq. 2.5 (as the paper notes).
+
+One-derivative insertions (the paper tunes the TSM on i psibar gamma_3 D_3 psi,
+Sec. 3, without defining D; reading: the symmetric covariant derivative
+D<->_mu = (D->_mu - D<-_mu) / 2 with D->_mu psi(x) = [U_mu(x) psi(x+mu) -
+U_mu(x-mu)^dag psi(x-mu)] / 2, the fermion boundary sign on hops across
+t = T-1 <-> 0, the operator and its phase at x):
+
+    O_{Gamma mu}(x) = 1/4 [psibar(x) Gamma U_mu(x) psi(x+mu) - psibar(x) Gamma U_mu(x-mu)^dag psi(x-mu)
+                          - psibar(x+mu) U_mu(x)^dag Gamma psi(x) + psibar(x-mu) U_mu(x-mu) Gamma psi(x)]
+
+whose loop (same trace convention as the local loops) is estimated per source by
+1/4 [eta(x)^dag Gamma (T+ s - T- s)(x) - ((T+ eta - T- eta)(x))^dag Gamma s(x)],
+T+ f(x) = U_mu(x) f(x+mu), T- f(x) = U_mu(x-mu)^dag f(x-mu) (signs included).
 """
 import numpy as np
 
 from .gamma import gamma_list
-from . import dirac, philox, solver
+from . import dirac, philox, ptnet, solver
 
 
 def phases(dims, moms):
@@ -96,6 +109,63 @@ def gen_one_end_loops(U, s, dims, kappa, gammas, moms, antiperiodic_t=True):
     dens = np.einsum('tzyxac,gab,tzyxbc->gtzyx', np.conj(s), Y, dw)
     ph = phases(dims, moms)
     return 2.0 * np.einsum('qtzyx,gtzyx->gqt', ph, dens)
+
+
+def deriv_loops(U, eta, s, dims, gammas, mus, moms, antiperiodic_t=True):
+    """Per-source one-derivative loops: [n_gamma, n_mu, n_q, T] complex."""
+    G = gamma_list()[list(gammas)]
+    ph = phases(dims, moms)
+    out = []
+    for mu in mus:
+        ts = (ptnet.transport(U, s, dims, 2 * mu + 1, antiperiodic_t)
+              - ptnet.transport(U, s, dims, 2 * mu + 2, antiperiodic_t))
+        te = (ptnet.transport(U, eta, dims, 2 * mu + 1, antiperiodic_t)
+              - ptnet.transport(U, eta, dims, 2 * mu + 2, antiperiodic_t))
+        dens = 0.25 * (np.einsum('tzyxac,gab,tzyxbc->gtzyx', np.conj(eta), G, ts)
+                       - np.einsum('tzyxac,gab,tzyxbc->gtzyx', np.conj(te), G, s))
+        out.append(np.einsum('qtzyx,gtzyx->gqt', ph, dens))
+    return np.transpose(np.array(out), (1, 0, 2, 3))
+
+
+def exact_deriv_loops(U, Dinv, dims, gammas, mus, moms, antiperiodic_t=True):
+    """One-derivative loops from a dense inverse, term by term from the operator's
+    definition: sum_{x in t} e^{iqx} Tr[A_{Gamma mu}(x) D^-1] with the four
+    site-pair blocks of A (index 12*site + 3*spin + colour)."""
+    lx, ly, lz, lt = dims
+    vol = lx * ly * lz * lt
+    B = Dinv.reshape(vol, 4, 3, vol, 4, 3)
+    G = gamma_list()[list(gammas)]
+    ph = phases(dims, moms)
+    out = np.zeros((len(gammas), len(mus), len(moms), lt), dtype=np.complex128)
+
+    def site(c):
+        return ((c[3] * lz + c[2]) * ly + c[1]) * lx + c[0]
+
+    for t in range(lt):
+        for z in range(lz):
+            for y in range(ly):
+                for x in range(lx):
+                    c = [x, y, z, t]
+                    i = site(c)
+                    for k, mu in enumerate(mus):
+                        cf, cb = list(c), list(c)
+                        cf[mu] = (c[mu] + 1) % dims[mu]
+                        cb[mu] = (c[mu] - 1) % dims[mu]
+                        sf = -1.0 if (mu == 3 and antiperiodic_t and c[3] == lt - 1) else 1.0
+                        sb = -1.0 if (mu == 3 and antiperiodic_t and c[3] == 0) else 1.0
+                        f, b = site(cf), site(cb)
+                        uf = U[t, z, y, x, mu]                                      # U_mu(x)
+                        ub = U[cb[3], cb[2], cb[1], cb[0], mu]                       # U_mu(x - mu)
+                        for gi in range(len(gammas)):
+                            g = G[gi]
+                            # tr[(Gamma x M) D^-1(z, y)] = sum g_{ss'} M_{ab} D^-1_{(z s' b), (y s a)}
+                            t1 = np.einsum('rs,ab,sbra->', g, uf, B[f, :, :, i, :, :]) * sf
+                            t2 = np.einsum('rs,ab,sbra->', g, ub.conj().T, B[b, :, :, i, :, :]) * sb
+                            t3 = np.einsum('rs,ab,sbra->', g, uf.conj().T, B[i, :, :, f, :, :]) * sf
+                            t4 = np.einsum('rs,ab,sbra->', g, ub, B[i, :, :, b, :, :]) * sb
+                            val = 0.25 * (t1 - t2 - t3 + t4)
+                            out[gi, k, :, t] += ph[:, t, z, y, x] * val
+    return out
 
 
 def exact_loops(Dinv, dims, gammas, moms):
