@@ -206,6 +206,20 @@ int tsm_contract_gen_one_end(tsm_ctx* ctx, int prec, const double* s_a, const do
                              const int* gammas, int n_gamma, const int* moms, int n_q,
                              double* out, int on_device);
 
+/* One-derivative insertions of one canonical solution with its regenerated
+ * noise source (the paper's TSM tuning operator i psibar gamma_3 D_3 psi,
+ * Sec. 3; D is not defined there -- reading: the symmetric covariant
+ * derivative D<->_mu = (D->_mu - D<-_mu) / 2, operator and phase at x):
+ *   out[k][g][q][t] = 1/4 sum_{x: x_4 = t} e^{i q.x} [eta(x)^dag Gamma_g (T+ s - T- s)(x)
+ *                                                   - ((T+ eta - T- eta)(x))^dag Gamma_g s(x)]
+ * for the k-th set bit mu of deriv_mask (1..15), T+ f(x) = U_mu(x) f(x+mu),
+ * T- f(x) = U_mu(x-mu)^dag f(x-mu), the fermion sign on hops across
+ * t = T-1 <-> 0, s = s_a - s_b (s_b may be NULL).  Tiers and errors as
+ * tsm_contract. */
+int tsm_contract_deriv(tsm_ctx* ctx, int prec, uint64_t seed, int kind, uint32_t source,
+                       const double* s_a, const double* s_b, const int* gammas, int n_gamma,
+                       int deriv_mask, const int* moms, int n_q, double* out, int on_device);
+
 /* TSM parameters (Sec. 2.2, Eq. 2.4).  Sources hp_begin .. hp_end-1 form this
  * call's part of the HP set and lp_begin .. lp_end-1 its part of the LP set;
  * a single process passes hp = [0, N_HP) and lp = [N_HP, N_HP + N_LP). */
@@ -229,6 +243,9 @@ typedef struct {
                                application per solution; not in tsm_loops_graph).
                                For 1 and 2 the TSM correction is f(s_HP) - f(s_LP) of
                                the quadratic per-source value */
+  int deriv_mask;           /* estimator 0 only: bit mu (0..3) adds the one-derivative
+                               insertion block along mu (see tsm_contract_deriv) after
+                               the local block in every output and per-source array */
 } tsm_params;
 
 /* Run the TSM over this call's source ranges.  Outputs (host or device per
@@ -239,6 +256,8 @@ typedef struct {
  *   corr_mean [n_gamma][n_q][T] complex   mean HP - LP correction over the HP set
  *   per_corr  [hp_end-hp_begin][n_gamma][n_q][T] complex  per-source L(s_HP - s_LP)
  *   per_lp    [lp_end-lp_begin][n_gamma][n_q][T] complex  per-source L(s_LP)
+ * With deriv_mask set, every [n_gamma][n_q][T] shape above becomes
+ * [1 + popcount(deriv_mask)][n_gamma][n_q][T] (local block first).
  * stats (host, may be NULL) receives iteration counts and residuals.
  * Var is the unbiased complex sample variance sum |X_j - mean|^2 / (N - 1),
  * evaluated in two passes in source order (bit-reproducible). */

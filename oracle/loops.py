@@ -207,13 +207,15 @@ def tsm_combine(corr, lp):
 
 
 def tsm_loops(U, dims, kappa, mu, seed, noise_kind, n_hp, n_lp, hp_stop, lp_stop,
-              gammas, moms, antiperiodic_t=True, estimator='standard'):
+              gammas, moms, antiperiodic_t=True, estimator='standard', deriv_mus=()):
     """The whole TSM estimate, source by source, in the order of Eq. 2.4.
 
     hp_stop / lp_stop = (rel_tol, max_iter).  Source j uses eta_j from
     oracle.philox.noise(seed, j, ...).  estimator: 'standard' (eta^dag Gamma s,
     loops of D_u^-1), 'one_end' (Eq. 2.5, loops of D_u^-1 - D_d^-1) or
     'gen_one_end' (Eq. 2.6, loops of D_u^-1 + D_d^-1).
+    deriv_mus (standard estimator only): directions of one-derivative blocks
+    appended after the local block, per-source layout [1 + n_mu][n_gamma][n_q][T].
     Returns a dict with the estimate, its error, the LP-only mean over the LP
     set, the mean correction, the per-source loops and iteration counts.
     """
@@ -223,6 +225,11 @@ def tsm_loops(U, dims, kappa, mu, seed, noise_kind, n_hp, n_lp, hp_stop, lp_stop
     elif estimator == 'gen_one_end':
         def value(eta, s):
             return gen_one_end_loops(U, s, dims, kappa, gammas, moms, antiperiodic_t)
+    elif deriv_mus:
+        def value(eta, s):
+            loc = local_loops(eta, s, dims, gammas, moms)
+            der = deriv_loops(U, eta, s, dims, gammas, deriv_mus, moms, antiperiodic_t)
+            return np.concatenate([loc[None], np.transpose(der, (1, 0, 2, 3))])
     else:
         def value(eta, s):
             return local_loops(eta, s, dims, gammas, moms)
@@ -241,6 +248,8 @@ def tsm_loops(U, dims, kappa, mu, seed, noise_kind, n_hp, n_lp, hp_stop, lp_stop
         else:
             lp_vals.append(l_lp)
     shape = (len(gammas), len(moms), dims[3])
+    if deriv_mus and estimator == 'standard':
+        shape = (1 + len(deriv_mus),) + shape
     corr = np.array(corr).reshape((n_hp,) + shape)
     lp_vals = np.array(lp_vals).reshape((n_lp,) + shape)
     est, err = tsm_combine(corr, lp_vals)

@@ -195,8 +195,12 @@ int prepare_run(Ctx& c, const tsm_params* p, TsmRun* run, bool branch = false) {
   if (p->estimator < 0 || p->estimator > 2) return bad(TSM_ERR_ARG, "estimator must be 0, 1 or 2");
   if (p->estimator == 2 && c.capturing)
     return bad(TSM_ERR_ARG, "the generalised one-end estimator runs eagerly (tsm_loops), not in a captured graph");
+  if (p->deriv_mask < 0 || p->deriv_mask > 15) return bad(TSM_ERR_ARG, "deriv_mask must be in [0, 15]");
+  if (p->deriv_mask && p->estimator != 0)
+    return bad(TSM_ERR_ARG, "one-derivative insertions use the standard estimator (estimator 0)");
   TSM_TRY(run->plan.prepare(c, p->gammas, p->n_gamma, p->moms, p->n_q));
   run->plan.one_end = p->estimator;
+  run->plan.deriv_mask = p->deriv_mask;
   run->E = run->plan.entries(c.lat.L[3]);
   run->n_hp = (int)(p->hp_end - p->hp_begin);
   run->n_lp = (int)(p->lp_end - p->lp_begin);
@@ -597,7 +601,7 @@ int tsm_noise(tsm_ctx* h, uint64_t seed, int kind, uint32_t source, double* out,
 
 static int contract_entry(tsm_ctx* h, int one_end, int prec, uint64_t seed, int kind, uint32_t source,
                           const double* s_a, const double* s_b, const int* gammas, int n_gamma, const int* moms,
-                          int n_q, double* out, int on_device) {
+                          int n_q, double* out, int on_device, int deriv_mask = 0) {
   if (h == nullptr || s_a == nullptr || out == nullptr) return bad(TSM_ERR_ARG, "null argument");
   if (kind != 4 && kind != 2) return bad(TSM_ERR_ARG, "noise kind must be 4 or 2");
   if (prec != TSM_F64 && prec != TSM_F32) return bad(TSM_ERR_ARG, "contraction tier must be TSM_F64 or TSM_F32");
@@ -607,6 +611,10 @@ static int contract_entry(tsm_ctx* h, int one_end, int prec, uint64_t seed, int 
   ContractPlan plan;
   TSM_TRY(plan.prepare(c, gammas, n_gamma, moms, n_q));
   plan.one_end = one_end;
+  if (deriv_mask) {
+    plan.local = 0;
+    plan.deriv_mask = deriv_mask;
+  }
   const size_t bytes = spinor_bytes(c);
   EOField fa, fb;
   TSM_TRY(eo_fields(c, "ct_a", TSM_F64, &fa));
@@ -659,6 +667,14 @@ int tsm_contract_one_end(tsm_ctx* h, int prec, const double* s_a, const double* 
 int tsm_contract_gen_one_end(tsm_ctx* h, int prec, const double* s_a, const double* s_b, const int* gammas,
                              int n_gamma, const int* moms, int n_q, double* out, int on_device) {
   return contract_entry(h, CT_GEN_ONE_END, prec, 0, 4, 0, s_a, s_b, gammas, n_gamma, moms, n_q, out, on_device);
+}
+
+int tsm_contract_deriv(tsm_ctx* h, int prec, uint64_t seed, int kind, uint32_t source, const double* s_a,
+                       const double* s_b, const int* gammas, int n_gamma, int deriv_mask, const int* moms, int n_q,
+                       double* out, int on_device) {
+  if (deriv_mask < 1 || deriv_mask > 15) return bad(TSM_ERR_ARG, "deriv_mask must have bits among 0..3 set");
+  return contract_entry(h, CT_STANDARD, prec, seed, kind, source, s_a, s_b, gammas, n_gamma, moms, n_q, out,
+                        on_device, deriv_mask);
 }
 
 int tsm_loops(tsm_ctx* h, const tsm_params* p, double* loops, double* err, double* lp_mean, double* corr_mean,

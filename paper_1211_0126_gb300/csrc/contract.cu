@@ -139,45 +139,70 @@ int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint3
   const int vs2 = c.lat.L[0] * c.lat.L[1] * c.lat.L[2] / 2;
   const int T = c.lat.L[3];
   const int nbx = (vs2 + NT - 1) / NT;
-  for (int q0 = 0; q0 < plan.n_q; q0 += CT_MAXQ) {
-    const int nq = std::min(CT_MAXQ, plan.n_q - q0);
-    const int nout = plan.ng * nq;
-    void* part = nullptr;
-    TSM_TRY(c.buffer("contract_partial", (size_t)T * 2 * nbx * CT_MAXG * CT_MAXQ * sizeof(double2), &part));
-    ContractArgs<SA, SB> args{};
-    args.g = c.g;
-    args.noise = ns;
-    args.source = source;
-    args.a[0] = a.e.as<SA>();
-    args.a[1] = a.o.as<SA>();
-    args.b[0] = b ? b->e.as<SB>() : nullptr;
-    args.b[1] = b ? b->o.as<SB>() : nullptr;
-    args.sstride = c.sstride;
-    args.gam = plan.gam;
-    args.nq = nq;
-    args.phx = plan.phx + (size_t)q0 * c.lat.L[0];
-    args.phy = plan.phy + (size_t)q0 * c.lat.L[1];
-    args.phz = plan.phz + (size_t)q0 * c.lat.L[2];
-    args.partial = static_cast<double2*>(part);
-    args.nbx = nbx;
-    args.wa[0] = wa ? wa->e.as<SA>() : nullptr;
-    args.wa[1] = wa ? wa->o.as<SA>() : nullptr;
-    args.wb[0] = wb ? wb->e.as<SB>() : nullptr;
-    args.wb[1] = wb ? wb->o.as<SB>() : nullptr;
-    args.fre = plan.one_end == CT_GEN_ONE_END ? 2.0 : 0.0;
-    args.fim = plan.one_end == CT_ONE_END ? -4.0 * c.lat.kappa * c.lat.mu : 0.0;
-    dim3 grid(nbx, T, 2);
-    if (plan.one_end == CT_ONE_END) contract_kernel<R, SA, SB, CT_ONE_END><<<grid, NT, 0, c.stream>>>(args);
-    else if (plan.one_end == CT_GEN_ONE_END)
-      contract_kernel<R, SA, SB, CT_GEN_ONE_END><<<grid, NT, 0, c.stream>>>(args);
-    else contract_kernel<R, SA, SB, CT_STANDARD><<<grid, NT, 0, c.stream>>>(args);
-    c.launches++;
-    TSM_TRY(check_launch(c, "contract_kernel"));
-    const int nred = nout * T;
-    contract_reduce_kernel<<<(nred + 127) / 128, 128, 0, c.stream>>>(static_cast<double2*>(part), T, nbx, plan.ng,
-                                                                      nq, plan.n_q, q0, out);
-    c.launches++;
-    TSM_TRY(check_launch(c, "contract_reduce_kernel"));
+  const size_t block = (size_t)plan.ng * plan.n_q * T;   // one [n_gamma][n_q][T] output block
+  // one kernel + fixed-order reduction per chunk of at most CT_MAXQ momenta
+  auto passes = [&](double2* dst, auto&& launch) -> int {
+    for (int q0 = 0; q0 < plan.n_q; q0 += CT_MAXQ) {
+      const int nq = std::min(CT_MAXQ, plan.n_q - q0);
+      const int nout = plan.ng * nq;
+      void* part = nullptr;
+      TSM_TRY(c.buffer("contract_partial", (size_t)T * 2 * nbx * CT_MAXG * CT_MAXQ * sizeof(double2), &part));
+      ContractArgs<SA, SB> args{};
+      args.g = c.g;
+      args.noise = ns;
+      args.source = source;
+      args.a[0] = a.e.as<SA>();
+      args.a[1] = a.o.as<SA>();
+      args.b[0] = b ? b->e.as<SB>() : nullptr;
+      args.b[1] = b ? b->o.as<SB>() : nullptr;
+      args.sstride = c.sstride;
+      args.gam = plan.gam;
+      args.nq = nq;
+      args.phx = plan.phx + (size_t)q0 * c.lat.L[0];
+      args.phy = plan.phy + (size_t)q0 * c.lat.L[1];
+      args.phz = plan.phz + (size_t)q0 * c.lat.L[2];
+      args.partial = static_cast<double2*>(part);
+      args.nbx = nbx;
+      args.wa[0] = wa ? wa->e.as<SA>() : nullptr;
+      args.wa[1] = wa ? wa->o.as<SA>() : nullptr;
+      args.wb[0] = wb ? wb->e.as<SB>() : nullptr;
+      args.wb[1] = wb ? wb->o.as<SB>() : nullptr;
+      args.fre = plan.one_end == CT_GEN_ONE_END ? 2.0 : 0.0;
+      args.fim = plan.one_end == CT_ONE_END ? -4.0 * c.lat.kappa * c.lat.mu : 0.0;
+      launch(args, dim3(nbx, T, 2));
+      c.launches++;
+      TSM_TRY(check_launch(c, "contract_kernel"));
+      const int nred = nout * T;
+      contract_reduce_kernel<<<(nred + 127) / 128, 128, 0, c.stream>>>(static_cast<double2*>(part), T, nbx,
+                                                                        plan.ng, nq, plan.n_q, q0, dst);
+      c.launches++;
+      TSM_TRY(check_launch(c, "contract_reduce_kernel"));
+    }
+    return TSM_OK;
+  };
+  double2* dst = out;
+  if (plan.local) {
+    TSM_TRY(passes(dst, [&](const ContractArgs<SA, SB>& args, dim3 grid) {
+      if (plan.one_end == CT_ONE_END) contract_kernel<R, SA, SB, CT_ONE_END><<<grid, NT, 0, c.stream>>>(args);
+      else if (plan.one_end == CT_GEN_ONE_END)
+        contract_kernel<R, SA, SB, CT_GEN_ONE_END><<<grid, NT, 0, c.stream>>>(args);
+      else contract_kernel<R, SA, SB, CT_STANDARD><<<grid, NT, 0, c.stream>>>(args);
+    }));
+    dst += block;
+  }
+  using LS = typename DerivLinks<R>::type;
+  for (int mu = 0; mu < 4; ++mu) {
+    if (!((plan.deriv_mask >> mu) & 1)) continue;
+    TSM_TRY(passes(dst, [&](const ContractArgs<SA, SB>& args, dim3 grid) {
+      DerivArgs<SA, SB, LS> d{};
+      d.base = args;
+      d.U[0] = c.links_of<LS>(0);
+      d.U[1] = c.links_of<LS>(1);
+      d.lstride = c.lstride;
+      d.mu = mu;
+      deriv_contract_kernel<R, SA, SB, LS><<<grid, NT, 0, c.stream>>>(d);
+    }));
+    dst += block;
   }
   return TSM_OK;
 }

@@ -237,14 +237,169 @@ __global__ void __launch_bounds__(ContractNT<R>::value) contract_kernel(const Co
   }
 }
 
+// ---------------------------------------------------------------- one-derivative insertions
+// Symmetric covariant derivative along mu (reading stated with the oracle):
+//   1/4 [eta(x)^dag Gamma (T+ s - T- s)(x) - ((T+ eta - T- eta)(x))^dag Gamma s(x)],
+//   T+ f(x) = U_mu(x) f(x+mu), T- f(x) = U_mu(x-mu)^dag f(x-mu), fermion sign on
+// hops across t = T-1 <-> 0.  s = a - b when b is given (linear in s).  Noise at
+// the neighbours is regenerated like at x.  Links: F64 (three rows) for R =
+// double, FP32 two-row with the third row rebuilt for R = float.
+template <class R> struct DerivLinks { using type = F32; };
+template <> struct DerivLinks<double> { using type = F64; };
+
+template <class SA, class SB, class LS>
+struct DerivArgs {
+  ContractArgs<SA, SB> base;
+  const typename LS::lchunk* U[2];   // links of each parity
+  int lstride;
+  int mu;
+};
+
+template <class R, class SA, class SB>
+__device__ __forceinline__ void deriv_field(const ContractArgs<SA, SB>& a, int parity, int ih, cx<R> s[12]) {
+  cx<typename SA::real> va[12];
+  load_spinor<SA>(a.a[parity], a.sstride, ih, va);
+  if (a.b[0] != nullptr) {
+    cx<typename SB::real> vb[12];
+    load_spinor<SB>(a.b[parity], a.sstride, ih, vb);
+    using W = typename SA::real;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s[k] = {(R)(va[k].re - (W)vb[k].re), (R)(va[k].im - (W)vb[k].im)};
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s[k] = {(R)va[k].re, (R)va[k].im};
+  }
+}
+
+// out[s][a] = sign * (U f)_s,a (DAGU: U^dag f), per spin
+template <bool DAGU, class R>
+__device__ __forceinline__ void colour_mul(const cx<R> u[9], const cx<R> f[12], R sign, cx<R> out[12]) {
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cx<R> acc = {0, 0};
+#pragma unroll
+      for (int b = 0; b < 3; ++b) acc = acc + (DAGU ? cjmul(u[3 * b + a], f[3 * sp + b]) : u[3 * a + b] * f[3 * sp + b]);
+      out[3 * sp + a] = sign * acc;
+    }
+}
+
+template <class R, class SA, class SB, class LS>
+__global__ void __launch_bounds__(ContractNT<R>::value) deriv_contract_kernel(const DerivArgs<SA, SB, LS> d) {
+  constexpr int NT = ContractNT<R>::value;
+  const ContractArgs<SA, SB>& a = d.base;
+  __shared__ cx<R> Gs[NT][CT_MAXG + 1];
+  __shared__ cx<R> Ps[NT][CT_MAXQ + 1];
+  const int t = blockIdx.y, parity = blockIdx.z;
+  const int vs2 = a.g.L[0] * a.g.L[1] * a.g.L[2] / 2;
+  const int local = blockIdx.x * NT + threadIdx.x;
+  const int ng = a.gam.n, nq = a.nq;
+  const int mu = d.mu;
+  if (local < vs2) {
+    const int ih = t * vs2 + local;
+    int c[4];
+    site_coords(a.g, parity, ih, c);
+    const Geom& g = a.g;
+    const uint32_t lex = (uint32_t)(((c[3] * g.L[2] + c[2]) * g.L[1] + c[1]) * g.L[0] + c[0]);
+    int cf[4] = {c[0], c[1], c[2], c[3]}, cb[4] = {c[0], c[1], c[2], c[3]};
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+      if (m == mu) {
+        cf[m] = (c[m] + 1 == g.L[m]) ? 0 : c[m] + 1;
+        cb[m] = (c[m] == 0) ? g.L[m] - 1 : c[m] - 1;
+      }
+    const R sf = (mu == 3 && g.apbc && c[3] == g.L[3] - 1) ? (R)-1 : (R)1;
+    const R sb = (mu == 3 && g.apbc && c[3] == 0) ? (R)-1 : (R)1;
+    const uint32_t lexf = (uint32_t)(((cf[3] * g.L[2] + cf[2]) * g.L[1] + cf[1]) * g.L[0] + cf[0]);
+    const uint32_t lexb = (uint32_t)(((cb[3] * g.L[2] + cb[2]) * g.L[1] + cb[1]) * g.L[0] + cb[0]);
+    const int hf = (int)(lexf >> 1), hb = (int)(lexb >> 1);
+    cx<R> uf[9], ub[9];
+    {
+      cx<typename LS::real> r[9];
+      load_link<LS>(d.U[parity], d.lstride, mu, ih, r);
+      if constexpr (!LS::full_links) third_row(r, r + 6);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) uf[k] = {(R)r[k].re, (R)r[k].im};
+      load_link<LS>(d.U[1 - parity], d.lstride, mu, hb, r);
+      if constexpr (!LS::full_links) third_row(r, r + 6);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) ub[k] = {(R)r[k].re, (R)r[k].im};
+    }
+    cx<R> eta[12], s[12], ds[12], de[12], tmp[12], f[12];
+    noise_site<R>(a.noise, lex, a.source, eta);
+    deriv_field<R>(a, parity, ih, s);
+    // D s = T+ s - T- s
+    deriv_field<R>(a, 1 - parity, hf, f);
+    colour_mul<false>(uf, f, sf, ds);
+    deriv_field<R>(a, 1 - parity, hb, f);
+    colour_mul<true>(ub, f, sb, tmp);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) ds[k] = ds[k] - tmp[k];
+    // D eta = T+ eta - T- eta
+    noise_site<R>(a.noise, lexf, a.source, f);
+    colour_mul<false>(uf, f, sf, de);
+    noise_site<R>(a.noise, lexb, a.source, f);
+    colour_mul<true>(ub, f, sb, tmp);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) de[k] = de[k] - tmp[k];
+    cx<R> S[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        cx<R> acc = {0, 0};
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc)
+          acc = acc + cjmul(eta[3 * x + cc], ds[3 * y + cc]) - cjmul(de[3 * x + cc], s[3 * y + cc]);
+        S[x][y] = (R)0.25 * acc;
+      }
+    for (int k = 0; k < ng; ++k) {
+      cx<R> v = {0, 0};
+#pragma unroll
+      for (int row = 0; row < 4; ++row) {
+        const int col = a.gam.col[k][row];
+        cx<R> sv;
+        switch (col) {
+          case 0: sv = S[row][0]; break;
+          case 1: sv = S[row][1]; break;
+          case 2: sv = S[row][2]; break;
+          default: sv = S[row][3]; break;
+        }
+        v = v + times_ipow(sv, a.gam.ph[k][row]);
+      }
+      Gs[threadIdx.x][k] = v;
+    }
+    for (int q = 0; q < nq; ++q) {
+      const double2 ex = __ldg(a.phx + q * g.L[0] + c[0]);
+      const double2 ey = __ldg(a.phy + q * g.L[1] + c[1]);
+      const double2 ez = __ldg(a.phz + q * g.L[2] + c[2]);
+      cx<R> p = cx<R>{(R)ex.x, (R)ex.y} * cx<R>{(R)ey.x, (R)ey.y};
+      Ps[threadIdx.x][q] = p * cx<R>{(R)ez.x, (R)ez.y};
+    }
+  } else {
+    for (int k = 0; k < ng; ++k) Gs[threadIdx.x][k] = {0, 0};
+    for (int q = 0; q < nq; ++q) Ps[threadIdx.x][q] = {0, 0};
+  }
+  __syncthreads();
+  const int nout = ng * nq;
+  double2* dst = a.partial + ((size_t)(t * 2 + parity) * a.nbx + blockIdx.x) * nout;
+  for (int k = threadIdx.x; k < nout; k += NT) {
+    const int gi = k % ng, q = k / ng;
+    cx<R> acc = {0, 0};
+    for (int s2 = 0; s2 < NT; ++s2) acc = acc + Ps[s2][q] * Gs[s2][gi];
+    dst[k] = make_double2((double)acc.re, (double)acc.im);
+  }
+}
+
 // sum the block partials of one timeslice in fixed order into the output
 // layout [g][q][t] (momenta q0 .. q0+nq-1 of nq_total)
 static __global__ void contract_reduce_kernel(const double2* __restrict__ partial, int T, int nbx, int ng, int nq,
                                        int nq_total, int q0, double2* __restrict__ out) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // k = (q * ng + g) * T + t
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // k = t * (ng * nq) + (q * ng + g): reads coalesce
   const int nout = ng * nq;
   if (k >= nout * T) return;
-  const int t = k % T, gq = k / T;
+  const int t = k / nout, gq = k % nout;
   double re = 0.0, im = 0.0;
   for (int par = 0; par < 2; ++par)
     for (int b = 0; b < nbx; ++b) {

@@ -14,8 +14,17 @@ struct ContractPlan {
   const double2* phz = nullptr;
   int one_end = 0;                // 1: one-end-trick values (Eq. 2.5) with factor -4 i kappa mu;
                                   // 2: generalised one-end trick (Eq. 2.6): 2 s^dag g5 Gamma g5 D_W s
+  int local = 1;                  // the local block (standard or one-end values)
+  int deriv_mask = 0;             // bit mu: one-derivative insertion block along mu (standard estimator)
   int prepare(Ctx& c, const int* gammas, int n_gamma, const int* moms, int n_q);
-  int entries(int T) const { return ng * n_q * T; }
+  int blocks() const {
+    int n = local;
+    for (int m = 0; m < 4; ++m) n += (deriv_mask >> m) & 1;
+    return n;
+  }
+  // outputs per source: blocks() consecutive [n_gamma][n_q][T] blocks (local
+  // first, then one per derivative direction in increasing mu)
+  int entries(int T) const { return ng * n_q * T * blocks(); }
 };
 
 int make_gamma_tab(const int* gammas, int n, GammaTab* tab);
