@@ -111,6 +111,16 @@ def gen_one_end_loops(U, s, dims, kappa, gammas, moms, antiperiodic_t=True):
     return 2.0 * np.einsum('qtzyx,gtzyx->gqt', ph, dens)
 
 
+def fft_loops(eta, s, dims, gammas):
+    """Local loops of one source at every spatial momentum, [n_gamma, T, Lz, Ly, Lx]:
+    index (n_z, n_y, n_x) holds q = 2 pi n / L with the phase e^{+i q.x} (numpy's
+    inverse FFT has that sign and a 1/N factor, undone here)."""
+    lx, ly, lz, lt = dims
+    G = gamma_list()[list(gammas)]
+    dens = np.einsum('tzyxac,gab,tzyxbc->gtzyx', np.conj(eta), G, s)
+    return np.fft.ifftn(dens, axes=(2, 3, 4)) * (lx * ly * lz)
+
+
 def deriv_loops(U, eta, s, dims, gammas, mus, moms, antiperiodic_t=True):
     """Per-source one-derivative loops: [n_gamma, n_mu, n_q, T] complex."""
     G = gamma_list()[list(gammas)]

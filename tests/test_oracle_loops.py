@@ -189,3 +189,19 @@ def test_config0_tsm_against_dense_inverse_4x4x4x4():
     assert np.median(z) < 1.5 and np.max(z) < 6.0
     # HP solves reached the requested residual, LP solves were truncated early
     assert max(out['lp_iters']) < min(out['hp_iters'])
+
+
+def test_fft_loops_equal_direct_phase_sums():
+    """Every momentum at once (FFT) against the direct phase sums of
+    local_loops, including negative momenta (index L - n)."""
+    dims = (4, 2, 6, 4)
+    rng = np.random.default_rng(31)
+    eta = philox.noise(5, 2, dims, 4)
+    s = rng.standard_normal(eta.shape) + 1j * rng.standard_normal(eta.shape)
+    gam = [0, 3, 5, 12]
+    allq = loops.fft_loops(eta, s, dims, gam)
+    moms = [(0, 0, 0), (1, 0, 0), (-1, 1, 2), (3, 1, -5), (2, 0, 3)]
+    direct = loops.local_loops(eta, s, dims, gam, moms)
+    for k, (nx, ny, nz) in enumerate(moms):
+        got = allq[:, :, nz % dims[2], ny % dims[1], nx % dims[0]]
+        assert np.abs(got - direct[:, k, :]).max() < 1e-12 * np.abs(direct).max()
