@@ -206,6 +206,17 @@ int tsm_contract_gen_one_end(tsm_ctx* ctx, int prec, const double* s_a, const do
                              const int* gammas, int n_gamma, const int* moms, int n_q,
                              double* out, int on_device);
 
+/* Local loops of one canonical solution at every spatial momentum (the paper
+ * Fourier-transforms with CUFFT, Sec. 3):
+ *   out[g][t][n_z][n_y][n_x] = sum_{x: x_4 = t} e^{+2 pi i (n_x x/Lx + n_y y/Ly + n_z z/Lz)}
+ *                              eta_j(x)^dag Gamma_g (s_a - s_b)(x),  n_i in [0, L_i)
+ * (momentum -n is index L - n).  Per-site densities in FP64 or FP32 (prec)
+ * and one batched 3-D cuFFT transform of n_gamma * T slices.  Host or device
+ * pointers per on_device; errors as tsm_contract. */
+int tsm_contract_fft(tsm_ctx* ctx, int prec, uint64_t seed, int kind, uint32_t source,
+                     const double* s_a, const double* s_b, const int* gammas, int n_gamma,
+                     double* out, int on_device);
+
 /* One-derivative insertions of one canonical solution with its regenerated
  * noise source (the paper's TSM tuning operator i psibar gamma_3 D_3 psi,
  * Sec. 3; D is not defined there -- reading: the symmetric covariant
@@ -246,6 +257,11 @@ typedef struct {
   int deriv_mask;           /* estimator 0 only: bit mu (0..3) adds the one-derivative
                                insertion block along mu (see tsm_contract_deriv) after
                                the local block in every output and per-source array */
+  int all_momenta;          /* 1 (estimator 0, no derivatives, eager only): every spatial
+                               momentum through one batched 3-D FFT per source (see
+                               tsm_contract_fft); moms / n_q are ignored, outputs are
+                               [n_gamma][T][Lz][Ly][Lx], per_corr / per_lp must be NULL
+                               (means and variances are accumulated in source order) */
 } tsm_params;
 
 /* Run the TSM over this call's source ranges.  Outputs (host or device per

@@ -34,6 +34,13 @@ def nvcc():
     return exe
 
 
+def _rpath():
+    """Run-time search path of the CUDA libraries next to the nvcc in use."""
+    root = os.path.dirname(os.path.dirname(os.path.realpath(nvcc())))
+    dirs = [d for d in (os.path.join(root, "lib64"), os.path.join(root, "lib")) if os.path.isdir(d)]
+    return ["-Xlinker", "-rpath," + ":".join(dirs)] if dirs else []
+
+
 def _sources():
     return sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
 
@@ -74,7 +81,7 @@ def build(verbose=False, force=False, ptxas_verbose=False):
         with cf.ThreadPoolExecutor(workers) as ex:
             list(ex.map(lambda j: _compile(j[0], j[1], extra, verbose or ptxas_verbose), jobs))
     if jobs or not os.path.exists(LIB):
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart"]
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcufft", "-lcudart"] + _rpath()
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), res.stderr))

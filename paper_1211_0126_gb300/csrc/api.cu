@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "contract.h"
+#include "fft.h"
 #include "fields.cuh"
 #include "solver.h"
 
@@ -183,6 +184,9 @@ struct TsmRun {
   EOField b_lp, s_lp, b_hp, s_hp;
   bool branch = false;   // LP set recorded as a second graph branch
   EOField b_lp1, s_lp1;  // its source / solution batches
+  bool fft = false;      // every spatial momentum: running moments instead of per-source values
+  FftProjector fftp;
+  ~TsmRun() { fftp.release(); }
 };
 
 int prepare_run(Ctx& c, const tsm_params* p, TsmRun* run, bool branch = false) {
@@ -198,10 +202,20 @@ int prepare_run(Ctx& c, const tsm_params* p, TsmRun* run, bool branch = false) {
   if (p->deriv_mask < 0 || p->deriv_mask > 15) return bad(TSM_ERR_ARG, "deriv_mask must be in [0, 15]");
   if (p->deriv_mask && p->estimator != 0)
     return bad(TSM_ERR_ARG, "one-derivative insertions use the standard estimator (estimator 0)");
-  TSM_TRY(run->plan.prepare(c, p->gammas, p->n_gamma, p->moms, p->n_q));
-  run->plan.one_end = p->estimator;
-  run->plan.deriv_mask = p->deriv_mask;
-  run->E = run->plan.entries(c.lat.L[3]);
+  if (p->all_momenta) {
+    if (p->estimator != 0 || p->deriv_mask) return bad(TSM_ERR_ARG, "all_momenta uses the local standard estimator");
+    if (c.capturing) return bad(TSM_ERR_ARG, "all_momenta runs eagerly (tsm_loops), not in a captured graph");
+    if (p->gammas == nullptr) return bad(TSM_ERR_ARG, "gammas must be non-null");
+    TSM_TRY(make_gamma_tab(p->gammas, p->n_gamma, &run->plan.gam));
+    run->plan.ng = p->n_gamma;
+    run->fft = true;
+    run->E = p->n_gamma * c.g.V;
+  } else {
+    TSM_TRY(run->plan.prepare(c, p->gammas, p->n_gamma, p->moms, p->n_q));
+    run->plan.one_end = p->estimator;
+    run->plan.deriv_mask = p->deriv_mask;
+    run->E = run->plan.entries(c.lat.L[3]);
+  }
   run->n_hp = (int)(p->hp_end - p->hp_begin);
   run->n_lp = (int)(p->lp_end - p->lp_begin);
   run->sp_lp = solution_prec(p->lp);
@@ -212,10 +226,12 @@ int prepare_run(Ctx& c, const tsm_params* p, TsmRun* run, bool branch = false) {
   c.batch_cap = std::max(c.batch_cap, run->B);
   void* vc = nullptr;
   void* vl = nullptr;
-  TSM_TRY(c.buffer("tsm_per_corr", (size_t)std::max(run->n_hp, 1) * run->E * sizeof(double2), &vc));
-  TSM_TRY(c.buffer("tsm_per_lp", (size_t)std::max(run->n_lp, 1) * run->E * sizeof(double2), &vl));
+  const size_t per = run->fft ? 1 : (size_t)run->E;   // all momenta: no per-source values are kept
+  TSM_TRY(c.buffer("tsm_per_corr", (size_t)std::max(run->n_hp, 1) * per * sizeof(double2), &vc));
+  TSM_TRY(c.buffer("tsm_per_lp", (size_t)std::max(run->n_lp, 1) * per * sizeof(double2), &vl));
   run->d_corr = static_cast<double2*>(vc);
   run->d_lp = static_cast<double2*>(vl);
+  if (run->fft) TSM_TRY(run->fftp.init(c, p->n_gamma, run->fp64_path));
   TSM_TRY(eo_fields(c, "tsm_b_lp", run->sp_lp, &run->b_lp, c.batch_cap));
   TSM_TRY(eo_fields(c, "tsm_s_lp", run->sp_lp, &run->s_lp, c.batch_cap));
   TSM_TRY(eo_fields(c, "tsm_b_hp", run->sp_hp, &run->b_hp, c.batch_cap));
@@ -265,7 +281,7 @@ int record_run(Ctx& c, const tsm_params* p, TsmRun& run, tsm_loop_stats* st) {
       return launch_noise<S>(c, 1, ns, j0, f.o, n);
     });
   };
-  auto contract = [&](uint32_t j, EOField a, int pa, const EOField* b, int pb, double2* out) {
+  auto contract_to = [&](uint32_t j, EOField a, int pa, const EOField* b, int pb, double2* out) {
     const ContractPlan& plan = run.plan;
     EOField wa{}, wb{};
     const EOField *pwa = nullptr, *pwb = nullptr;
@@ -286,6 +302,18 @@ int record_run(Ctx& c, const tsm_params* p, TsmRun& run, tsm_loop_stats* st) {
     if (pa == TSM_F64) return launch_contract<float, F64, F32>(c, plan, ns, j, a, b, out, pwa, pwb);
     if (b == nullptr || pb == TSM_F32) return launch_contract<float, F32, F32>(c, plan, ns, j, a, b, out, pwa, pwb);
     return launch_contract<float, F32, F64>(c, plan, ns, j, a, b, out, pwa, pwb);
+  };
+  // value of source j for set 0 (HP-set corrections) or 1 (LP set), idx-th of its set
+  auto contract = [&](uint32_t j, EOField a, int pa, const EOField* b, int pb, int set, int idx) -> int {
+    if (!run.fft) return contract_to(j, a, pa, b, pb, (set ? run.d_lp : run.d_corr) + (size_t)idx * E);
+    FftProjector& f = run.fftp;
+    const GammaTab& gam = run.plan.gam;
+    if (run.fp64_path) return f.accumulate<double, F64, F64>(c, gam, ns, j, a, b, set, idx + 1);
+    if (pa == TSM_F64 && (b == nullptr || pb == TSM_F64))
+      return f.accumulate<float, F64, F64>(c, gam, ns, j, a, b, set, idx + 1);
+    if (pa == TSM_F64) return f.accumulate<float, F64, F32>(c, gam, ns, j, a, b, set, idx + 1);
+    if (b == nullptr || pb == TSM_F32) return f.accumulate<float, F32, F32>(c, gam, ns, j, a, b, set, idx + 1);
+    return f.accumulate<float, F32, F64>(c, gam, ns, j, a, b, set, idx + 1);
   };
   // state slots: fixed in eager mode, one fresh range per solve under capture
   auto slots = [&](int n, std::vector<std::pair<int, int>>& log) {
@@ -315,8 +343,8 @@ int record_run(Ctx& c, const tsm_params* p, TsmRun& run, tsm_loop_stats* st) {
       rc = gen(sp_lp, j0, run.b_lp1, n);
       if (rc == TSM_OK) rc = solve_batch(c, p->lp, slots(n, c.cap_lp), n, run.b_lp1, run.s_lp1, r_lp.data());
       for (int r = 0; r < n && rc == TSM_OK; ++r)
-        rc = contract(j0 + r, eo_at(run.s_lp1, sp_lp, c.g.Vh, r), sp_lp, nullptr, sp_lp,
-                      run.d_lp + (size_t)(j0 + r - p->lp_begin) * E);
+        rc = contract(j0 + r, eo_at(run.s_lp1, sp_lp, c.g.Vh, r), sp_lp, nullptr, sp_lp, 1,
+                      (int)(j0 + r - p->lp_begin));
     }
     std::swap(r_lp, r_lp1);
     if (rc == TSM_OK && cudaEventRecord(c.join_ev, c.stream) != cudaSuccess) rc = TSM_ERR_CUDA;
@@ -346,8 +374,8 @@ int record_run(Ctx& c, const tsm_params* p, TsmRun& run, tsm_loop_stats* st) {
         if (!r_hp[r].converged) st->hp_not_converged++;
       }
       const EOField sl = eo_at(run.s_lp, sp_lp, c.g.Vh, r);
-      TSM_TRY(contract(j0 + r, eo_at(run.s_hp, sp_hp, c.g.Vh, r), sp_hp, &sl, sp_lp,
-                       run.d_corr + (size_t)(j0 + r - p->hp_begin) * E));
+      TSM_TRY(contract(j0 + r, eo_at(run.s_hp, sp_hp, c.g.Vh, r), sp_hp, &sl, sp_lp, 0,
+                       (int)(j0 + r - p->hp_begin)));
     }
   }
   // LP set: the same LP map, L(s_LP)
@@ -361,8 +389,8 @@ int record_run(Ctx& c, const tsm_params* p, TsmRun& run, tsm_loop_stats* st) {
           if (r_lp[r].status != TSM_OK) return bad(TSM_ERR_NONFINITE, "NaN/Inf in a solve");
           st->lp_iters += r_lp[r].iters;
         }
-        TSM_TRY(contract(j0 + r, eo_at(sl, sp_lp, c.g.Vh, r), sp_lp, nullptr, sp_lp,
-                         run.d_lp + (size_t)(j0 + r - p->lp_begin) * E));
+        TSM_TRY(contract(j0 + r, eo_at(sl, sp_lp, c.g.Vh, r), sp_lp, nullptr, sp_lp, 1,
+                         (int)(j0 + r - p->lp_begin)));
       }
     }
     return TSM_OK;
@@ -669,6 +697,54 @@ int tsm_contract_gen_one_end(tsm_ctx* h, int prec, const double* s_a, const doub
   return contract_entry(h, CT_GEN_ONE_END, prec, 0, 4, 0, s_a, s_b, gammas, n_gamma, moms, n_q, out, on_device);
 }
 
+int tsm_contract_fft(tsm_ctx* h, int prec, uint64_t seed, int kind, uint32_t source, const double* s_a,
+                     const double* s_b, const int* gammas, int n_gamma, double* out, int on_device) {
+  if (h == nullptr || s_a == nullptr || out == nullptr || gammas == nullptr) return bad(TSM_ERR_ARG, "null argument");
+  if (kind != 4 && kind != 2) return bad(TSM_ERR_ARG, "noise kind must be 4 or 2");
+  if (prec != TSM_F64 && prec != TSM_F32) return bad(TSM_ERR_ARG, "contraction tier must be TSM_F64 or TSM_F32");
+  Ctx& c = h->c;
+  if (!c.has_gauge) return bad(TSM_ERR_NO_GAUGE, "no lattice loaded");
+  TSM_TRY(select_device(c));
+  GammaTab gam{};
+  TSM_TRY(make_gamma_tab(gammas, n_gamma, &gam));
+  const size_t bytes = spinor_bytes(c);
+  EOField fa, fb;
+  TSM_TRY(eo_fields(c, "ct_a", TSM_F64, &fa));
+  TSM_TRY(eo_fields(c, "ct_b", TSM_F64, &fb));
+  const double* da = nullptr;
+  TSM_TRY(stage_in(c, "io_in", s_a, bytes, on_device, &da));
+  TSM_TRY(pack_eo(c, TSM_F64, da, fa));
+  if (s_b) {
+    const double* db = nullptr;
+    TSM_TRY(stage_in(c, "io_in2", s_b, bytes, on_device, &db));
+    TSM_TRY(pack_eo(c, TSM_F64, db, fb));
+  }
+  FftProjector f;
+  int rc = f.init(c, n_gamma, prec == TSM_F64);
+  const NoiseSpec ns = make_noise(seed, kind);
+  if (rc == TSM_OK) {
+    rc = prec == TSM_F64 ? f.transform<double, F64, F64>(c, gam, ns, source, fa, s_b ? &fb : nullptr)
+                         : f.transform<float, F64, F64>(c, gam, ns, source, fa, s_b ? &fb : nullptr);
+  }
+  if (rc == TSM_OK) {
+    // widen to complex double in the caller's layout [n_gamma][T][Lz][Ly][Lx]
+    const size_t ob = (size_t)f.E * sizeof(double2);
+    double* dout = nullptr;
+    rc = stage_out_ptr(c, "io_fft", out, ob, on_device, &dout);
+    if (rc == TSM_OK) {
+      if (prec == TSM_F64) {
+        if (cudaMemcpyAsync(dout, f.dens, ob, cudaMemcpyDeviceToDevice, c.stream) != cudaSuccess) rc = TSM_ERR_CUDA;
+      } else {
+        rc = launch_widen(c, static_cast<const float2*>(f.dens), reinterpret_cast<double2*>(dout), f.E);
+      }
+    }
+    if (rc == TSM_OK) rc = stage_out_finish(c, out, dout, ob, on_device);
+    if (rc == TSM_OK && cudaStreamSynchronize(c.stream) != cudaSuccess) rc = TSM_ERR_CUDA;
+  }
+  f.release();
+  return rc;
+}
+
 int tsm_contract_deriv(tsm_ctx* h, int prec, uint64_t seed, int kind, uint32_t source, const double* s_a,
                        const double* s_b, const int* gammas, int n_gamma, int deriv_mask, const int* moms, int n_q,
                        double* out, int on_device) {
@@ -682,6 +758,8 @@ int tsm_loops(tsm_ctx* h, const tsm_params* p, double* loops, double* err, doubl
   if (h == nullptr || p == nullptr) return bad(TSM_ERR_ARG, "null argument");
   Ctx& c = h->c;
   TSM_TRY(select_device(c));
+  if (p->all_momenta && (per_corr || per_lp))
+    return bad(TSM_ERR_ARG, "all_momenta keeps no per-source values (per_corr / per_lp must be NULL)");
   TsmRun run;
   TSM_TRY(prepare_run(c, p, &run));
   tsm_loop_stats st{};
@@ -694,8 +772,12 @@ int tsm_loops(tsm_ctx* h, const tsm_params* p, double* loops, double* err, doubl
   if (err) TSM_TRY(stage_out_ptr(c, "out_err", err, rb, on_device, &d_err));
   if (lp_mean) TSM_TRY(stage_out_ptr(c, "out_lpm", lp_mean, cb, on_device, &d_lpm));
   if (corr_mean) TSM_TRY(stage_out_ptr(c, "out_cm", corr_mean, cb, on_device, &d_cm));
-  TSM_TRY(launch_combine(c, run.d_corr, n_hp, run.d_lp, n_lp, E, reinterpret_cast<double2*>(d_est), d_err,
-                         reinterpret_cast<double2*>(d_lpm), reinterpret_cast<double2*>(d_cm)));
+  if (run.fft)
+    TSM_TRY(run.fftp.finalize(c, n_hp, n_lp, reinterpret_cast<double2*>(d_est), d_err,
+                              reinterpret_cast<double2*>(d_lpm), reinterpret_cast<double2*>(d_cm)));
+  else
+    TSM_TRY(launch_combine(c, run.d_corr, n_hp, run.d_lp, n_lp, E, reinterpret_cast<double2*>(d_est), d_err,
+                           reinterpret_cast<double2*>(d_lpm), reinterpret_cast<double2*>(d_cm)));
   if (loops) TSM_TRY(stage_out_finish(c, loops, d_est, cb, on_device));
   if (err) TSM_TRY(stage_out_finish(c, err, d_err, rb, on_device));
   if (lp_mean) TSM_TRY(stage_out_finish(c, lp_mean, d_lpm, cb, on_device));

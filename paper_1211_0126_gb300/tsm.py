@@ -53,7 +53,7 @@ class TsmParams(ctypes.Structure):
                 ("hp", TmStop), ("lp", TmStop), ("batch", ctypes.c_int),
                 ("gammas", ctypes.POINTER(ctypes.c_int)), ("n_gamma", ctypes.c_int),
                 ("moms", ctypes.POINTER(ctypes.c_int)), ("n_q", ctypes.c_int), ("verify", ctypes.c_int),
-                ("estimator", ctypes.c_int), ("deriv_mask", ctypes.c_int)]
+                ("estimator", ctypes.c_int), ("deriv_mask", ctypes.c_int), ("all_momenta", ctypes.c_int)]
 
 
 # exported symbol -> (restype, argtypes)
@@ -72,6 +72,8 @@ _SIGS = {
                                             ctypes.c_int]),
     "tsm_contract_gen_one_end": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, ctypes.c_int,
                                                 _P, ctypes.c_int]),
+    "tsm_contract_fft": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, _P, _P, _P,
+                                        ctypes.c_int, _P, ctypes.c_int]),
     "tsm_contract_deriv": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, _P, _P,
                                           _P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int]),
     "tsm_loops": (ctypes.c_int, [_P, ctypes.POINTER(TsmParams), _P, _P, _P, _P, _P, _P, ctypes.c_int,
@@ -279,6 +281,15 @@ def tsm_contract_gen_one_end(h, prec, s_a, s_b, gammas, moms, out):
                                                      _same_side(da, db, do)), "tsm_contract_gen_one_end")
 
 
+def tsm_contract_fft(h, prec, seed, kind, source, s_a, s_b, gammas, out):
+    g, gp = _int_array(gammas, "gammas")
+    pa, da = _ptr(s_a)
+    pb, db = _ptr(s_b)
+    po, do = _ptr(out, True)
+    return _check(library().tsm_contract_fft(h, int(prec), ctypes.c_uint64(seed), int(kind), ctypes.c_uint32(source),
+                                             pa, pb, gp, len(g), po, _same_side(da, db, do)), "tsm_contract_fft")
+
+
 def tsm_contract_deriv(h, prec, seed, kind, source, s_a, s_b, gammas, deriv_mask, moms, out):
     g, gp = _int_array(gammas, "gammas")
     m, mp = _int_array(moms, "moms")
@@ -306,7 +317,7 @@ def tsm_contract_noalloc(lat, seed, kind, source, s_dev, gammas, moms, out_dev, 
 
 
 def params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batch=1, verify=False,
-           estimator=0, deriv_mask=0):
+           estimator=0, deriv_mask=0, all_momenta=False):
     """TsmParams; keeps the integer arrays alive on the returned object."""
     p = TsmParams()
     p.seed = int(seed)
@@ -326,6 +337,7 @@ def params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batc
     p.verify = 1 if verify else 0
     p.estimator = int(estimator)
     p.deriv_mask = int(deriv_mask)
+    p.all_momenta = 1 if all_momenta else 0
     return p
 
 
@@ -563,14 +575,19 @@ class Context:
         return out
 
     def loops(self, seed, noise, n_hp, n_lp, hp_stop, lp_stop, gammas, moms, hp_range=None, lp_range=None,
-              per_source=False, batch=1, verify=True, estimator=0, deriv_mask=0):
+              per_source=False, batch=1, verify=True, estimator=0, deriv_mask=0, all_momenta=False):
         hp_range = hp_range or (0, n_hp)
         lp_range = lp_range or (n_hp, n_hp + n_lp)
+        if all_momenta:
+            moms = [(0, 0, 0)]
         p = params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batch, verify, estimator,
-                   deriv_mask)
+                   deriv_mask, all_momenta)
         shape = (len(gammas), len(moms), self.dims[3])
         if deriv_mask:
             shape = (1 + bin(int(deriv_mask)).count("1"),) + shape
+        if all_momenta:
+            lx, ly, lz, lt = self.dims
+            shape = (len(gammas), lt, lz, ly, lx)
         out = {k: np.zeros(shape, dtype=np.complex128) for k in ("loops", "lp_mean", "corr_mean")}
         out["err"] = np.zeros(shape, dtype=np.float64)
         pc = pl = None
@@ -597,6 +614,16 @@ class Context:
             s_b = np.ascontiguousarray(s_b, dtype=np.complex128)
         out = np.zeros((len(gammas), len(moms), self.dims[3]), dtype=np.complex128)
         tsm_contract_gen_one_end(self.h, prec, s_a, s_b, gammas, moms, out)
+        return out
+
+    def contract_fft(self, seed, source, s_a, gammas, s_b=None, kind=4, prec=TSM_F64):
+        """[n_gamma][T][Lz][Ly][Lx] local loops of one source at every spatial momentum."""
+        s_a = np.ascontiguousarray(s_a, dtype=np.complex128)
+        if s_b is not None:
+            s_b = np.ascontiguousarray(s_b, dtype=np.complex128)
+        lx, ly, lz, lt = self.dims
+        out = np.zeros((len(gammas), lt, lz, ly, lx), dtype=np.complex128)
+        tsm_contract_fft(self.h, prec, seed, kind, source, s_a, s_b, gammas, out)
         return out
 
     def contract_deriv(self, seed, source, s_a, gammas, deriv_mask, moms, s_b=None, kind=4, prec=TSM_F64):
