@@ -1,8 +1,9 @@
 """CG on the normal equations of the even/odd Schur complement (oracle; test infrastructure).
 
-The paper truncates the low-precision (LP) inversions "at a large residual or
-equivalently a fixed number of iterations" (Sec. 2.2) and runs a few
-high-precision (HP) ones, but never names the solver.  Reading used here:
+The paper truncates the low-precision (LP) inversions either at a loose
+residual or after a fixed number of iterations, treating the two as the same
+rule (Sec. 2.2), and runs a few high-precision (HP) ones, but never names the
+solver.  Reading used here:
 conjugate gradient on  Dhat^dagger Dhat x = Dhat^dagger bhat  (CGNR), zero
 initial guess, stopped when the iterated normal residual satisfies
 ||r_k|| / ||Dhat^dagger bhat|| < rel_tol (not squared), or after max_iter
