@@ -57,10 +57,12 @@ def parse():
     ap.add_argument("--mode", default="eager", choices=["eager", "graph"],
                     help="eager: host-driven chunked CG loops; graph: one captured CUDA graph per step "
                          "(device-side loops, LP set beside the HP set)")
-    ap.add_argument("--workload", default="tsm24", choices=["tsm24", "three-lattice", "learned"],
+    ap.add_argument("--workload", default="tsm24", choices=["tsm24", "three-lattice", "learned", "scale"],
                     help="tsm24: the headline 24^3x48 TSM step; three-lattice: 8^3x16 + 12^3x24 + 16^3x32 "
                          "in one captured graph (batching workload, its own JSON line); learned: the learned "
-                         "LP preconditioner at 16^3x32 (training + held-out evaluation, its own JSON line)")
+                         "LP preconditioner at 16^3x32 (training + held-out evaluation, its own JSON line); "
+                         "scale: the full TSM at 32^3x64 with local and one-derivative insertions (its own "
+                         "JSON line)")
     ap.add_argument("--train-steps", type=int, default=400, help="learned workload: Adam steps")
     ap.add_argument("--pairs-per-field", type=int, default=500, help="learned workload: pairs per training field")
     ap.add_argument("--net-only", action="store_true",
@@ -718,6 +720,54 @@ def run_learned(args):
         c.close()
 
 
+def run_scale(args):
+    """TSM at scale: 32^3x64, links eps = 0.2 after 2 APE steps (alpha = 0.5,
+    seed 301), kappa = 0.1248, mu = 0.003; N_HP = 32 FP32 + FP64-reliable solves
+    at 1e-10, N_LP = 2048 BF16 solves at 1e-2, blocks of 16 sources; 16 local
+    insertions plus the one-derivative insertions along all four directions at
+    13 momenta.  One timed step after a smaller warm-up (oracle spot checks of
+    sources at this size are GPU tests, not part of the bench)."""
+    import torch
+    from paper_1211_0126_gb300 import build, tsm
+    from paper_1211_0126_gb300 import synthetic as S
+    if not os.path.exists(tsm.LIB_PATH):
+        build.build()
+    dims = (32, 32, 32, 64)
+    kappa, mu = 0.1248, 0.003
+    n_hp, n_lp = 32, 2048
+    gam, moms = list(range(16)), S.default_momenta(13)
+    U = S.gauge_field(dims, 0.2, 301, ape_steps=2, ape_alpha=0.5)
+    stream = torch.cuda.current_stream()
+    ctx = tsm.Context(0, stream.cuda_stream)
+    ctx.load_gauge(U, dims, kappa, mu)
+    hp = tsm.stop(1e-10, HP_MAXIT, tsm.TSM_F32, reliable=True, reliable_delta=RELIABLE_DELTA)
+    lp = tsm.stop(1e-2, 500, tsm.TSM_BF16)
+    ctx.loops(5, 4, 2, 16, hp, lp, gam, moms, batch=16, deriv_mask=0b1111)     # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0.record(stream)
+    out = ctx.loops(6, 4, n_hp, n_lp, hp, lp, gam, moms, batch=16, deriv_mask=0b1111)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st = out["stats"]
+    line = {"metric": "TSM sources/s at 32^3x64 with local and one-derivative insertions",
+            "value": (n_hp + n_lp) / (ms * 1e-3), "unit": "sources/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": ms, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "scale-32^3x64-eps0.2-ape2-k0.1248-mu0.003 hp32(f32+f64rel,1e-10) "
+                                   "lp2048(bf16,1e-2) batch16 16G+4 derivative directions x 13q",
+                       "lp_iters_per_source": st["lp_iters"] / float(n_hp + n_lp),
+                       "hp_iters_per_source": st["hp_iters"] / float(n_hp),
+                       "hp_not_converged": st["hp_not_converged"], "hp_max_true_res": st["hp_max_true_res"],
+                       "verify": "every HP solution's true residual recomputed in FP64"},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.warmup < 3:
@@ -732,6 +782,8 @@ def main():
         run_three_lattice(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "scale":
+        run_scale(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -187,8 +187,13 @@ static __global__ void __launch_bounds__(SITE_NT) accumulate_solution_kernel(int
 
 // reliable update, last step: iterated residual r (F32) = true residual r64
 // (F64), only for right-hand sides with a pending update
+// residual replacement of a reliable update: r = p = the true FP64 residual
+// (the search direction restarts from it: after many FP32 iterations the
+// iterated residual can lie orders of magnitude below the true one, and the
+// old direction would then no longer be conjugate to the replaced residual)
 static __global__ void __launch_bounds__(SITE_NT) replace_residual_kernel(int Vh, const double2* __restrict__ r64,
-                                                                          float4* __restrict__ r, int sstride,
+                                                                          float4* __restrict__ r,
+                                                                          float4* __restrict__ p, int sstride,
                                                                           const int* active, const CGState* st) {
   const int rhs = rhs_slot(active);
   if (!st[rhs].need_rel) return;
@@ -200,6 +205,7 @@ static __global__ void __launch_bounds__(SITE_NT) replace_residual_kernel(int Vh
 #pragma unroll
   for (int k = 0; k < 12; ++k) w[k] = {(float)v[k].re, (float)v[k].im};
   store_spinor<F32>(r + rhs_offset<F32>(rhs, sstride), sstride, ih, w);
+  store_spinor<F32>(p + rhs_offset<F32>(rhs, sstride), sstride, ih, w);
 }
 
 // closes the reliable updates of one iteration: clears need_rel and, where the

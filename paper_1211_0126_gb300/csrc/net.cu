@@ -7,6 +7,8 @@
 #include <new>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "contract.h"
 #include "net.h"
 #include "ptnet.cuh"
@@ -26,6 +28,52 @@ int umma_launch(cudaStream_t stream, dim3 grid, const __nv_bfloat16* A, const __
   umma_gemm_kernel<BN><<<grid, UMMA_THREADS, smem, stream>>>(A, B, C, M, N, K, ldc, beta, error, lda, ldb, kchunk,
                                                              czs);
   return cudaGetLastError() == cudaSuccess ? TSM_OK : TSM_ERR_CUDA;
+}
+
+// cuTensorMapEncodeTiled from the driver (no link-time dependency on libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// tensor map of a row-major BF16 matrix [rows][cols] with leading dimension
+// ld, read in boxes of 8 columns x box_rows rows, zero fill outside
+bool make_tensor_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+  if (fn == nullptr || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)UMMA_TMA_BOX_K, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool g_umma_tma = true;   // TMA-fed kernel when the operands allow it
+
+template <int BN>
+int umma_launch_any(cudaStream_t stream, dim3 grid, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int M,
+                    int N, int K, int ldc, int beta, int* error, int lda, int ldb, int kchunk, long long czs) {
+  CUtensorMap ta, tb;
+  if (g_umma_tma && make_tensor_map(&ta, A, M, K, lda, UMMA_BM) && make_tensor_map(&tb, B, N, K, ldb, BN)) {
+    const int smem = umma_tma_smem_bytes<BN>();
+    if (cudaFuncSetAttribute(umma_tma_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+      return TSM_ERR_CUDA;
+    umma_tma_gemm_kernel<BN><<<grid, UMMA_THREADS, smem, stream>>>(ta, tb, C, M, N, K, ldc, beta, error, kchunk, czs);
+    return cudaGetLastError() == cudaSuccess ? TSM_OK : TSM_ERR_CUDA;
+  }
+  return umma_launch<BN>(stream, grid, A, B, C, M, N, K, ldc, beta, error, lda, ldb, kchunk, czs);
 }
 
 }  // namespace
@@ -54,7 +102,7 @@ int launch_umma_gemm_ex(cudaStream_t stream, const __nv_bfloat16* A, int lda, co
   const int w = (N + gn - 1) / gn;
   const dim3 grid(gm, gn, splits);
 #define TSM_UMMA_CASE(BN) \
-  if (w <= BN) return umma_launch<BN>(stream, grid, A, B, C, M, N, K, ldc, beta, error, lda, ldb, kchunk, czs);
+  if (w <= BN) return umma_launch_any<BN>(stream, grid, A, B, C, M, N, K, ldc, beta, error, lda, ldb, kchunk, czs);
   TSM_UMMA_CASE(16)
   TSM_UMMA_CASE(32)
   TSM_UMMA_CASE(48)

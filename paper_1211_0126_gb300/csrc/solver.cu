@@ -290,8 +290,9 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
       // reliable update (Sleijpen & van der Vorst; Clark et al. for lattice QCD):
       // for every right-hand side whose residual fell by delta since the last
       // update, or that met its stopping rule, fold the FP32 increment into the
-      // FP64 solution and replace the iterated residual by the true FP64 normal
-      // residual; the others return at once from these kernels
+      // FP64 solution, replace the iterated residual by the true FP64 normal
+      // residual and restart the search direction from it; the others return
+      // at once from these kernels
       const int blocks = (c.g.Vh + SITE_NT - 1) / SITE_NT;
       accumulate_solution_kernel<<<dim3(n, blocks), SITE_NT, 0, c.stream>>>(c.g.Vh, x.as<F32>(), x64.as<F64>(),
                                                                            c.sstride, dact, st);
@@ -299,7 +300,7 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
       TSM_TRY(check_launch(c, "accumulate_solution_kernel"));
       TSM_TRY(normal_residual_f64(c, x64, r0, r64, st, dact, n));
       replace_residual_kernel<<<dim3(n, blocks), SITE_NT, 0, c.stream>>>(c.g.Vh, r64.as<F64>(), r.as<F32>(),
-                                                                        c.sstride, dact, st);
+                                                                        p.as<F32>(), c.sstride, dact, st);
       c.launches++;
       TSM_TRY(check_launch(c, "replace_residual_kernel"));
       rel_finish_kernel<<<1, Ctx::kMaxBatch, 0, c.stream>>>(st, dact, n);

@@ -16,6 +16,7 @@
 // (bounded) for its copies and MMAs in flight, frees its TMEM and returns.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -236,6 +237,186 @@ __global__ void __launch_bounds__(UMMA_THREADS) umma_gemm_kernel(const __nv_bflo
     // give MMAs still in flight a second bounded wait before TMEM is released
     if (last >= 0) mbar_wait(&bar[last % UMMA_STAGES], (uint32_t)((last / UMMA_STAGES) & 1));
     if (threadIdx.x == 0 && error != nullptr) atomicExch(error, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+}  // namespace tsm
+
+// ---------------------------------------------------------------- TMA-fed variant
+// The same product with the operand tiles brought in by the tensor memory
+// accelerator: thread 0 issues, per stage, 8 boxes of 8 columns x 128 rows of
+// A and 8 boxes of 8 columns x BN rows of B (cp.async.bulk.tensor, zero fill
+// outside the matrices) onto an mbarrier with an expected byte count; each
+// box lands as a column of core matrices (8 rows x 16 B, 8-row groups 128 B
+// apart), so K-adjacent core matrices are one box apart (LBO = rows x 16 B,
+// SBO = 128 B).  Thread 32 waits for a stage, issues its four MMAs and lets
+// tcgen05.commit release the stage to the producer; a last commit signals the
+// accumulator to the epilogue.  No thread-wide barrier inside the K loop.
+// Every wait is bounded; on timeout the CTA records the error, waits (bounded)
+// for the copies it issued and for its MMAs, frees TMEM and returns.
+namespace tsm {
+
+constexpr int UMMA_TMA_BOX_K = 8;   // columns per TMA box (16 bytes of BF16)
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int BN> __host__ __device__ constexpr int umma_tma_stages() { return BN >= 64 ? 3 : 4; }
+template <int BN> __host__ __device__ constexpr int umma_tma_smem_bytes() {
+  return umma_tma_stages<BN>() * umma_stage_bytes<BN>() + 1024;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(UMMA_THREADS) umma_tma_gemm_kernel(const __grid_constant__ CUtensorMap ta,
+                                                                     const __grid_constant__ CUtensorMap tb,
+                                                                     float* __restrict__ C, int M, int N, int K,
+                                                                     int ldc, int beta, int* __restrict__ error,
+                                                                     int kchunk, long long czstride) {
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "BN must be a multiple of 16 in [16, 256]");
+  constexpr int TMEM_COLS = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+  constexpr int ST = umma_tma_stages<BN>();
+  constexpr int SB = umma_stage_bytes<BN>();
+  constexpr uint32_t STAGE_TX = (uint32_t)(UMMA_BM + BN) * UMMA_BK * 2;
+  extern __shared__ uint8_t umma_dyn[];
+  __shared__ __align__(8) uint64_t full[ST], empty[ST], done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int timed_out, issued, consumed;
+  const uint32_t ring = (smem_u32(umma_dyn) + 1023u) & ~1023u;
+  const int m0 = blockIdx.x * UMMA_BM, n0 = blockIdx.y * BN;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
+    timed_out = 0;
+    issued = 0;
+    consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  constexpr uint32_t idesc = umma_idesc_bf16(UMMA_BM, BN);
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  const int ktiles = kend > kbeg ? (kend - kbeg + UMMA_BK - 1) / UMMA_BK : 0;
+  C += (size_t)blockIdx.z * (size_t)czstride;
+  if (threadIdx.x == 0) {
+    // producer
+    for (int kt = 0; kt < ktiles; ++kt) {
+      const int s = kt % ST;
+      if (kt >= ST && !mbar_wait(&empty[s], (uint32_t)(((kt / ST) - 1) & 1))) {
+        atomicExch(&timed_out, 1);
+        break;
+      }
+      if (*reinterpret_cast<volatile int*>(&timed_out)) break;
+      mbar_expect_tx(&full[s], STAGE_TX);
+      const uint32_t sa = ring + s * SB, sb = sa + UMMA_A_BYTES;
+      const int k0 = kbeg + kt * UMMA_BK;
+#pragma unroll
+      for (int j = 0; j < UMMA_BK / UMMA_TMA_BOX_K; ++j) {
+        tma_load_2d(sa + j * (UMMA_BM * 16), &ta, k0 + j * UMMA_TMA_BOX_K, m0, &full[s]);
+        tma_load_2d(sb + j * (BN * 16), &tb, k0 + j * UMMA_TMA_BOX_K, n0, &full[s]);
+      }
+      *reinterpret_cast<volatile int*>(&issued) = kt + 1;
+    }
+  } else if (threadIdx.x == 32) {
+    // MMA issuer
+    for (int kt = 0; kt < ktiles; ++kt) {
+      const int s = kt % ST;
+      if (!mbar_wait(&full[s], (uint32_t)((kt / ST) & 1))) {
+        atomicExch(&timed_out, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = ring + s * SB, b0 = a0 + UMMA_A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < UMMA_BK / 16; ++kk) {
+        // K = 16 per MMA = two K-adjacent core columns (two boxes)
+        const uint64_t da = umma_desc(a0 + kk * 2 * (UMMA_BM * 16), UMMA_BM * 16, 128);
+        const uint64_t db = umma_desc(b0 + kk * 2 * (BN * 16), BN * 16, 128);
+        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&empty[s]))
+                   : "memory");
+      *reinterpret_cast<volatile int*>(&consumed) = kt + 1;
+    }
+    // the accumulator is complete when every MMA issued so far is
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(&done))
+                 : "memory");
+  }
+  __syncthreads();
+  if (!mbar_wait(&done, 0)) atomicExch(&timed_out, 1);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!timed_out) {
+    const int row = m0 + warp * 32 + lane;
+    const bool vec = (ldc % 4) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
+    for (int c0 = 0; c0 < BN; c0 += 8) {
+      uint32_t v[8];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float f[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) f[e] = ktiles == 0 ? 0.f : __uint_as_float(v[e]);
+      const int col = n0 + c0;
+      if (row < M && col < N) {
+        float* dst = C + (size_t)row * ldc + col;
+        if (vec && col + 8 <= N) {
+          float4 lo = make_float4(f[0], f[1], f[2], f[3]), hi = make_float4(f[4], f[5], f[6], f[7]);
+          if (beta) {
+            const float4 a = *reinterpret_cast<const float4*>(dst), b = *reinterpret_cast<const float4*>(dst + 4);
+            lo = make_float4(lo.x + a.x, lo.y + a.y, lo.z + a.z, lo.w + a.w);
+            hi = make_float4(hi.x + b.x, hi.y + b.y, hi.z + b.z, hi.w + b.w);
+          }
+          *reinterpret_cast<float4*>(dst) = lo;
+          *reinterpret_cast<float4*>(dst + 4) = hi;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            if (col + e < N) dst[e] = beta ? dst[e] + f[e] : f[e];
+        }
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    // let the copies already issued land before the shared memory goes away
+    const int n_issued = *reinterpret_cast<volatile int*>(&issued);
+    const int n_used = *reinterpret_cast<volatile int*>(&consumed);
+    for (int kt = n_used; kt < n_issued; ++kt) mbar_wait(&full[kt % ST], (uint32_t)((kt / ST) & 1));
+    if (error != nullptr) atomicExch(error, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
