@@ -46,7 +46,8 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // tensor map of a row-major BF16 matrix [rows][cols] with leading dimension
-// ld, read in boxes of 8 columns x box_rows rows, zero fill outside
+// ld, read in boxes of 64 columns x box_rows rows with 128-byte swizzle, zero
+// fill outside
 bool make_tensor_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
   if (fn == nullptr || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
@@ -55,7 +56,7 @@ bool make_tensor_map(CUtensorMap* m, const void* base, int rows, int cols, int l
   const cuuint32_t box[2] = {(cuuint32_t)UMMA_TMA_BOX_K, (cuuint32_t)box_rows};
   const cuuint32_t es[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

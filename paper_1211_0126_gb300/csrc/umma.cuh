@@ -249,19 +249,33 @@ __global__ void __launch_bounds__(UMMA_THREADS) umma_gemm_kernel(const __nv_bflo
 
 // ---------------------------------------------------------------- TMA-fed variant
 // The same product with the operand tiles brought in by the tensor memory
-// accelerator: thread 0 issues, per stage, 8 boxes of 8 columns x 128 rows of
-// A and 8 boxes of 8 columns x BN rows of B (cp.async.bulk.tensor, zero fill
-// outside the matrices) onto an mbarrier with an expected byte count; each
-// box lands as a column of core matrices (8 rows x 16 B, 8-row groups 128 B
-// apart), so K-adjacent core matrices are one box apart (LBO = rows x 16 B,
-// SBO = 128 B).  Thread 32 waits for a stage, issues its four MMAs and lets
-// tcgen05.commit release the stage to the producer; a last commit signals the
-// accumulator to the epilogue.  No thread-wide barrier inside the K loop.
-// Every wait is bounded; on timeout the CTA records the error, waits (bounded)
-// for the copies it issued and for its MMAs, frees TMEM and returns.
+// accelerator: thread 0 issues, per stage, one box of 64 columns x 128 rows
+// of A and one of 64 columns x BN rows of B (cp.async.bulk.tensor with
+// 128-byte swizzle, zero fill outside the matrices) onto an mbarrier with an
+// expected byte count.  Rows land 128 B apart with their 16-byte chunks
+// XOR-permuted within each 1024-byte group of 8 rows -- the canonical K-major
+// SWIZZLE_128B layout of the MMA descriptors (8-row groups 1024 B apart; the
+// K = 16 slices of a stage are 32 B apart inside the swizzle atom).  Thread 32
+// waits for a stage, issues its four MMAs and lets tcgen05.commit release the
+// stage to the producer; a last commit signals the accumulator to the
+// epilogue.  No thread-wide barrier inside the K loop.  Every wait is bounded;
+// on timeout the CTA records the error, waits (bounded) for the copies it
+// issued and for its MMAs, frees TMEM and returns.
 namespace tsm {
 
-constexpr int UMMA_TMA_BOX_K = 8;   // columns per TMA box (16 bytes of BF16)
+constexpr int UMMA_TMA_BOX_K = UMMA_BK;   // columns per TMA box: 64 BF16 = one 128-byte swizzle span
+
+// shared-memory matrix descriptor, canonical K-major layout with 128-byte
+// swizzle: 8-row groups 1024 B apart (SBO), leading offset unused (1)
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;   // swizzle mode: 128 B
+  return d;
+}
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
@@ -336,11 +350,8 @@ __global__ void __launch_bounds__(UMMA_THREADS) umma_tma_gemm_kernel(const __gri
       mbar_expect_tx(&full[s], STAGE_TX);
       const uint32_t sa = ring + s * SB, sb = sa + UMMA_A_BYTES;
       const int k0 = kbeg + kt * UMMA_BK;
-#pragma unroll
-      for (int j = 0; j < UMMA_BK / UMMA_TMA_BOX_K; ++j) {
-        tma_load_2d(sa + j * (UMMA_BM * 16), &ta, k0 + j * UMMA_TMA_BOX_K, m0, &full[s]);
-        tma_load_2d(sb + j * (BN * 16), &tb, k0 + j * UMMA_TMA_BOX_K, n0, &full[s]);
-      }
+      tma_load_2d(sa, &ta, k0, m0, &full[s]);
+      tma_load_2d(sb, &tb, k0, n0, &full[s]);
       *reinterpret_cast<volatile int*>(&issued) = kt + 1;
     }
   } else if (threadIdx.x == 32) {
@@ -355,9 +366,9 @@ __global__ void __launch_bounds__(UMMA_THREADS) umma_tma_gemm_kernel(const __gri
       const uint32_t a0 = ring + s * SB, b0 = a0 + UMMA_A_BYTES;
 #pragma unroll
       for (int kk = 0; kk < UMMA_BK / 16; ++kk) {
-        // K = 16 per MMA = two K-adjacent core columns (two boxes)
-        const uint64_t da = umma_desc(a0 + kk * 2 * (UMMA_BM * 16), UMMA_BM * 16, 128);
-        const uint64_t db = umma_desc(b0 + kk * 2 * (BN * 16), BN * 16, 128);
+        // K = 16 per MMA = 32 bytes further inside the 128-byte swizzle span
+        const uint64_t da = umma_desc_sw128(a0 + kk * 32);
+        const uint64_t db = umma_desc_sw128(b0 + kk * 32);
         const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
