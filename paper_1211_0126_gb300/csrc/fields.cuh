@@ -185,26 +185,36 @@ static __global__ void __launch_bounds__(SITE_NT) accumulate_solution_kernel(int
   store_spinor<F32>(y, sstride, ih, yv);
 }
 
-// reliable update, last step: iterated residual r (F32) = true residual r64
-// (F64), only for right-hand sides with a pending update
-// residual replacement of a reliable update: r = p = the true FP64 residual
-// (the search direction restarts from it: after many FP32 iterations the
-// iterated residual can lie orders of magnitude below the true one, and the
-// old direction would then no longer be conjugate to the replaced residual)
-static __global__ void __launch_bounds__(SITE_NT) replace_residual_kernel(int Vh, const double2* __restrict__ r64,
-                                                                          float4* __restrict__ r,
-                                                                          float4* __restrict__ p, int sstride,
-                                                                          const int* active, const CGState* st) {
+// FP64 -> FP32 copy of a field for the right-hand sides with a reliable
+// update pending (the others return at once)
+static __global__ void __launch_bounds__(SITE_NT) rel_narrow_kernel(int Vh, const double2* __restrict__ in,
+                                                                    float4* __restrict__ out, int sstride,
+                                                                    const int* active, const CGState* st) {
   const int rhs = rhs_slot(active);
   if (!st[rhs].need_rel) return;
   const int ih = blockIdx.y * SITE_NT + threadIdx.x;
   if (ih >= Vh) return;
   cx<double> v[12];
   cx<float> w[12];
-  load_spinor<F64>(r64 + rhs_offset<F64>(rhs, sstride), sstride, ih, v);
+  load_spinor<F64>(in + rhs_offset<F64>(rhs, sstride), sstride, ih, v);
 #pragma unroll
   for (int k = 0; k < 12; ++k) w[k] = {(float)v[k].re, (float)v[k].im};
-  store_spinor<F32>(r + rhs_offset<F32>(rhs, sstride), sstride, ih, w);
+  store_spinor<F32>(out + rhs_offset<F32>(rhs, sstride), sstride, ih, w);
+}
+
+// after a residual replacement the search direction restarts from the new
+// residual, p = r: after many FP32 iterations the iterated residual can lie
+// orders of magnitude below the true one, and the old direction would no
+// longer be conjugate to the replaced residual
+static __global__ void __launch_bounds__(SITE_NT) restart_direction_kernel(int Vh, const float4* __restrict__ r,
+                                                                           float4* __restrict__ p, int sstride,
+                                                                           const int* active, const CGState* st) {
+  const int rhs = rhs_slot(active);
+  if (!st[rhs].need_rel) return;
+  const int ih = blockIdx.y * SITE_NT + threadIdx.x;
+  if (ih >= Vh) return;
+  cx<float> w[12];
+  load_spinor<F32>(r + rhs_offset<F32>(rhs, sstride), sstride, ih, w);
   store_spinor<F32>(p + rhs_offset<F32>(rhs, sstride), sstride, ih, w);
 }
 

@@ -56,57 +56,73 @@ static int upload_list(Ctx& c, int which, const std::vector<int>& list, const in
   return TSM_OK;
 }
 
-// r = b - Dhat^dag Dhat x in FP64 for the listed right-hand sides that have a
-// reliable update pending (st[rhs].need_rel); <r, r> -> st[rhs].rr
-static int normal_residual_f64(Ctx& c, PField x, PField b, PField r, CGState* st, const int* list, int n) {
+// Residual replacement of a reliable update, for the listed right-hand sides
+// that have one pending (st[rhs].need_rel): the true residual of the Schur
+// system bhat - Dhat x is formed in FP64 from the FP64 solution (the only
+// place where cancellation makes FP64 necessary), then the normal residual
+// r = Dhat^dag (bhat - Dhat x) is applied in FP32 into the iterated residual
+// r32, with <r, r> -> st[rhs].rr (POST_SETRR).  Two FP64 and two FP32 hops.
+static int normal_residual_mixed(Ctx& c, PField x, PField bhat, PField r32, CGState* st, const int* list, int n) {
   const double k = c.lat.kappa, mu = c.lat.mu, k2 = k * k;
-  PField t, w;
-  TSM_TRY(c.field("rel_t", TSM_F64, &t, c.batch_cap));
-  TSM_TRY(c.field("rel_w", TSM_F64, &w, c.batch_cap));
-  HopArgs<F64> h = hop_args<F64>(c, 1);
+  PField t64, u64, u32, t32;
+  TSM_TRY(c.field("rel_t", TSM_F64, &t64, c.batch_cap));
+  TSM_TRY(c.field("rel_w", TSM_F64, &u64, c.batch_cap));
+  TSM_TRY(c.field("rel_u32", TSM_F32, &u32, c.batch_cap));
+  TSM_TRY(c.field("rel_t32", TSM_F32, &t32, c.batch_cap));
+  HopArgs<F64> h = hop_args<F64>(c, 1);   // t = A^-1 H_oe x
   h.active = list;
   h.skip = st;
   h.skip_rel = 1;
   h.in = x.as<F64>();
-  h.out = t.as<F64>();
+  h.out = t64.as<F64>();
   h.to = twist_Ainv(k, mu);
   TSM_TRY(launch_hop<F64>(c, h, 0, 0, -1, n));
-  h = hop_args<F64>(c, 0);
+  Twist neg = twist_Ainv(k, mu);           // -A^-1
+  for (int q = 0; q < 2; ++q) {
+    neg.re[q] = -neg.re[q];
+    neg.im[q] = -neg.im[q];
+  }
+  h = hop_args<F64>(c, 0);                 // u = A^-1(-mu) (bhat - Dhat x)
   h.active = list;
   h.skip = st;
   h.skip_rel = 1;
-  h.in = t.as<F64>();
+  h.in = t64.as<F64>();
   h.center = x.as<F64>();
   h.tc = twist_A(k, mu);
   h.ac = 1.0;
   h.ah = -k2;
-  h.to = twist_Ainv(k, mu);
+  h.to = neg;
+  h.base = bhat.as<F64>();
   h.ts = twist_Ainv(k, -mu);
-  h.out = w.as<F64>();
-  TSM_TRY(launch_hop<F64>(c, h, 0, HOP_CENTER, -1, n));
-  h = hop_args<F64>(c, 1);
-  h.active = list;
-  h.skip = st;
-  h.skip_rel = 1;
-  h.in = w.as<F64>();
-  h.out = t.as<F64>();
-  h.to = twist_Ainv(k, -mu);
-  TSM_TRY(launch_hop<F64>(c, h, 1, 0, -1, n));
-  h = hop_args<F64>(c, 0);
-  h.active = list;
-  h.skip = st;
-  h.skip_rel = 1;
-  h.in = t.as<F64>();
-  h.center = w.as<F64>();
-  h.tc = twist_A(k, -mu);
-  h.ac = 1.0;
-  h.ah = -k2;
-  h.to = twist_scale(-1.0);
-  h.base = b.as<F64>();
-  h.out = r.as<F64>();
-  h.st = st;
-  h.post = POST_SETRR;
-  return launch_hop<F64>(c, h, 1, HOP_CENTER | HOP_NORM | HOP_BASE, -1, n);
+  h.out = u64.as<F64>();
+  h.st = nullptr;                          // the norm of this variant is not used
+  TSM_TRY(launch_hop<F64>(c, h, 0, HOP_CENTER | HOP_NORM | HOP_BASE, -1, n));
+  const int blocks = (c.g.Vh + SITE_NT - 1) / SITE_NT;
+  rel_narrow_kernel<<<dim3(n, blocks), SITE_NT, 0, c.stream>>>(c.g.Vh, u64.as<F64>(), u32.as<F32>(), c.sstride,
+                                                                list, st);
+  c.launches++;
+  TSM_TRY(check_launch(c, "rel_narrow_kernel"));
+  HopArgs<F32> g = hop_args<F32>(c, 1);    // t = A^-1(-mu) H^dag_oe u
+  g.active = list;
+  g.skip = st;
+  g.skip_rel = 1;
+  g.in = u32.as<F32>();
+  g.out = t32.as<F32>();
+  g.to = twist_Ainv(k, -mu);
+  TSM_TRY(launch_hop<F32>(c, g, 1, 0, -1, n));
+  g = hop_args<F32>(c, 0);                 // r = A(-mu) u - kappa^2 H^dag_eo t
+  g.active = list;
+  g.skip = st;
+  g.skip_rel = 1;
+  g.in = t32.as<F32>();
+  g.center = u32.as<F32>();
+  g.tc = twist_A(k, -mu);
+  g.ac = 1.0;
+  g.ah = -k2;
+  g.out = r32.as<F32>();
+  g.st = st;
+  g.post = POST_SETRR;
+  return launch_hop<F32>(c, g, 1, HOP_CENTER | HOP_NORM, -1, n);
 }
 
 // Graph while-loop over one batched solve: the condition starts at 1 (the body
@@ -221,7 +237,7 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
     h.post = POST_INIT;
     TSM_TRY(launch_hop<SP>(c, h, 1, HOP_CENTER | HOP_NORM, -1, nrhs));
   }
-  PField p, t, w, r, x, x64, r64;
+  PField p, t, w, r, x, x64;
   TSM_TRY(c.field("cg_p", pS, &p, nb));
   TSM_TRY(c.field("cg_t", pS, &t, nb));
   TSM_TRY(c.field("cg_w", pS, &w, nb));
@@ -232,7 +248,6 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
   TSM_TRY((launch_convert<SA, SA>(c, PField{}, x, nullptr, nrhs)));
   if constexpr (REL) {
     TSM_TRY(c.field("cg_x64", TSM_F64, &x64, nb));
-    TSM_TRY(c.field("cg_r64", TSM_F64, &r64, nb));
     TSM_TRY((launch_convert<F64, F64>(c, PField{}, x64, nullptr, nrhs)));
   }
   // one CG iteration over the listed right-hand sides (n of them), followed,
@@ -290,19 +305,19 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
       // reliable update (Sleijpen & van der Vorst; Clark et al. for lattice QCD):
       // for every right-hand side whose residual fell by delta since the last
       // update, or that met its stopping rule, fold the FP32 increment into the
-      // FP64 solution, replace the iterated residual by the true FP64 normal
-      // residual and restart the search direction from it; the others return
-      // at once from these kernels
+      // FP64 solution, replace the iterated residual by the normal residual of
+      // the true (FP64) Schur residual and restart the search direction from
+      // it; the others return at once from these kernels
       const int blocks = (c.g.Vh + SITE_NT - 1) / SITE_NT;
       accumulate_solution_kernel<<<dim3(n, blocks), SITE_NT, 0, c.stream>>>(c.g.Vh, x.as<F32>(), x64.as<F64>(),
                                                                            c.sstride, dact, st);
       c.launches++;
       TSM_TRY(check_launch(c, "accumulate_solution_kernel"));
-      TSM_TRY(normal_residual_f64(c, x64, r0, r64, st, dact, n));
-      replace_residual_kernel<<<dim3(n, blocks), SITE_NT, 0, c.stream>>>(c.g.Vh, r64.as<F64>(), r.as<F32>(),
-                                                                        p.as<F32>(), c.sstride, dact, st);
+      TSM_TRY(normal_residual_mixed(c, x64, bhat, r, st, dact, n));
+      restart_direction_kernel<<<dim3(n, blocks), SITE_NT, 0, c.stream>>>(c.g.Vh, r.as<F32>(), p.as<F32>(), c.sstride,
+                                                                         dact, st);
       c.launches++;
-      TSM_TRY(check_launch(c, "replace_residual_kernel"));
+      TSM_TRY(check_launch(c, "restart_direction_kernel"));
       rel_finish_kernel<<<1, Ctx::kMaxBatch, 0, c.stream>>>(st, dact, n);
       c.launches++;
       TSM_TRY(check_launch(c, "rel_finish_kernel"));
@@ -387,8 +402,10 @@ int reserve_solver(Ctx& c, const tm_stop& stop) {
   for (const char* name : {"cg_tmp_o", "cg_bhat", "cg_w0", "cg_t0", "cg_r0"}) TSM_TRY(c.field(name, pP, &f, nb));
   for (const char* name : {"cg_p", "cg_t", "cg_w"}) TSM_TRY(c.field(name, pS, &f, nb));
   for (const char* name : {"cg_r", "cg_x"}) TSM_TRY(c.field(name, pA, &f, nb));
-  if (stop.prec == TSM_F32 && stop.reliable)
-    for (const char* name : {"cg_x64", "cg_r64", "rel_t", "rel_w"}) TSM_TRY(c.field(name, TSM_F64, &f, nb));
+  if (stop.prec == TSM_F32 && stop.reliable) {
+    for (const char* name : {"cg_x64", "rel_t", "rel_w"}) TSM_TRY(c.field(name, TSM_F64, &f, nb));
+    for (const char* name : {"rel_u32", "rel_t32"}) TSM_TRY(c.field(name, TSM_F32, &f, nb));
+  }
   return TSM_OK;
 }
 
