@@ -245,6 +245,25 @@ struct Twist {
   double re[2], im[2];
 };
 
+// the same factors rounded once on the host for the FP32-arithmetic kernels
+// (a double-to-float conversion per thread runs on GB300's narrow FP64 pipe)
+struct TwistF {
+  float re[2], im[2];
+};
+
+inline TwistF to_float(const Twist& t) {
+  return TwistF{{(float)t.re[0], (float)t.re[1]}, {(float)t.im[0], (float)t.im[1]}};
+}
+
+template <class R>
+__device__ __forceinline__ void apply_twist(const TwistF& f, cx<R> v[12]) {
+  const cx<R> a = {f.re[0], f.im[0]}, b = {f.re[1], f.im[1]};
+#pragma unroll
+  for (int k = 0; k < 6; ++k) v[k] = a * v[k];
+#pragma unroll
+  for (int k = 6; k < 12; ++k) v[k] = b * v[k];
+}
+
 template <class R>
 __device__ __forceinline__ void apply_twist(const Twist& f, cx<R> v[12]) {
   cx<R> a = {(R)f.re[0], (R)f.im[0]};
@@ -305,6 +324,7 @@ struct CGState {
   double rr0;       // <Dhat^dag bhat, Dhat^dag bhat>
   double pAp;       // <Dhat p, Dhat p>
   double alpha, beta;
+  float alpha_f, beta_f;   // alpha, beta rounded once for the FP32 kernels
   double tol;       // rel_tol
   double aux;       // scratch result (norms of helper reductions)
   double rr_ref;    // <r, r> at the last reliable update
@@ -350,6 +370,7 @@ __device__ __forceinline__ void post_action(CGState* st, int op, double sum) {
     case POST_ALPHA:
       st->pAp = sum;
       st->alpha = st->rr / sum;
+      st->alpha_f = (float)st->alpha;
       if (!finite || !isfinite(st->alpha)) {
         st->status = -5;
         st->done = 1;
@@ -357,6 +378,7 @@ __device__ __forceinline__ void post_action(CGState* st, int op, double sum) {
       break;
     case POST_RR: {
       st->beta = sum / st->rr;
+      st->beta_f = (float)st->beta;
       st->rr = sum;
       st->iter += 1;
       if (!finite) {

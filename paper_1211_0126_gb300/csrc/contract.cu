@@ -125,6 +125,15 @@ int ContractPlan::prepare(Ctx& c, const int* gammas, int n_gamma, const int* mom
   phx = static_cast<double2*>(dev);
   phy = phx + (size_t)n_q * L[0];
   phz = phy + (size_t)n_q * L[1];
+  std::vector<float2> ftab(tab.size());
+  for (size_t k = 0; k < tab.size(); ++k) ftab[k] = make_float2((float)tab[k].x, (float)tab[k].y);
+  void* fdev = nullptr;
+  TSM_TRY(c.buffer("phase_tab_f32", ftab.size() * sizeof(float2), &fdev));
+  TSM_CUDA(cudaMemcpyAsync(fdev, ftab.data(), ftab.size() * sizeof(float2), cudaMemcpyHostToDevice, c.stream));
+  TSM_CUDA(cudaStreamSynchronize(c.stream));
+  fphx = static_cast<float2*>(fdev);
+  fphy = fphx + (size_t)n_q * L[0];
+  fphz = fphy + (size_t)n_q * L[1];
   return TSM_OK;
 }
 
@@ -161,6 +170,9 @@ int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint3
       args.phx = plan.phx + (size_t)q0 * c.lat.L[0];
       args.phy = plan.phy + (size_t)q0 * c.lat.L[1];
       args.phz = plan.phz + (size_t)q0 * c.lat.L[2];
+      args.fphx = plan.fphx + (size_t)q0 * c.lat.L[0];
+      args.fphy = plan.fphy + (size_t)q0 * c.lat.L[1];
+      args.fphz = plan.fphz + (size_t)q0 * c.lat.L[2];
       args.partial = static_cast<double2*>(part);
       args.nbx = nbx;
       args.wa[0] = wa ? wa->e.as<SA>() : nullptr;
@@ -169,6 +181,8 @@ int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint3
       args.wb[1] = wb ? wb->o.as<SB>() : nullptr;
       args.fre = plan.one_end == CT_GEN_ONE_END ? 2.0 : 0.0;
       args.fim = plan.one_end == CT_ONE_END ? -4.0 * c.lat.kappa * c.lat.mu : 0.0;
+      args.ffre = (float)args.fre;
+      args.ffim = (float)args.fim;
       launch(args, dim3(nbx, T, 2));
       c.launches++;
       TSM_TRY(check_launch(c, "contract_kernel"));

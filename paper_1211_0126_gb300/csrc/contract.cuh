@@ -51,7 +51,27 @@ struct ContractArgs {
   double2* partial;     // [T][2][nbx][ng*nq]
   int nbx;
   double fre, fim;      // one-end factor -4 i kappa mu (OE only)
+  const float2* fphx;   // phase tables and factor rounded once to FP32 on the host
+  const float2* fphy;
+  const float2* fphz;
+  float ffre, ffim;
 };
+
+// e^{i q.x} of momentum q (of this pass) at site c, from the per-axis tables
+template <class R, class SA, class SB>
+__device__ __forceinline__ cx<R> phase_at(const ContractArgs<SA, SB>& a, int q, const int c[4]) {
+  if constexpr (sizeof(R) == 4) {
+    const float2 ex = __ldg(a.fphx + q * a.g.L[0] + c[0]);
+    const float2 ey = __ldg(a.fphy + q * a.g.L[1] + c[1]);
+    const float2 ez = __ldg(a.fphz + q * a.g.L[2] + c[2]);
+    return (cx<R>{ex.x, ex.y} * cx<R>{ey.x, ey.y}) * cx<R>{ez.x, ez.y};
+  } else {
+    const double2 ex = __ldg(a.phx + q * a.g.L[0] + c[0]);
+    const double2 ey = __ldg(a.phy + q * a.g.L[1] + c[1]);
+    const double2 ez = __ldg(a.phz + q * a.g.L[2] + c[2]);
+    return (cx<R>{ex.x, ex.y} * cx<R>{ey.x, ey.y}) * cx<R>{ez.x, ez.y};
+  }
+}
 
 template <class R>
 __device__ __forceinline__ cx<R> times_ipow(cx<R> v, int p) {
@@ -210,17 +230,11 @@ __global__ void __launch_bounds__(ContractNT<R>::value) contract_kernel(const Co
         }
         v = v + times_ipow(sv, a.gam.ph[k][row]);
       }
-      if constexpr (MODE != CT_STANDARD) v = cx<R>{(R)a.fre, (R)a.fim} * v;
+      if constexpr (MODE != CT_STANDARD)
+        v = (sizeof(R) == 4 ? cx<R>{(R)a.ffre, (R)a.ffim} : cx<R>{(R)a.fre, (R)a.fim}) * v;
       Gs[threadIdx.x][k] = v;
     }
-    for (int q = 0; q < nq; ++q) {
-      const double2 ex = __ldg(a.phx + q * a.g.L[0] + c[0]);
-      const double2 ey = __ldg(a.phy + q * a.g.L[1] + c[1]);
-      const double2 ez = __ldg(a.phz + q * a.g.L[2] + c[2]);
-      cx<R> p = cx<R>{(R)ex.x, (R)ex.y} * cx<R>{(R)ey.x, (R)ey.y};
-      p = p * cx<R>{(R)ez.x, (R)ez.y};
-      Ps[threadIdx.x][q] = p;
-    }
+    for (int q = 0; q < nq; ++q) Ps[threadIdx.x][q] = phase_at<R>(a, q, c);
   } else {
     for (int k = 0; k < ng; ++k) Gs[threadIdx.x][k] = {0, 0};
     for (int q = 0; q < nq; ++q) Ps[threadIdx.x][q] = {0, 0};
@@ -370,13 +384,7 @@ __global__ void __launch_bounds__(ContractNT<R>::value) deriv_contract_kernel(co
       }
       Gs[threadIdx.x][k] = v;
     }
-    for (int q = 0; q < nq; ++q) {
-      const double2 ex = __ldg(a.phx + q * g.L[0] + c[0]);
-      const double2 ey = __ldg(a.phy + q * g.L[1] + c[1]);
-      const double2 ez = __ldg(a.phz + q * g.L[2] + c[2]);
-      cx<R> p = cx<R>{(R)ex.x, (R)ex.y} * cx<R>{(R)ey.x, (R)ey.y};
-      Ps[threadIdx.x][q] = p * cx<R>{(R)ez.x, (R)ez.y};
-    }
+    for (int q = 0; q < nq; ++q) Ps[threadIdx.x][q] = phase_at<R>(a, q, c);
   } else {
     for (int k = 0; k < ng; ++k) Gs[threadIdx.x][k] = {0, 0};
     for (int q = 0; q < nq; ++q) Ps[threadIdx.x][q] = {0, 0};

@@ -12,6 +12,9 @@ struct ContractPlan {
   const double2* phx = nullptr;   // device phase tables [n_q][Lx], [n_q][Ly], [n_q][Lz]
   const double2* phy = nullptr;
   const double2* phz = nullptr;
+  const float2* fphx = nullptr;   // the same tables rounded once to FP32 (FP32 contractions)
+  const float2* fphy = nullptr;
+  const float2* fphz = nullptr;
   int one_end = 0;                // 1: one-end-trick values (Eq. 2.5) with factor -4 i kappa mu;
                                   // 2: generalised one-end trick (Eq. 2.6): 2 s^dag g5 Gamma g5 D_W s
   int local = 1;                  // the local block (standard or one-end values)

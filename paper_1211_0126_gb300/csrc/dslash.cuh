@@ -184,6 +184,8 @@ struct HopArgs {
   CGState* st;                             // states receiving the HOP_NORM post action
   RedSlot red;                             // HOP_NORM
   int post;                                // PostOp for HOP_NORM
+  float fac, fah;                          // ac, ah, tc, to, ts rounded on the host
+  TwistF ftc, fto, fts;                    // (set by launch_hop)
 };
 
 constexpr int HOP_NT = 128;
@@ -208,18 +210,21 @@ __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) hop_kernel(con
     site_coords(a.g, a.p_out, ih, c);
     cx<R> acc[12];
     hop_site<S, DAG>(a.g, ih, c, a.Uout, a.Uin, a.lstride, a.in + off, a.sstride, acc);
-    const R ah = (R)a.ah;
+    constexpr bool FP32 = sizeof(R) == 4;
+    const R ah = FP32 ? (R)a.fah : (R)a.ah;
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = ah * acc[k];
     if constexpr (MODE & HOP_CENTER) {
       cx<R> v[12];
       load_spinor<S>(a.center + off, a.sstride, ih, v);
-      apply_twist(a.tc, v);
-      const R ac = (R)a.ac;
+      if constexpr (FP32) apply_twist(a.ftc, v);
+      else apply_twist(a.tc, v);
+      const R ac = FP32 ? (R)a.fac : (R)a.ac;
 #pragma unroll
       for (int k = 0; k < 12; ++k) acc[k] = acc[k] + ac * v[k];
     }
-    apply_twist(a.to, acc);
+    if constexpr (FP32) apply_twist(a.fto, acc);
+    else apply_twist(a.to, acc);
     if constexpr (MODE & HOP_BASE) {
       cx<R> v[12];
       load_spinor<S>(a.base + off, a.sstride, ih, v);
@@ -232,7 +237,8 @@ __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) hop_kernel(con
       for (int k = 0; k < 12; ++k) s += norm2(acc[k]);
       part = (double)s;
     }
-    apply_twist(a.ts, acc);
+    if constexpr (FP32) apply_twist(a.fts, acc);
+    else apply_twist(a.ts, acc);
     store_spinor<S>(a.out + off, a.sstride, ih, acc);
   }
   if constexpr (MODE & HOP_NORM) {
@@ -260,6 +266,8 @@ struct CGUpdArgs {
   int sstride;
   double kappa2;
   Twist tw;                         // A(-mu)
+  float fkappa2;                    // kappa2 and tw rounded on the host (set by launch_cg_update)
+  TwistF ftw;
   const int* active;
   CGState* st;
   RedSlot red;
@@ -281,11 +289,13 @@ __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) cg_update_kern
     cx<R> acc[12], v[12];
     hop_site<S, 1>(a.g, ih, c, a.Ue, a.Uo, a.lstride, a.t + off, a.sstride, acc);
     load_spinor<S>(a.w + off, a.sstride, ih, v);
-    apply_twist(a.tw, v);
-    const R k2 = (R)a.kappa2;
+    constexpr bool FP32 = sizeof(R) == 4;
+    if constexpr (FP32) apply_twist(a.ftw, v);
+    else apply_twist(a.tw, v);
+    const R k2 = FP32 ? (R)a.fkappa2 : (R)a.kappa2;
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = v[k] - k2 * acc[k];
-    const RA alpha = (RA)st->alpha;
+    const RA alpha = sizeof(RA) == 4 ? (RA)st->alpha_f : (RA)st->alpha;
     cx<RA> rv[12], xv[12];
     load_spinor<SA>(a.r + offa, a.sstride, ih, rv);
     load_spinor<SA>(a.x + offa, a.sstride, ih, xv);
@@ -318,7 +328,7 @@ __global__ void __launch_bounds__(256) cg_p_kernel(const typename SA::schunk* __
   using RA = typename SA::real;
   r += rhs_offset<SA>(rhs, sstride);
   p += rhs_offset<S>(rhs, sstride);
-  const RA beta = (RA)st[rhs].beta;
+  const RA beta = sizeof(RA) == 4 ? (RA)st[rhs].beta_f : (RA)st[rhs].beta;
   cx<RA> rv[12];
   cx<R> pv[12];
   load_spinor<SA>(r, sstride, ih, rv);

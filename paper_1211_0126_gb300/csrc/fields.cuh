@@ -267,6 +267,7 @@ static __global__ void state_init_kernel(CGState* st, int n, double tol, int max
   s.final_check = 0;
   s.delta2 = delta2;
   s.rr = s.rr0 = s.pAp = s.alpha = s.beta = s.aux = s.rr_ref = 0.0;
+  s.alpha_f = s.beta_f = 0.0f;
 }
 
 }  // namespace tsm

@@ -44,9 +44,15 @@ struct TimedLaunch {
 };
 
 template <class S>
-int launch_hop(Ctx& c, const HopArgs<S>& a, int dag, int mode, int prof_kind, int nrhs) {
-  const int nb = blocks_for(a.g.Vh, HOP_NT);
+int launch_hop(Ctx& c, const HopArgs<S>& a0, int dag, int mode, int prof_kind, int nrhs) {
+  const int nb = blocks_for(a0.g.Vh, HOP_NT);
   if (nb == 0 || nrhs == 0) return TSM_OK;
+  HopArgs<S> a = a0;
+  a.fac = (float)a.ac;
+  a.fah = (float)a.ah;
+  a.ftc = to_float(a.tc);
+  a.fto = to_float(a.to);
+  a.fts = to_float(a.ts);
   const int kind = prof_kind >= 0 ? prof_kind : hop_kind_of<S>(dag, mode);
   const double sb = spinor_site_bytes(S::id), lb = link_site_bytes(S::id);
   // links once per launch (shared by the right-hand sides), spinor streams per RHS
@@ -75,9 +81,12 @@ int launch_hop(Ctx& c, const HopArgs<S>& a, int dag, int mode, int prof_kind, in
 }
 
 template <class S, class SA>
-int launch_cg_update(Ctx& c, const CGUpdArgs<S, SA>& a, int nrhs) {
-  const int nb = blocks_for(a.g.Vh, HOP_NT);
+int launch_cg_update(Ctx& c, const CGUpdArgs<S, SA>& a0, int nrhs) {
+  const int nb = blocks_for(a0.g.Vh, HOP_NT);
   if (nb == 0 || nrhs == 0) return TSM_OK;
+  CGUpdArgs<S, SA> a = a0;
+  a.fkappa2 = (float)a.kappa2;
+  a.ftw = to_float(a.tw);
   const double sb = spinor_site_bytes(S::id), lb = link_site_bytes(S::id), sa = spinor_site_bytes(SA::id);
   TimedLaunch tl(c, 4 * S::id + PK_HOP_UPDATE, (double)a.g.Vh * (lb + nrhs * (3 * sb + 4 * sa)));
   cg_update_kernel<S, SA><<<dim3(nrhs, nb), HOP_NT, 0, c.stream>>>(a);
