@@ -480,14 +480,7 @@ int tsm_load_gauge(tsm_ctx* h, const tm_lattice* lat, const double* U, int on_de
   const bool resize = !c.has_gauge || (int)V != c.g.V;
   c.has_gauge = false;
   c.lat = *lat;
-  c.g.L[0] = lat->L[0];
-  c.g.L[1] = lat->L[1];
-  c.g.L[2] = lat->L[2];
-  c.g.L[3] = lat->L[3];
-  c.g.V = (int)V;
-  c.g.Vh = (int)(V / 2);
-  c.g.Lxh = lat->L[0] / 2;
-  c.g.apbc = lat->t_antiperiodic ? 1 : 0;
+  c.g = make_geom(lat->L, lat->t_antiperiodic);
   c.sstride = c.g.Vh;
   c.lstride = c.g.Vh;
   if (resize) {

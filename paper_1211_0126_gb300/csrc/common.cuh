@@ -44,19 +44,53 @@ struct Geom {
   int V, Vh;    // volume, half volume
   int Lxh;      // Lx / 2
   int apbc;     // 1: antiperiodic in t
+  // division of a half-site index by Lxh, Ly and Lz as a multiply-high:
+  // n / d = umulhi(n, floor(2^32 / d) + 1) exactly whenever n * d < 2^32
+  // (n = q d + r: the product's error term n e / 2^32, e <= d, stays below
+  // d - r >= 1).  m = 0 marks d = 1.  fastdiv = 0 (Vh * max(L) >= 2^32)
+  // falls back to the hardware-free integer division.
+  uint32_t mxh, my, mz;
+  int fastdiv;
 };
 
+inline uint32_t div_magic(int d) { return d <= 1 ? 0u : (uint32_t)((1ull << 32) / (unsigned)d + 1ull); }
+
+// geometry of an Lx x Ly x Lz x T lattice (Lx even)
+inline Geom make_geom(const int L[4], int apbc) {
+  Geom g{};
+  for (int k = 0; k < 4; ++k) g.L[k] = L[k];
+  const long long V = (long long)L[0] * L[1] * L[2] * L[3];
+  g.V = (int)V;
+  g.Vh = (int)(V / 2);
+  g.Lxh = L[0] / 2;
+  g.apbc = apbc ? 1 : 0;
+  g.mxh = div_magic(g.Lxh);
+  g.my = div_magic(L[1]);
+  g.mz = div_magic(L[2]);
+  int lmax = g.Lxh;
+  if (L[1] > lmax) lmax = L[1];
+  if (L[2] > lmax) lmax = L[2];
+  g.fastdiv = (unsigned long long)g.Vh * (unsigned long long)lmax < (1ull << 32) ? 1 : 0;
+  return g;
+}
+
+__device__ __forceinline__ uint32_t geom_div(const Geom& g, uint32_t n, uint32_t d, uint32_t m) {
+  if (g.fastdiv) return m ? __umulhi(n, m) : n;
+  return n / d;
+}
+
 __device__ __forceinline__ void site_coords(const Geom& g, int parity, int ih, int c[4]) {
-  int xh = ih % g.Lxh;
-  int r = ih / g.Lxh;
-  int y = r % g.L[1];
-  r /= g.L[1];
-  int z = r % g.L[2];
-  int t = r / g.L[2];
-  c[0] = 2 * xh + ((parity + y + z + t) & 1);
+  const uint32_t n = (uint32_t)ih;
+  const uint32_t r1 = geom_div(g, n, (uint32_t)g.Lxh, g.mxh);
+  const int xh = (int)(n - r1 * (uint32_t)g.Lxh);
+  const uint32_t r2 = geom_div(g, r1, (uint32_t)g.L[1], g.my);
+  const int y = (int)(r1 - r2 * (uint32_t)g.L[1]);
+  const uint32_t t = geom_div(g, r2, (uint32_t)g.L[2], g.mz);
+  const int z = (int)(r2 - t * (uint32_t)g.L[2]);
+  c[0] = 2 * xh + ((parity + y + z + (int)t) & 1);
   c[1] = y;
   c[2] = z;
-  c[3] = t;
+  c[3] = (int)t;
 }
 
 __device__ __forceinline__ int half_index(const Geom& g, int x, int y, int z, int t) {

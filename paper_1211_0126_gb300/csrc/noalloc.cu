@@ -230,14 +230,7 @@ extern "C" int tsm_contract_noalloc(const tm_lattice* lat, uint64_t seed, int ki
   TSM_CUDA(cudaMemcpyAsync(scratch, g_noalloc_phase, (size_t)n_phase * sizeof(double2), cudaMemcpyHostToDevice,
                            stream));
   NoallocArgs a{};
-  a.g.L[0] = lat->L[0];
-  a.g.L[1] = lat->L[1];
-  a.g.L[2] = lat->L[2];
-  a.g.L[3] = lat->L[3];
-  a.g.V = (int)V;
-  a.g.Vh = (int)(V / 2);
-  a.g.Lxh = lat->L[0] / 2;
-  a.g.apbc = lat->t_antiperiodic ? 1 : 0;
+  a.g = make_geom(lat->L, lat->t_antiperiodic);
   a.noise = make_noise(seed, kind);
   a.source = source;
   a.s = reinterpret_cast<const double2*>(s_dev);
