@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / equal-error / cpu-baseline legs")
     ap.add_argument("--batch", type=int, default=32, help="sources solved together (multi-RHS kernels)")
     ap.add_argument("--reliable-delta", type=float, default=None, help="override the HP reliable-update delta")
+    ap.add_argument("--hp-warm-start", action="store_true",
+                    help="HP solves start from their source's LP solution instead of zero")
     ap.add_argument("--mode", default="eager", choices=["eager", "graph"],
                     help="eager: host-driven chunked CG loops; graph: one captured CUDA graph per step "
                          "(device-side loops, LP set beside the HP set)")
@@ -364,7 +366,8 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
 
     def step(seed, verify=False):
-        p = tsm.params(seed, 4, hp_range, lp_range, hp_stop, lp_stop, gam, moms, batch=args.batch, verify=verify)
+        p = tsm.params(seed, 4, hp_range, lp_range, hp_stop, lp_stop, gam, moms, batch=args.batch, verify=verify,
+                       hp_warm_start=args.hp_warm_start)
         if args.mode == "graph" and not verify:
             return tsm.tsm_loops_graph([ctx.h], [p], loops=[d_loops], err=[d_err], per_corr=[d_pc],
                                        per_lp=[d_pl])[0]
@@ -444,6 +447,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "lattice": list(DIMS), "n_hp_per_gpu": N_HP, "n_lp_per_gpu": N_LP,
                        "batch": args.batch, "reliable_delta": rdelta,
+                       "hp_start": "lp-solution" if args.hp_warm_start else "zero",
                        "mode": args.mode,
                        "l2": "flushed between steps (256 MB write)",
                        "lp_iters_per_source": st.lp_iters / float(N_HP + N_LP),
@@ -454,7 +458,7 @@ def run_ours(args):
     if rank == 0 and not args.no_extras:
         line["dslash"] = dslash_gbs(ctx, S, tsm, flush, peak)
         line["e2e"] = e2e_leg(ctx, tsm, U_pinned, lp_stop, hp_stop, gam, moms, stream, hp_range, lp_range,
-                              batch=args.batch)
+                              batch=args.batch, warm=args.hp_warm_start)
         line["equal_error"] = equal_error(ctx, tsm, S, d_pc, d_pl, step_ms, stream)
         t_it, t_src = oracle_sample(U)
         cpu_val = oracle_rate(t_it, t_src, st.lp_iters / float(N_HP + N_LP), st.hp_iters / float(N_HP))
@@ -497,7 +501,8 @@ def dslash_gbs(ctx, S, tsm, flush, peak):
     return res
 
 
-def e2e_leg(ctx, tsm, U_pinned, lp_stop, hp_stop, gam, moms, stream, hp_range, lp_range, steps=2, batch=1):
+def e2e_leg(ctx, tsm, U_pinned, lp_stop, hp_stop, gam, moms, stream, hp_range, lp_range, steps=2, batch=1,
+            warm=False):
     """The same TSM step through the public API with host buffers: gauge field
     uploaded from pinned host memory, loops and errors read back to host."""
     import torch
@@ -509,7 +514,8 @@ def e2e_leg(ctx, tsm, U_pinned, lp_stop, hp_stop, gam, moms, stream, hp_range, l
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tsm.tsm_load_gauge(ctx.h, ctx.lat, U_pinned)
-        p = tsm.params(30_000 + k, 4, hp_range, lp_range, hp_stop, lp_stop, gam, moms, batch=batch)
+        p = tsm.params(30_000 + k, 4, hp_range, lp_range, hp_stop, lp_stop, gam, moms, batch=batch,
+                       hp_warm_start=warm)
         tsm.tsm_loops(ctx.h, p, loops, err)
         ms.append((time.perf_counter() - t0) * 1e3)
     t = float(np.mean(ms))

@@ -262,6 +262,10 @@ typedef struct {
                                tsm_contract_fft); moms / n_q are ignored, outputs are
                                [n_gamma][T][Lz][Ly][Lx], per_corr / per_lp must be NULL
                                (means and variances are accumulated in source order) */
+  int hp_warm_start;        /* 1: each HP solve of tier FP32 with FP64 reliable updates starts
+                               from its source's LP solution (the LP map is unchanged, so the
+                               estimate stays unbiased; the HP solution still meets hp.rel_tol);
+                               ignored for the other HP tiers.  0: zero start */
 } tsm_params;
 
 /* Run the TSM over this call's source ranges.  Outputs (host or device per

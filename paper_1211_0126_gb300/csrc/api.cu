@@ -360,7 +360,11 @@ int record_run(Ctx& c, const tsm_params* p, TsmRun& run, tsm_loop_stats* st) {
     TSM_TRY(solve_batch(c, p->lp, slots(n, c.cap_lp), n, run.b_lp, run.s_lp, r_lp.data()));
     if (sp_hp != sp_lp) TSM_TRY(gen(sp_hp, j0, run.b_hp, n));
     EOField bh = (sp_hp != sp_lp) ? run.b_hp : run.b_lp;
-    TSM_TRY(solve_batch(c, p->hp, slots(n, c.cap_hp), n, bh, run.s_hp, r_hp.data()));
+    // optional warm start of the HP solves from the LP solutions (the LP map
+    // itself is untouched, so both sets keep the same LP solver)
+    const bool warm = p->hp_warm_start && p->hp.prec == TSM_F32 && p->hp.reliable && !p->hp.precond;
+    TSM_TRY(solve_batch(c, p->hp, slots(n, c.cap_hp), n, bh, run.s_hp, r_hp.data(), warm ? &run.s_lp.e : nullptr,
+                        solution_prec(p->lp)));
     for (int r = 0; r < n; ++r) {
       if (!c.capturing) {
         if (r_lp[r].status != TSM_OK || r_hp[r].status != TSM_OK) return bad(TSM_ERR_NONFINITE, "NaN/Inf in a solve");

@@ -233,6 +233,18 @@ static __global__ void rel_finish_kernel(CGState* st, const int* active, int n) 
   }
 }
 
+// a warm-started solve asks every iterating source for a residual replacement
+// before its first iteration; final_check lets rel_finish_kernel stop a source
+// whose starting guess already meets the rule
+static __global__ void warm_start_kernel(CGState* st, int n) {
+  const int k = threadIdx.x + blockIdx.x * blockDim.x;
+  if (k >= n) return;
+  CGState& s = st[k];
+  if (s.done || s.status != 0) return;
+  s.need_rel = 1;
+  s.final_check = 1;
+}
+
 // <v, v> per right-hand side with post action (deterministic two-stage sum)
 template <class S>
 __global__ void __launch_bounds__(SITE_NT) norm_kernel(int Vh, const typename S::schunk* __restrict__ v, int sstride,

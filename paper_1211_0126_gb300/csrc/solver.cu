@@ -190,7 +190,8 @@ static int capture_while(Ctx& c, CGState* st, int n, int max_iter, Body&& body) 
 // solution storage (also used for bhat and the initial Dhat^dag bhat);
 // REL: FP32 iterations with an FP64 solution and FP64 residual replacement.
 template <class S, class SA, class SP, bool REL>
-static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EOField s, SolveResult* res) {
+static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EOField s, SolveResult* res,
+                    const PField* x0, int x0_prec) {
   const double k = c.lat.kappa, mu = c.lat.mu, k2 = k * k;
   CGState* st = c.states + s0;
   const int pS = S::id, pA = SA::id, pP = SP::id;
@@ -248,7 +249,27 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
   TSM_TRY((launch_convert<SA, SA>(c, PField{}, x, nullptr, nrhs)));
   if constexpr (REL) {
     TSM_TRY(c.field("cg_x64", TSM_F64, &x64, nb));
-    TSM_TRY((launch_convert<F64, F64>(c, PField{}, x64, nullptr, nrhs)));
+    if (x0 == nullptr) {
+      TSM_TRY((launch_convert<F64, F64>(c, PField{}, x64, nullptr, nrhs)));
+    } else {
+      // warm start: x = x0, r = Dhat^dag (bhat - Dhat x0) in the reliable
+      // update's mixed precision, p = r; a source whose start already meets
+      // the stopping rule stops here (rel_finish_kernel)
+      if (x0_prec == TSM_F64) TSM_TRY((launch_convert<F64, F64>(c, *x0, x64, nullptr, nrhs)));
+      else TSM_TRY((launch_convert<F32, F64>(c, *x0, x64, nullptr, nrhs)));
+      warm_start_kernel<<<1, Ctx::kMaxBatch, 0, c.stream>>>(st, nrhs);
+      c.launches++;
+      TSM_TRY(check_launch(c, "warm_start_kernel"));
+      TSM_TRY(normal_residual_mixed(c, x64, bhat, r, st, nullptr, nrhs));
+      const int blocks = (c.g.Vh + SITE_NT - 1) / SITE_NT;
+      restart_direction_kernel<<<dim3(nrhs, blocks), SITE_NT, 0, c.stream>>>(c.g.Vh, r.as<F32>(), p.as<F32>(),
+                                                                             c.sstride, nullptr, st);
+      c.launches++;
+      TSM_TRY(check_launch(c, "restart_direction_kernel"));
+      rel_finish_kernel<<<1, Ctx::kMaxBatch, 0, c.stream>>>(st, nullptr, nrhs);
+      c.launches++;
+      TSM_TRY(check_launch(c, "rel_finish_kernel"));
+    }
   }
   // one CG iteration over the listed right-hand sides (n of them), followed,
   // with reliable updates, by the FP64 update of those that asked for one
@@ -409,19 +430,26 @@ int reserve_solver(Ctx& c, const tm_stop& stop) {
   return TSM_OK;
 }
 
-int solve_batch(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EOField s, SolveResult* res) {
+int solve_batch(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EOField s, SolveResult* res,
+                const PField* x0, int x0_prec) {
   if (stop.precond) return fgmres_batch(c, stop, nrhs, b, s, res);
   if (nrhs < 1 || nrhs > c.batch_cap || s0 < 0 || s0 + nrhs > Ctx::kMaxStates - 4) {
     set_error("batch of %d right-hand sides at state %d exceeds the capacity (%d)", nrhs, s0, c.batch_cap);
     return TSM_ERR_TOO_LARGE;
   }
   switch (stop.prec) {
-    case TSM_F64: return cg_solve<F64, F64, F64, false>(c, stop, s0, nrhs, b, s, res);
+    case TSM_F64: return cg_solve<F64, F64, F64, false>(c, stop, s0, nrhs, b, s, res, nullptr, -1);
     case TSM_F32:
-      if (stop.reliable) return cg_solve<F32, F32, F64, true>(c, stop, s0, nrhs, b, s, res);
-      return cg_solve<F32, F32, F32, false>(c, stop, s0, nrhs, b, s, res);
-    case TSM_F16: return cg_solve<F16, F32, F32, false>(c, stop, s0, nrhs, b, s, res);
-    case TSM_BF16: return cg_solve<BF16, F32, F32, false>(c, stop, s0, nrhs, b, s, res);
+      if (stop.reliable) {
+        if (x0 != nullptr && x0_prec != TSM_F32 && x0_prec != TSM_F64) {
+          set_error("starting guess of tier %d (FP32 or FP64 expected)", x0_prec);
+          return TSM_ERR_ARG;
+        }
+        return cg_solve<F32, F32, F64, true>(c, stop, s0, nrhs, b, s, res, x0, x0_prec);
+      }
+      return cg_solve<F32, F32, F32, false>(c, stop, s0, nrhs, b, s, res, nullptr, -1);
+    case TSM_F16: return cg_solve<F16, F32, F32, false>(c, stop, s0, nrhs, b, s, res, nullptr, -1);
+    case TSM_BF16: return cg_solve<BF16, F32, F32, false>(c, stop, s0, nrhs, b, s, res, nullptr, -1);
     default: set_error("unknown solver tier %d", stop.prec); return TSM_ERR_ARG;
   }
 }

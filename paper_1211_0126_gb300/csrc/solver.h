@@ -21,8 +21,13 @@ int solution_prec(const tm_stop& stop);
 // Solve D_tm s_r = b_r for nrhs independent sources at once.  b and s are
 // batches of nrhs contiguous even/odd fields of tier solution_prec(stop) laid
 // out for c.batch_cap sources; device solver states s0 .. s0+nrhs-1 are used;
-// res receives nrhs results.
-int solve_batch(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EOField s, SolveResult* res);
+// res receives nrhs results.  x0 (optional; FP32 with FP64 reliable updates
+// only, ignored by the other tiers): a batch of even-site starting guesses of
+// storage tier x0_prec (TSM_F32 or TSM_F64); the first iterate's residual is
+// then the true normal residual of b - D x0, computed as in a reliable update,
+// and the stopping rule stays relative to ||Dhat^dag bhat||.
+int solve_batch(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EOField s, SolveResult* res,
+                const PField* x0 = nullptr, int x0_prec = -1);
 
 // Allocate the solver workspace of a tier for c.batch_cap sources in advance.
 int reserve_solver(Ctx& c, const tm_stop& stop);

@@ -53,7 +53,8 @@ class TsmParams(ctypes.Structure):
                 ("hp", TmStop), ("lp", TmStop), ("batch", ctypes.c_int),
                 ("gammas", ctypes.POINTER(ctypes.c_int)), ("n_gamma", ctypes.c_int),
                 ("moms", ctypes.POINTER(ctypes.c_int)), ("n_q", ctypes.c_int), ("verify", ctypes.c_int),
-                ("estimator", ctypes.c_int), ("deriv_mask", ctypes.c_int), ("all_momenta", ctypes.c_int)]
+                ("estimator", ctypes.c_int), ("deriv_mask", ctypes.c_int), ("all_momenta", ctypes.c_int),
+                ("hp_warm_start", ctypes.c_int)]
 
 
 # exported symbol -> (restype, argtypes)
@@ -317,7 +318,7 @@ def tsm_contract_noalloc(lat, seed, kind, source, s_dev, gammas, moms, out_dev, 
 
 
 def params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batch=1, verify=False,
-           estimator=0, deriv_mask=0, all_momenta=False):
+           estimator=0, deriv_mask=0, all_momenta=False, hp_warm_start=False):
     """TsmParams; keeps the integer arrays alive on the returned object."""
     p = TsmParams()
     p.seed = int(seed)
@@ -338,6 +339,7 @@ def params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batc
     p.estimator = int(estimator)
     p.deriv_mask = int(deriv_mask)
     p.all_momenta = 1 if all_momenta else 0
+    p.hp_warm_start = 1 if hp_warm_start else 0
     return p
 
 
@@ -575,13 +577,14 @@ class Context:
         return out
 
     def loops(self, seed, noise, n_hp, n_lp, hp_stop, lp_stop, gammas, moms, hp_range=None, lp_range=None,
-              per_source=False, batch=1, verify=True, estimator=0, deriv_mask=0, all_momenta=False):
+              per_source=False, batch=1, verify=True, estimator=0, deriv_mask=0, all_momenta=False,
+              hp_warm_start=False):
         hp_range = hp_range or (0, n_hp)
         lp_range = lp_range or (n_hp, n_hp + n_lp)
         if all_momenta:
             moms = [(0, 0, 0)]
         p = params(seed, noise, hp_range, lp_range, hp_stop, lp_stop, gammas, moms, batch, verify, estimator,
-                   deriv_mask, all_momenta)
+                   deriv_mask, all_momenta, hp_warm_start)
         shape = (len(gammas), len(moms), self.dims[3])
         if deriv_mask:
             shape = (1 + bin(int(deriv_mask)).count("1"),) + shape

@@ -110,3 +110,30 @@ def test_batched_tsm_bit_identical(ctx, field, batch):
     for k in ("loops", "err", "per_corr", "per_lp"):
         assert np.array_equal(one[k], many[k]), k
     assert one["stats"]["lp_iters"] == many["stats"]["lp_iters"]
+
+
+def test_hp_warm_start(ctx):
+    """HP solves started from the LP solutions: the LP map and the LP-set loops
+    are bit-identical to the zero-start run, every HP solution still meets the
+    FP64 true-residual bar, each source's HP loop L(s_HP) = corr + L(s_LP)
+    agrees with the zero-start one to the HP tolerance, and fewer HP iterations
+    are needed.  6^3x8 so that the HP solves take enough iterations to show it."""
+    dims = (6, 6, 6, 8)
+    u = S.gauge_field(dims, 0.25, 3)
+    ctx.load_gauge(u, dims, 0.1245, 0.005)
+    moms = S.default_momenta(7)
+    hp = tsm.stop(1e-10, 5000, tsm.TSM_F32, reliable=True, reliable_delta=1e-5)
+    lp = tsm.stop(5e-3, 60, tsm.TSM_F16)
+    cold = ctx.loops(41, 4, 6, 10, hp, lp, GAM, moms, per_source=True, batch=6)
+    warm = ctx.loops(41, 4, 6, 10, hp, lp, GAM, moms, per_source=True, batch=6, hp_warm_start=True)
+    assert np.array_equal(cold["per_lp"], warm["per_lp"])
+    assert cold["stats"]["lp_iters"] == warm["stats"]["lp_iters"]
+    assert warm["stats"]["hp_not_converged"] == 0
+    assert warm["stats"]["hp_max_true_res"] < 1e-9
+    # same LP solutions on both sides, so the difference of the corrections is
+    # L(s_HP, zero start) - L(s_HP, LP start): the HP tolerance plus the FP32
+    # rounding of the site sums of the contraction (216 sites per timeslice)
+    diff = cold["per_corr"] - warm["per_corr"]
+    assert np.abs(diff).max() <= 2e-6 * max(np.abs(cold["per_corr"]).max(), 1.0)
+    assert warm["stats"]["hp_iters"] <= 0.95 * cold["stats"]["hp_iters"]
+    assert np.isfinite(warm["loops"]).all()
