@@ -416,7 +416,7 @@ int reserve_solver(Ctx& c, const tm_stop& stop) {
   switch (stop.prec) {
     case TSM_F64: pS = pA = pP = TSM_F64; break;
     case TSM_F32: pS = pA = TSM_F32; pP = stop.reliable ? TSM_F64 : TSM_F32; break;
-    default: pS = stop.prec; pA = pP = TSM_F32; break;
+    default: pS = stop.prec; pA = stop.prec == TSM_F16 ? TSM_F16 : TSM_F32; pP = TSM_F32; break;
   }
   const int nb = c.batch_cap;
   PField f;
@@ -448,7 +448,9 @@ int solve_batch(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EOFiel
         return cg_solve<F32, F32, F64, true>(c, stop, s0, nrhs, b, s, res, x0, x0_prec);
       }
       return cg_solve<F32, F32, F32, false>(c, stop, s0, nrhs, b, s, res, nullptr, -1);
-    case TSM_F16: return cg_solve<F16, F32, F32, false>(c, stop, s0, nrhs, b, s, res, nullptr, -1);
+    // FP16 tier: r and x in FP16 too (relative storage precision 2^-11, an order
+    // below the LP truncation; the memory-bound CG update moves 36 % fewer bytes)
+    case TSM_F16: return cg_solve<F16, F16, F32, false>(c, stop, s0, nrhs, b, s, res, nullptr, -1);
     case TSM_BF16: return cg_solve<BF16, F32, F32, false>(c, stop, s0, nrhs, b, s, res, nullptr, -1);
     default: set_error("unknown solver tier %d", stop.prec); return TSM_ERR_ARG;
   }
