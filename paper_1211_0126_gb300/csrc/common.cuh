@@ -456,12 +456,15 @@ struct RedSlot {
   int stride;
 };
 
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* sh) {
+// fixed-order block sum: the warp stage in the value's own type (an FP32
+// partial stays FP32 across the 32 lanes, off GB300's narrow FP64 pipe), the
+// warps' sums in FP64
+template <int NT, class V>
+__device__ __forceinline__ double block_sum(V v, double* sh) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) sh[warp] = v;
+  if (lane == 0) sh[warp] = (double)v;
   __syncthreads();
   double s = 0.0;
   if (threadIdx.x == 0) {
@@ -474,8 +477,8 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // Called by all threads of every block of right-hand side `rhs`.  Returns
 // true in the last block of that RHS, in which thread 0 holds its total.
-template <int NT>
-__device__ __forceinline__ bool grid_sum(double v, RedSlot slot, int rhs, double* total) {
+template <int NT, class V>
+__device__ __forceinline__ bool grid_sum(V v, RedSlot slot, int rhs, double* total) {
   __shared__ double sh[NT / 32];
   __shared__ bool is_last;
   const int nblocks = gridDim.y;

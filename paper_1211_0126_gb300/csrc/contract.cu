@@ -187,8 +187,9 @@ int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint3
       c.launches++;
       TSM_TRY(check_launch(c, "contract_kernel"));
       const int nred = nout * T;
-      contract_reduce_kernel<<<(nred + 127) / 128, 128, 0, c.stream>>>(static_cast<double2*>(part), T, nbx,
-                                                                        plan.ng, nq, plan.n_q, q0, dst);
+      const unsigned rblocks = (unsigned)(((size_t)nred * 32 + 127) / 128);   // a warp per output
+      contract_reduce_kernel<<<rblocks, 128, 0, c.stream>>>(static_cast<double2*>(part), T, nbx, plan.ng, nq,
+                                                            plan.n_q, q0, dst);
       c.launches++;
       TSM_TRY(check_launch(c, "contract_reduce_kernel"));
     }

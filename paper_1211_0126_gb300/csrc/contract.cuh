@@ -83,6 +83,22 @@ __device__ __forceinline__ cx<R> times_ipow(cx<R> v, int p) {
   }
 }
 
+// sum over the block's sites of phase(q) x density(g): four interleaved
+// accumulators (sites s, s+4, ...) added pairwise at the end, so that the
+// dependent FMA chain is a quarter as long; a fixed order
+template <int NT, class R, int LD>
+__device__ __forceinline__ cx<R> block_phase_sum(const cx<R> (*Ps)[LD], const cx<R> (*Gs)[LD], int q, int gi) {
+  cx<R> a0 = {0, 0}, a1 = {0, 0}, a2 = {0, 0}, a3 = {0, 0};
+#pragma unroll 4
+  for (int s2 = 0; s2 < NT; s2 += 4) {
+    a0 = a0 + Ps[s2][q] * Gs[s2][gi];
+    a1 = a1 + Ps[s2 + 1][q] * Gs[s2 + 1][gi];
+    a2 = a2 + Ps[s2 + 2][q] * Gs[s2 + 2][gi];
+    a3 = a3 + Ps[s2 + 3][q] * Gs[s2 + 3][gi];
+  }
+  return (a0 + a1) + (a2 + a3);
+}
+
 template <class R> struct ContractNT { static constexpr int value = 128; };
 template <> struct ContractNT<double> { static constexpr int value = 64; };
 
@@ -245,8 +261,7 @@ __global__ void __launch_bounds__(ContractNT<R>::value) contract_kernel(const Co
   double2* dst = a.partial + ((size_t)(t * 2 + parity) * a.nbx + blockIdx.x) * nout;
   for (int k = threadIdx.x; k < nout; k += NT) {
     const int gi = k % ng, q = k / ng;
-    cx<R> acc = {0, 0};
-    for (int s2 = 0; s2 < NT; ++s2) acc = acc + Ps[s2][q] * Gs[s2][gi];
+    const cx<R> acc = block_phase_sum<NT>(Ps, Gs, q, gi);
     dst[k] = make_double2((double)acc.re, (double)acc.im);
   }
 }
@@ -394,29 +409,37 @@ __global__ void __launch_bounds__(ContractNT<R>::value) deriv_contract_kernel(co
   double2* dst = a.partial + ((size_t)(t * 2 + parity) * a.nbx + blockIdx.x) * nout;
   for (int k = threadIdx.x; k < nout; k += NT) {
     const int gi = k % ng, q = k / ng;
-    cx<R> acc = {0, 0};
-    for (int s2 = 0; s2 < NT; ++s2) acc = acc + Ps[s2][q] * Gs[s2][gi];
+    const cx<R> acc = block_phase_sum<NT>(Ps, Gs, q, gi);
     dst[k] = make_double2((double)acc.re, (double)acc.im);
   }
 }
 
 // sum the block partials of one timeslice in fixed order into the output
 // layout [g][q][t] (momenta q0 .. q0+nq-1 of nq_total)
+// one warp per output k = t * (ng * nq) + (q * ng + g): lane l adds the
+// block partials l, l + 32, ... of both parities, then a fixed shuffle tree
 static __global__ void contract_reduce_kernel(const double2* __restrict__ partial, int T, int nbx, int ng, int nq,
                                        int nq_total, int q0, double2* __restrict__ out) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // k = t * (ng * nq) + (q * ng + g): reads coalesce
+  const int k = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   const int nout = ng * nq;
-  if (k >= nout * T) return;
+  if (k >= nout * T) return;   // the same for the whole warp
   const int t = k / nout, gq = k % nout;
   double re = 0.0, im = 0.0;
-  for (int par = 0; par < 2; ++par)
-    for (int b = 0; b < nbx; ++b) {
-      const double2 v = partial[((size_t)(t * 2 + par) * nbx + b) * nout + gq];
-      re += v.x;
-      im += v.y;
-    }
-  const int gi = gq % ng, q = gq / ng;
-  out[((size_t)gi * nq_total + q0 + q) * T + t] = make_double2(re, im);
+  for (int i = lane; i < 2 * nbx; i += 32) {
+    const int par = i / nbx, b = i % nbx;
+    const double2 v = partial[((size_t)(t * 2 + par) * nbx + b) * nout + gq];
+    re += v.x;
+    im += v.y;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_down_sync(0xffffffffu, re, o);
+    im += __shfl_down_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) {
+    const int gi = gq % ng, q = gq / ng;
+    out[((size_t)gi * nq_total + q0 + q) * T + t] = make_double2(re, im);
+  }
 }
 
 // Eq. 2.4 per entry: mean of the corrections + mean of the LP set; error from

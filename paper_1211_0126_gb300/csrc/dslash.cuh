@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) hop_kernel(con
   if (a.skip != nullptr && (a.skip_rel ? !a.skip[rhs].need_rel : a.skip[rhs].done)) return;
   const size_t off = rhs_offset<S>(rhs, a.sstride);
   const int ih = blockIdx.y * HOP_NT + threadIdx.x;
-  double part = 0.0;
+  R part = 0;   // FP32 kernels: FP32 up to the warp sums
   if (ih < a.g.Vh) {
     int c[4];
     site_coords(a.g, a.p_out, ih, c);
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) hop_kernel(con
       R s = 0;
 #pragma unroll
       for (int k = 0; k < 12; ++k) s += norm2(acc[k]);
-      part = (double)s;
+      part = s;
     }
     if constexpr (FP32) apply_twist(a.fts, acc);
     else apply_twist(a.ts, acc);
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) cg_update_kern
   if (st->done) return;
   const size_t off = rhs_offset<S>(rhs, a.sstride), offa = rhs_offset<SA>(rhs, a.sstride);
   const int ih = blockIdx.y * HOP_NT + threadIdx.x;
-  double part = 0.0;
+  typename SA::real part = 0;
   if (ih < a.g.Vh) {
     int c[4];
     site_coords(a.g, 0, ih, c);
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) cg_update_kern
       xv[k] = xv[k] + alpha * cx<RA>{(RA)v[k].re, (RA)v[k].im};
       s += norm2(rv[k]);
     }
-    part = (double)s;
+    part = s;
     store_spinor<SA>(a.r + offa, a.sstride, ih, rv);
     store_spinor<SA>(a.x + offa, a.sstride, ih, xv);
   }
