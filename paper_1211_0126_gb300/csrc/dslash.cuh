@@ -40,6 +40,71 @@ __device__ __forceinline__ void project(const cx<R> v[12], cx<R> h[6]) {
   }
 }
 
+// FP16 storage: the same projection on the stored words in packed f16x2
+// arithmetic (one rounding of a sum of two stored values, below the storage
+// rounding of the LP tier), then widened: 6 packed adds and 12 conversions
+// instead of 24 conversions and 12 FP32 adds.  A word holds (re, im) with the
+// real part in the low half; i v = (-im, re) and -i v = (im, -re) are a swap
+// and a sign flip.
+__device__ __forceinline__ uint32_t h2_add(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ uint32_t h2_sub(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ uint32_t h2_mul_i(uint32_t a) { return __byte_perm(a, 0u, 0x1032) ^ 0x00008000u; }
+__device__ __forceinline__ uint32_t h2_mul_mi(uint32_t a) { return __byte_perm(a, 0u, 0x1032) ^ 0x80000000u; }
+
+template <int MU, int SG>
+__device__ __forceinline__ void project_f16(const uint32_t v[12], cx<float> h[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const uint32_t p0 = v[c], p1 = v[3 + c], p2 = v[6 + c], p3 = v[9 + c];
+    uint32_t h0, h1;
+    if constexpr (MU == 0) {
+      h0 = (SG > 0) ? h2_add(p0, h2_mul_mi(p3)) : h2_add(p0, h2_mul_i(p3));
+      h1 = (SG > 0) ? h2_add(p1, h2_mul_mi(p2)) : h2_add(p1, h2_mul_i(p2));
+    } else if constexpr (MU == 1) {
+      h0 = (SG > 0) ? h2_sub(p0, p3) : h2_add(p0, p3);
+      h1 = (SG > 0) ? h2_add(p1, p2) : h2_sub(p1, p2);
+    } else if constexpr (MU == 2) {
+      h0 = (SG > 0) ? h2_add(p0, h2_mul_mi(p2)) : h2_add(p0, h2_mul_i(p2));
+      h1 = (SG > 0) ? h2_add(p1, h2_mul_i(p3)) : h2_add(p1, h2_mul_mi(p3));
+    } else {
+      h0 = (SG > 0) ? h2_add(p0, p2) : h2_sub(p0, p2);
+      h1 = (SG > 0) ? h2_add(p1, p3) : h2_sub(p1, p3);
+    }
+    h[c] = Pack16<F16>::unpack(h0);
+    h[3 + c] = Pack16<F16>::unpack(h1);
+  }
+}
+
+// the projected half spinor of the neighbour at index n
+template <class S, int MU, int SG>
+__device__ __forceinline__ void load_projected(const typename S::schunk* __restrict__ in, int sstride, int n,
+                                               cx<typename S::real> h[6]) {
+  if constexpr (S::id == F16::id) {
+    uint32_t v[12];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const uint4 u = in[j * sstride + n];
+      v[4 * j] = u.x;
+      v[4 * j + 1] = u.y;
+      v[4 * j + 2] = u.z;
+      v[4 * j + 3] = u.w;
+    }
+    project_f16<MU, SG>(v, h);
+  } else {
+    cx<typename S::real> v[12];
+    load_spinor<S>(in, sstride, n, v);
+    project<MU, SG>(v, h);
+  }
+}
+
 // acc += (1 + s gamma_mu)-reconstruction of the link-multiplied half spinor u
 template <int MU, int SG, class R>
 __device__ __forceinline__ void accumulate(cx<R> acc[12], const cx<R> u[6]) {
@@ -95,7 +160,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, int ih, const int c[4],
   using R = typename S::real;
   constexpr int SF = DAG ? +1 : -1;   // forward hop: (1 + SF gamma_mu)
   constexpr int SB = -SF;             // backward hop
-  cx<R> v[12], h[6], u[6], r[9];
+  cx<R> h[6], u[6], r[9];
   // forward neighbour x + mu
   {
     int x = c[0], y = c[1], z = c[2], t = c[3];
@@ -104,8 +169,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, int ih, const int c[4],
     if constexpr (MU == 2) z = (z + 1 == g.L[2]) ? 0 : z + 1;
     if constexpr (MU == 3) t = (t + 1 == g.L[3]) ? 0 : t + 1;
     const int nf = half_index(g, x, y, z, t);
-    load_spinor<S>(in, sstride, nf, v);
-    project<MU, SF>(v, h);
+    load_projected<S, MU, SF>(in, sstride, nf, h);
     if constexpr (MU == 3) {
       if (g.apbc && c[3] == g.L[3] - 1) {
 #pragma unroll
@@ -125,8 +189,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, int ih, const int c[4],
     if constexpr (MU == 2) z = (z == 0) ? g.L[2] - 1 : z - 1;
     if constexpr (MU == 3) t = (t == 0) ? g.L[3] - 1 : t - 1;
     const int nb = half_index(g, x, y, z, t);
-    load_spinor<S>(in, sstride, nb, v);
-    project<MU, SB>(v, h);
+    load_projected<S, MU, SB>(in, sstride, nb, h);
     if constexpr (MU == 3) {
       if (g.apbc && c[3] == 0) {
 #pragma unroll
