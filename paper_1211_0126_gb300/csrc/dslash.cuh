@@ -106,25 +106,28 @@ __device__ __forceinline__ void load_projected(const typename S::schunk* __restr
 }
 
 // acc += (1 + s gamma_mu)-reconstruction of the link-multiplied half spinor u
-template <int MU, int SG, class R>
+// (FIRST: acc = ..., the site's first hop, instead of adding to zeros)
+template <int MU, int SG, bool FIRST, class R>
 __device__ __forceinline__ void accumulate(cx<R> acc[12], const cx<R> u[6]) {
+  auto put = [&](int k, cx<R> v) { acc[k] = FIRST ? v : acc[k] + v; };
+  auto neg = [](cx<R> v) { return cx<R>{-v.re, -v.im}; };
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const cx<R> u0 = u[c], u1 = u[3 + c];
-    acc[c] = acc[c] + u0;
-    acc[3 + c] = acc[3 + c] + u1;
+    put(c, u0);
+    put(3 + c, u1);
     if constexpr (MU == 0) {        // lower = s i sigma_1 h = s (i h1, i h0)
-      acc[6 + c] = (SG > 0) ? acc[6 + c] + times_i(u1) : acc[6 + c] - times_i(u1);
-      acc[9 + c] = (SG > 0) ? acc[9 + c] + times_i(u0) : acc[9 + c] - times_i(u0);
+      put(6 + c, (SG > 0) ? times_i(u1) : neg(times_i(u1)));
+      put(9 + c, (SG > 0) ? times_i(u0) : neg(times_i(u0)));
     } else if constexpr (MU == 1) { // lower = s (h1, -h0)
-      acc[6 + c] = (SG > 0) ? acc[6 + c] + u1 : acc[6 + c] - u1;
-      acc[9 + c] = (SG > 0) ? acc[9 + c] - u0 : acc[9 + c] + u0;
+      put(6 + c, (SG > 0) ? u1 : neg(u1));
+      put(9 + c, (SG > 0) ? neg(u0) : u0);
     } else if constexpr (MU == 2) { // lower = s (i h0, -i h1)
-      acc[6 + c] = (SG > 0) ? acc[6 + c] + times_i(u0) : acc[6 + c] - times_i(u0);
-      acc[9 + c] = (SG > 0) ? acc[9 + c] - times_i(u1) : acc[9 + c] + times_i(u1);
+      put(6 + c, (SG > 0) ? times_i(u0) : neg(times_i(u0)));
+      put(9 + c, (SG > 0) ? neg(times_i(u1)) : times_i(u1));
     } else {                        // lower = s h
-      acc[6 + c] = (SG > 0) ? acc[6 + c] + u0 : acc[6 + c] - u0;
-      acc[9 + c] = (SG > 0) ? acc[9 + c] + u1 : acc[9 + c] - u1;
+      put(6 + c, (SG > 0) ? u0 : neg(u0));
+      put(9 + c, (SG > 0) ? u1 : neg(u1));
     }
   }
 }
@@ -179,7 +182,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, int ih, const int c[4],
     load_link<S>(Uout, lstride, MU, ih, r);
     if constexpr (!S::full_links) third_row(r, r + 6);
     su3_mul<false>(r, h, u);
-    accumulate<MU, SF>(acc, u);
+    accumulate<MU, SF, MU == 0>(acc, u);   // the site's first hop assigns
   }
   // backward neighbour x - mu
   {
@@ -199,7 +202,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, int ih, const int c[4],
     load_link<S>(Uin, lstride, MU, nb, r);
     if constexpr (!S::full_links) third_row(r, r + 6);
     su3_mul<true>(r, h, u);
-    accumulate<MU, SB>(acc, u);
+    accumulate<MU, SB, false>(acc, u);
   }
 }
 
@@ -209,9 +212,7 @@ __device__ __forceinline__ void hop_site(const Geom& g, int ih, const int c[4],
                                          const typename S::lchunk* __restrict__ Uin, int lstride,
                                          const typename S::schunk* __restrict__ in, int sstride,
                                          cx<typename S::real> acc[12]) {
-#pragma unroll
-  for (int k = 0; k < 12; ++k) acc[k] = {0, 0};
-  hop_dir<S, DAG, 0>(g, ih, c, Uout, Uin, lstride, in, sstride, acc);
+  hop_dir<S, DAG, 0>(g, ih, c, Uout, Uin, lstride, in, sstride, acc);   // assigns acc
   hop_dir<S, DAG, 1>(g, ih, c, Uout, Uin, lstride, in, sstride, acc);
   hop_dir<S, DAG, 2>(g, ih, c, Uout, Uin, lstride, in, sstride, acc);
   hop_dir<S, DAG, 3>(g, ih, c, Uout, Uin, lstride, in, sstride, acc);
@@ -249,6 +250,8 @@ struct HopArgs {
   int post;                                // PostOp for HOP_NORM
   float fac, fah;                          // ac, ah, tc, to, ts rounded on the host
   TwistF ftc, fto, fts;                    // (set by launch_hop)
+  TwistF fto_ah, fto_tc_ac;                // FP32 kernels: to * ah and to * tc * ac, formed in FP64
+                                           // on the host and rounded once (set by launch_hop)
 };
 
 constexpr int HOP_NT = 128;
@@ -274,20 +277,30 @@ __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) hop_kernel(con
     cx<R> acc[12];
     hop_site<S, DAG>(a.g, ih, c, a.Uout, a.Uin, a.lstride, a.in + off, a.sstride, acc);
     constexpr bool FP32 = sizeof(R) == 4;
-    const R ah = FP32 ? (R)a.fah : (R)a.ah;
+    if constexpr (FP32) {
+      // q = (to ah) acc + (to tc ac) center with the combined factors
+      apply_twist(a.fto_ah, acc);
+      if constexpr (MODE & HOP_CENTER) {
+        cx<R> v[12];
+        load_spinor<S>(a.center + off, a.sstride, ih, v);
+        apply_twist(a.fto_tc_ac, v);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = ah * acc[k];
-    if constexpr (MODE & HOP_CENTER) {
-      cx<R> v[12];
-      load_spinor<S>(a.center + off, a.sstride, ih, v);
-      if constexpr (FP32) apply_twist(a.ftc, v);
-      else apply_twist(a.tc, v);
-      const R ac = FP32 ? (R)a.fac : (R)a.ac;
+        for (int k = 0; k < 12; ++k) acc[k] = acc[k] + v[k];
+      }
+    } else {
+      const R ah = (R)a.ah;
 #pragma unroll
-      for (int k = 0; k < 12; ++k) acc[k] = acc[k] + ac * v[k];
+      for (int k = 0; k < 12; ++k) acc[k] = ah * acc[k];
+      if constexpr (MODE & HOP_CENTER) {
+        cx<R> v[12];
+        load_spinor<S>(a.center + off, a.sstride, ih, v);
+        apply_twist(a.tc, v);
+        const R ac = (R)a.ac;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = acc[k] + ac * v[k];
+      }
+      apply_twist(a.to, acc);
     }
-    if constexpr (FP32) apply_twist(a.fto, acc);
-    else apply_twist(a.to, acc);
     if constexpr (MODE & HOP_BASE) {
       cx<R> v[12];
       load_spinor<S>(a.base + off, a.sstride, ih, v);

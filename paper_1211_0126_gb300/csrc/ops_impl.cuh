@@ -53,6 +53,17 @@ int launch_hop(Ctx& c, const HopArgs<S>& a0, int dag, int mode, int prof_kind, i
   a.ftc = to_float(a.tc);
   a.fto = to_float(a.to);
   a.fts = to_float(a.ts);
+  {
+    Twist toah, totc;
+    for (int q = 0; q < 2; ++q) {
+      toah.re[q] = a.to.re[q] * a.ah;
+      toah.im[q] = a.to.im[q] * a.ah;
+      totc.re[q] = (a.to.re[q] * a.tc.re[q] - a.to.im[q] * a.tc.im[q]) * a.ac;
+      totc.im[q] = (a.to.re[q] * a.tc.im[q] + a.to.im[q] * a.tc.re[q]) * a.ac;
+    }
+    a.fto_ah = to_float(toah);
+    a.fto_tc_ac = to_float(totc);
+  }
   const int kind = prof_kind >= 0 ? prof_kind : hop_kind_of<S>(dag, mode);
   const double sb = spinor_site_bytes(S::id), lb = link_site_bytes(S::id);
   // links once per launch (shared by the right-hand sides), spinor streams per RHS
