@@ -59,12 +59,14 @@ def parse():
     ap.add_argument("--mode", default="eager", choices=["eager", "graph"],
                     help="eager: host-driven chunked CG loops; graph: one captured CUDA graph per step "
                          "(device-side loops, LP set beside the HP set)")
-    ap.add_argument("--workload", default="tsm24", choices=["tsm24", "three-lattice", "learned", "scale"],
+    ap.add_argument("--workload", default="tsm24",
+                    choices=["tsm24", "three-lattice", "learned", "scale", "estimators"],
                     help="tsm24: the headline 24^3x48 TSM step; three-lattice: 8^3x16 + 12^3x24 + 16^3x32 "
                          "in one captured graph (batching workload, its own JSON line); learned: the learned "
                          "LP preconditioner at 16^3x32 (training + held-out evaluation, its own JSON line); "
                          "scale: the full TSM at 32^3x64 with local and one-derivative insertions (its own "
-                         "JSON line)")
+                         "JSON line); estimators: the 24^3x48 step with each estimator (standard, one-end, "
+                         "generalised one-end, derivative insertions, all momenta by FFT) and its kernels")
     ap.add_argument("--train-steps", type=int, default=400, help="learned workload: Adam steps")
     ap.add_argument("--pairs-per-field", type=int, default=500, help="learned workload: pairs per training field")
     ap.add_argument("--net-only", action="store_true",
@@ -422,8 +424,8 @@ def run_ours(args):
     # each hop; source-sites recovered from the byte count of each kernel kind
     # (links once per launch + spinor streams per source, as accounted in the library)
     vh = int(np.prod(DIMS)) // 2
-    lb, sb, sa = 8 * 12 * 2.0, 24 * 2.0, 24 * 4.0
-    streams = {0: 2 * sb, 1: 3 * sb, 2: 2 * sb, 3: 3 * sb + 4 * sa}
+    lb, sb = 8 * 12 * 2.0, 24 * 2.0
+    streams = {0: 2 * sb, 1: 3 * sb, 2: 2 * sb, 3: 3 * sb + 4 * sb}   # the FP16 tier keeps r and x in FP16
     site_rhs = sum((prof_bytes[12 + k] / vh - prof_cnt[12 + k] * lb) / streams[k] * vh for k in range(4))
     alu_tflops = 1320.0 * site_rhs / (tot_ms * 1e-3) / 1e12 if tot_ms > 0 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -774,6 +776,94 @@ def run_scale(args):
     ctx.close()
 
 
+def run_estimators(args):
+    """Every estimator of the path on the 24^3x48 workload (the same 8 HP + 256
+    LP solves, 16 Gamma x 7 momenta): the standard one, the one-end trick
+    (Eq. 2.5), the generalised one-end trick (Eq. 2.6, one Wilson application
+    per solution), the one-derivative insertions along all four directions,
+    and all spatial momenta through the batched 3-D FFT.  Per estimator: the
+    step time (CUDA events, L2 flushed between steps) and, from one
+    instrumented step, the estimator's own kernels (contraction passes,
+    derivative passes, FFT projection, Wilson application) with their
+    algorithmic bytes against the measured HBM peak."""
+    import torch
+    from paper_1211_0126_gb300 import build, tsm
+    from paper_1211_0126_gb300 import synthetic as S
+    if not os.path.exists(tsm.LIB_PATH):
+        build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_kind = measured_peaks()
+    U = S.gauge_field(DIMS, EPS, GAUGE_SEED)
+    ctx = tsm.Context(0, stream.cuda_stream)
+    ctx.load_gauge(U, DIMS, KAPPA, MU)
+    gam, moms = list(range(N_GAMMA)), S.default_momenta(N_Q)
+    hp_stop = tsm.stop(HP_TOL, HP_MAXIT, tsm.TSM_F32, reliable=True, reliable_delta=RELIABLE_DELTA)
+    lp_stop = tsm.stop(LP_TOL, LP_MAXIT, tsm.TSM_F16)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+    variants = [("standard", {}), ("one_end", {"estimator": 1}), ("gen_one_end", {"estimator": 2}),
+                ("derivative_4_directions", {"deriv_mask": 0b1111}), ("all_momenta_fft", {"all_momenta": True})]
+    buckets = {tsm.PB_CONTRACT: "contraction", tsm.PB_DERIV: "derivative_contraction", tsm.PB_FFT: "fft_projection",
+               tsm.PB_WILSON: "wilson_application"}
+    clocks = ClockSampler(0)
+    clocks.start()
+    results = {}
+    for name, kw in variants:
+        if kw.get("all_momenta"):
+            shape, mom = (N_GAMMA, DIMS[3], DIMS[2], DIMS[1], DIMS[0]), [(0, 0, 0)]
+            pc = pl = None
+        else:
+            nblk = 1 + bin(kw.get("deriv_mask", 0)).count("1")
+            shape, mom = ((nblk,) if nblk > 1 else ()) + (N_GAMMA, N_Q, DIMS[3]), moms
+            pc = torch.zeros((N_HP,) + shape, dtype=torch.complex128, device=dev)
+            pl = torch.zeros((N_LP,) + shape, dtype=torch.complex128, device=dev)
+        d_loops = torch.zeros(shape, dtype=torch.complex128, device=dev)
+        d_err = torch.zeros(shape, dtype=torch.float64, device=dev)
+
+        def step(seed):
+            p = tsm.params(seed, 4, (0, N_HP), (N_HP, N_HP + N_LP), hp_stop, lp_stop, gam, mom, batch=args.batch,
+                           **kw)
+            return tsm.tsm_loops(ctx.h, p, d_loops, d_err, None, None, pc, pl)
+
+        for k in range(args.warmup):
+            step(100 + k)
+        times = []
+        for k in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(200 + k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        tsm.tsm_profile(ctx.h, True)
+        step(300)
+        bms, bcnt, bby = ctx.profile_read_ex()
+        tsm.tsm_profile(ctx.h, False)
+        kern = {}
+        for b, label in buckets.items():
+            if bcnt[b] > 0 and bms[b] > 0:
+                gbs = bby[b] / (bms[b] * 1e-3) / 1e9
+                kern[label] = {"calls": int(bcnt[b]), "us_per_call": 1e3 * bms[b] / bcnt[b],
+                               "algorithmic_bytes_per_call": bby[b] / bcnt[b], "algorithmic_gbs": gbs,
+                               "frac": gbs / peak}
+        ms = float(np.mean(times))
+        results[name] = {"ms_per_step": ms, "sources_per_s": (N_HP + N_LP) / (ms * 1e-3),
+                         "output_entries": int(np.prod(shape)), "kernels": kern}
+    clk = clocks.stop()
+    line = {"metric": "TSM sources/s per estimator at 24^3x48 (the same solves; estimator-specific contraction)",
+            "value": results["standard"]["sources_per_s"], "unit": "sources/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": WORKLOAD + " x {standard, one-end, generalised one-end, 4 derivative "
+                                              "directions, all momenta by FFT}",
+                       "l2": "flushed between steps (256 MB write)",
+                       "peak": {"hbm_gbs": peak, "source": peak_kind}},
+            "estimators": results, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.warmup < 3:
@@ -790,6 +880,8 @@ def main():
         run_learned(args)
     elif args.workload == "scale":
         run_scale(args)
+    elif args.workload == "estimators":
+        run_estimators(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

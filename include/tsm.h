@@ -400,6 +400,15 @@ int tsm_combine(tsm_ctx* ctx, const double* per_corr, int n_hp, const double* pe
  * tsm_launch_count returns the number of library kernels launched so far. */
 int tsm_profile(tsm_ctx* ctx, int enable);
 int tsm_profile_read(tsm_ctx* ctx, double ms[16], long long count[16], double bytes[16]);
+/* All buckets: the 16 hop buckets above, then 16 local contraction passes
+ * (kernel + fixed-order reduction, any estimator; bytes = fields read + block
+ * partials + output), 17 derivative-insertion passes (+ the direction's two
+ * links per site), 18 all-momenta FFT projections (fields, densities, one
+ * read and one write pass of the transform, running moments), 19 Wilson
+ * applications of the generalised one-end estimator (both parities).  These
+ * are timed on every launch while instrumentation is on.  n: length of the
+ * caller's arrays (entries past the library's buckets read 0; any may be NULL). */
+int tsm_profile_read_ex(tsm_ctx* ctx, int n, double* ms, long long* count, double* bytes);
 long long tsm_launch_count(tsm_ctx* ctx);
 
 /* Contraction for callers that cannot allocate device memory.

@@ -1036,10 +1036,24 @@ int tsm_profile_read(tsm_ctx* h, double ms[16], long long count[16], double byte
   Ctx& c = h->c;
   TSM_TRY(select_device(c));
   TSM_TRY(c.harvest_events());
-  for (int k = 0; k < Ctx::kProfBuckets; ++k) {
+  for (int k = 0; k < 16; ++k) {   // the hop buckets (tsm_profile_read_ex: all)
     if (ms) ms[k] = c.prof_ms[k];
     if (count) count[k] = c.prof_cnt[k];
     if (bytes) bytes[k] = c.prof_bytes[k];
+  }
+  return TSM_OK;
+}
+
+int tsm_profile_read_ex(tsm_ctx* h, int n, double* ms, long long* count, double* bytes) {
+  if (h == nullptr || n < 0) return bad(TSM_ERR_ARG, "null context or negative bucket count");
+  Ctx& c = h->c;
+  TSM_TRY(select_device(c));
+  TSM_TRY(c.harvest_events());
+  for (int k = 0; k < n; ++k) {
+    const bool in = k < Ctx::kProfBuckets;
+    if (ms) ms[k] = in ? c.prof_ms[k] : 0.0;
+    if (count) count[k] = in ? c.prof_cnt[k] : 0;
+    if (bytes) bytes[k] = in ? c.prof_bytes[k] : 0.0;
   }
   return TSM_OK;
 }

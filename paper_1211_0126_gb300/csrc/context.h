@@ -46,6 +46,11 @@ struct EOField {
 };
 
 enum HopKind { PK_HOP = 0, PK_HOP_XPAY = 1, PK_HOP_DAG = 2, PK_HOP_UPDATE = 3 };
+// profile buckets after the 16 hop buckets: local contraction passes (kernel +
+// fixed-order reduction, every estimator), derivative-insertion passes, the
+// all-momenta FFT projection (densities, cuFFT, running moments), the Wilson
+// application of the generalised one-end estimator
+enum ProfContract { PB_CONTRACT = 16, PB_DERIV = 17, PB_FFT = 18, PB_WILSON = 19 };
 
 struct Net;
 
@@ -94,7 +99,8 @@ struct Ctx {
     double bytes;
   };
   std::vector<EvRec> ev_free, ev_pending;
-  static constexpr int kProfBuckets = 16;   // 4 storage tiers x 4 hop kinds
+  // 4 storage tiers x 4 hop kinds, then the contraction kinds (ProfContract)
+  static constexpr int kProfBuckets = 24;
   double prof_ms[kProfBuckets] = {};
   long long prof_cnt[kProfBuckets] = {};
   double prof_bytes[kProfBuckets] = {};
@@ -172,6 +178,35 @@ int dispatch_prec(int prec, F&& f) {
 // streams of the fused epilogues) -- used only for instrumentation
 double spinor_site_bytes(int prec);
 double link_site_bytes(int prec);   // 8 links x 12 reals
+
+// records the CUDA-event time of the launches it brackets when instrumentation
+// is on for this launch (c.profile && c.prof_this_launch); bytes = algorithmic bytes
+struct TimedLaunch {
+  Ctx& c;
+  Ctx::EvRec rec{};
+  bool on = false;
+  // any_launch: time it whenever instrumentation is on (contraction buckets)
+  TimedLaunch(Ctx& cc, int kind, double bytes, bool any_launch = false) : c(cc) {
+    if (!c.profile || !(c.prof_this_launch || any_launch)) return;
+    if (c.ev_free.empty()) {
+      Ctx::EvRec r{};
+      if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
+      c.ev_free.push_back(r);
+    }
+    rec = c.ev_free.back();
+    c.ev_free.pop_back();
+    rec.kind = kind;
+    rec.bytes = bytes;
+    on = (cudaEventRecord(rec.a, c.stream) == cudaSuccess);
+    if (!on) c.ev_free.push_back(rec);
+  }
+  void done() {
+    if (!on) return;
+    if (cudaEventRecord(rec.b, c.stream) == cudaSuccess) c.ev_pending.push_back(rec);
+    else c.ev_free.push_back(rec);
+    on = false;
+  }
+};
 
 int check_launch(Ctx& c, const char* what);
 

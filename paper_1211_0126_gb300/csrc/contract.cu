@@ -150,10 +150,16 @@ int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint3
   const int nbx = (vs2 + NT - 1) / NT;
   const size_t block = (size_t)plan.ng * plan.n_q * T;   // one [n_gamma][n_q][T] output block
   // one kernel + fixed-order reduction per chunk of at most CT_MAXQ momenta
-  auto passes = [&](double2* dst, auto&& launch) -> int {
+  // algorithmic bytes per site of a pass: the fields it reads (noise is regenerated)
+  const double sa = spinor_site_bytes(SA::id), sbb = spinor_site_bytes(SB::id);
+  const double fields = sa + (b ? sbb : 0.0) + (wa ? sa : 0.0) + (wb ? sbb : 0.0);
+  auto passes = [&](double2* dst, int kind, double site_bytes, auto&& launch) -> int {
     for (int q0 = 0; q0 < plan.n_q; q0 += CT_MAXQ) {
       const int nq = std::min(CT_MAXQ, plan.n_q - q0);
       const int nout = plan.ng * nq;
+      // + block partials written and read back, + the output block
+      TimedLaunch tl(c, kind,
+                     (double)c.g.V * site_bytes + (double)T * 2 * nbx * nout * 32.0 + (double)nout * T * 16.0, true);
       void* part = nullptr;
       TSM_TRY(c.buffer("contract_partial", (size_t)T * 2 * nbx * CT_MAXG * CT_MAXQ * sizeof(double2), &part));
       ContractArgs<SA, SB> args{};
@@ -192,12 +198,13 @@ int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint3
                                                             plan.n_q, q0, dst);
       c.launches++;
       TSM_TRY(check_launch(c, "contract_reduce_kernel"));
+      tl.done();
     }
     return TSM_OK;
   };
   double2* dst = out;
   if (plan.local) {
-    TSM_TRY(passes(dst, [&](const ContractArgs<SA, SB>& args, dim3 grid) {
+    TSM_TRY(passes(dst, PB_CONTRACT, fields, [&](const ContractArgs<SA, SB>& args, dim3 grid) {
       if (plan.one_end == CT_ONE_END) contract_kernel<R, SA, SB, CT_ONE_END><<<grid, NT, 0, c.stream>>>(args);
       else if (plan.one_end == CT_GEN_ONE_END)
         contract_kernel<R, SA, SB, CT_GEN_ONE_END><<<grid, NT, 0, c.stream>>>(args);
@@ -208,7 +215,9 @@ int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint3
   using LS = typename DerivLinks<R>::type;
   for (int mu = 0; mu < 4; ++mu) {
     if (!((plan.deriv_mask >> mu) & 1)) continue;
-    TSM_TRY(passes(dst, [&](const ContractArgs<SA, SB>& args, dim3 grid) {
+    // the direction's forward and backward link of every site on top of the fields
+    TSM_TRY(passes(dst, PB_DERIV, fields + link_site_bytes(LS::id) / 4.0, [&](const ContractArgs<SA, SB>& args,
+                                                                             dim3 grid) {
       DerivArgs<SA, SB, LS> d{};
       d.base = args;
       d.U[0] = c.links_of<LS>(0);
@@ -238,6 +247,8 @@ template int launch_contract<float, F32, F64>(Ctx&, const ContractPlan&, const N
 int apply_wilson(Ctx& c, int prec, EOField in, EOField out) {
   return dispatch_prec(prec, [&](auto tag) -> int {
     using S = decltype(tag);
+    // both parities: links, neighbour field, centre field, output
+    TimedLaunch tl(c, PB_WILSON, (double)c.g.V * (link_site_bytes(S::id) + 3.0 * spinor_site_bytes(S::id)), true);
     for (int par = 0; par < 2; ++par) {
       HopArgs<S> h{};
       h.g = c.g;
@@ -258,6 +269,7 @@ int apply_wilson(Ctx& c, int prec, EOField in, EOField out) {
       h.post = POST_NONE;
       TSM_TRY(launch_hop<S>(c, h, 0, HOP_CENTER, -1));
     }
+    tl.done();
     return (int)TSM_OK;
   });
 }

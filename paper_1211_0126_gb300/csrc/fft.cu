@@ -181,11 +181,21 @@ int FftProjector::transform(Ctx& c, const GammaTab& gam, const NoiseSpec& ns, ui
 template <class R, class SA, class SB>
 int FftProjector::accumulate(Ctx& c, const GammaTab& gam, const NoiseSpec& ns, uint32_t source, EOField a,
                              const EOField* b, int set, int k) {
+  // algorithmic bytes: the fields read, the densities written, one read and
+  // one write pass of the transform, the densities read and the running
+  // mean (16 B) and sum of squares (8 B) read and written per entry
+  const double csz = sizeof(cx<R>);
+  TimedLaunch tl(c, PB_FFT,
+                 (double)c.g.V * (spinor_site_bytes(SA::id) + (b ? spinor_site_bytes(SB::id) : 0.0)) +
+                     (double)E * (csz + 2.0 * csz + csz + 2.0 * 24.0),
+                 true);
   TSM_TRY((transform<R, SA, SB>(c, gam, ns, source, a, b)));
   welford_kernel<R><<<(unsigned)((E + 255) / 256), 256, 0, c.stream>>>(static_cast<const cx<R>*>(dens), k, mean[set],
                                                                        m2[set], E);
   c.launches++;
-  return check_launch(c, "welford_kernel");
+  TSM_TRY(check_launch(c, "welford_kernel"));
+  tl.done();
+  return TSM_OK;
 }
 
 int FftProjector::finalize(Ctx& c, int n_hp, int n_lp, double2* est, double* err, double2* lp_mean,

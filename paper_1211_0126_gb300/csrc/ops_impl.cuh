@@ -16,32 +16,6 @@ static int hop_kind_of(int dag, int mode) {
   return (mode & HOP_CENTER) ? PK_HOP_XPAY : PK_HOP;
 }
 
-// record a timed launch when instrumentation is on for this launch
-struct TimedLaunch {
-  Ctx& c;
-  Ctx::EvRec rec{};
-  bool on = false;
-  TimedLaunch(Ctx& cc, int kind, double bytes) : c(cc) {
-    if (!c.profile || !c.prof_this_launch) return;
-    if (c.ev_free.empty()) {
-      Ctx::EvRec r{};
-      if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
-      c.ev_free.push_back(r);
-    }
-    rec = c.ev_free.back();
-    c.ev_free.pop_back();
-    rec.kind = kind;
-    rec.bytes = bytes;
-    on = (cudaEventRecord(rec.a, c.stream) == cudaSuccess);
-    if (!on) c.ev_free.push_back(rec);
-  }
-  void done() {
-    if (!on) return;
-    if (cudaEventRecord(rec.b, c.stream) == cudaSuccess) c.ev_pending.push_back(rec);
-    else c.ev_free.push_back(rec);
-    on = false;
-  }
-};
 
 template <class S>
 int launch_hop(Ctx& c, const HopArgs<S>& a0, int dag, int mode, int prof_kind, int nrhs) {

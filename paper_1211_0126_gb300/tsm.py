@@ -104,6 +104,7 @@ _SIGS = {
     "tsm_set_precond": (ctypes.c_int, [_P, _P]),
     "tsm_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "tsm_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
+    "tsm_profile_read_ex": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "tsm_launch_count": (ctypes.c_longlong, [_P]),
     "tsm_last_error": (ctypes.c_char_p, []),
     "tsm_status_str": (ctypes.c_char_p, [ctypes.c_int]),
@@ -510,6 +511,19 @@ def tsm_profile_read(h):
     return ms, cnt, by
 
 
+# profile buckets after the 16 hop buckets (tsm_profile_read_ex)
+PB_CONTRACT, PB_DERIV, PB_FFT, PB_WILSON = 16, 17, 18, 19
+
+
+def tsm_profile_read_ex(h, n=24):
+    ms = np.zeros(n)
+    cnt = np.zeros(n, dtype=np.int64)
+    by = np.zeros(n)
+    _check(library().tsm_profile_read_ex(h, int(n), ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(cnt.ctypes.data),
+                                         ctypes.c_void_p(by.ctypes.data)), "tsm_profile_read_ex")
+    return ms, cnt, by
+
+
 def tsm_launch_count(h):
     return int(library().tsm_launch_count(h))
 
@@ -655,6 +669,9 @@ class Context:
 
     def profile_read(self):
         return tsm_profile_read(self.h)
+
+    def profile_read_ex(self, n=24):
+        return tsm_profile_read_ex(self.h, n)
 
     def launch_count(self):
         return tsm_launch_count(self.h)
