@@ -501,7 +501,7 @@ int tsm_load_gauge(tsm_ctx* h, const tm_lattice* lat, const double* U, int on_de
     TSM_CUDA(cudaMalloc(&c.links[TSM_BF16], 2 * 4 * BF16::LN * vh * sizeof(uint2)));
     TSM_CUDA(cudaMalloc(&c.links[TSM_F16], 2 * 4 * F16::LN * vh * sizeof(uint2)));
     if (c.red.partials) cudaFree(c.red.partials);
-    c.red_cap = vh / 64 + 64;
+    c.red_cap = vh / 32 + 64;   // block partials: up to one per 32 sites (link-sharing stencil)
     c.red.stride = (int)c.red_cap;
     TSM_CUDA(cudaMalloc(&c.red.partials, Ctx::kMaxBatch * c.red_cap * sizeof(double)));
     c.batch_cap = 1;

@@ -153,13 +153,11 @@ __device__ __forceinline__ void su3_mul(const cx<R> r[9], const cx<R> h[6], cx<R
 }
 
 // One direction of the stencil at output site (c, ih) of parity p.
-// Uout: links of the output parity, Uin: links of the input parity.
-template <class S, int DAG, int MU>
-__device__ __forceinline__ void hop_dir(const Geom& g, int ih, const int c[4],
-                                        const typename S::lchunk* __restrict__ Uout,
-                                        const typename S::lchunk* __restrict__ Uin, int lstride,
-                                        const typename S::schunk* __restrict__ in, int sstride,
-                                        cx<typename S::real> acc[12]) {
+// links(h, nb, r) fills r[0..8] with the three rows of the link of hop h
+// (2 MU forward at x, 2 MU + 1 backward at x - mu, neighbour index nb).
+template <class S, int DAG, int MU, class Links>
+__device__ __forceinline__ void hop_dir(const Geom& g, const int c[4], const typename S::schunk* __restrict__ in,
+                                        int sstride, Links&& links, cx<typename S::real> acc[12]) {
   using R = typename S::real;
   constexpr int SF = DAG ? +1 : -1;   // forward hop: (1 + SF gamma_mu)
   constexpr int SB = -SF;             // backward hop
@@ -179,8 +177,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, int ih, const int c[4],
         for (int k = 0; k < 6; ++k) h[k] = (R)(-1) * h[k];
       }
     }
-    load_link<S>(Uout, lstride, MU, ih, r);
-    if constexpr (!S::full_links) third_row(r, r + 6);
+    links(2 * MU, -1, r);
     su3_mul<false>(r, h, u);
     accumulate<MU, SF, MU == 0>(acc, u);   // the site's first hop assigns
   }
@@ -199,11 +196,32 @@ __device__ __forceinline__ void hop_dir(const Geom& g, int ih, const int c[4],
         for (int k = 0; k < 6; ++k) h[k] = (R)(-1) * h[k];
       }
     }
-    load_link<S>(Uin, lstride, MU, nb, r);
-    if constexpr (!S::full_links) third_row(r, r + 6);
+    links(2 * MU + 1, nb, r);
     su3_mul<true>(r, h, u);
     accumulate<MU, SB, false>(acc, u);
   }
+}
+
+// the link of hop h from global memory: 2 MU forward at the output site ih
+// (links of the output parity), 2 MU + 1 backward at the neighbour nb
+template <class S>
+struct GlobalLinks {
+  const typename S::lchunk* __restrict__ Uout;
+  const typename S::lchunk* __restrict__ Uin;
+  int lstride, ih;
+  __device__ __forceinline__ void operator()(int h, int nb, cx<typename S::real> r[9]) const {
+    load_link<S>((h & 1) ? Uin : Uout, lstride, h >> 1, (h & 1) ? nb : ih, r);
+    if constexpr (!S::full_links) third_row(r, r + 6);
+  }
+};
+
+template <class S, int DAG, class Links>
+__device__ __forceinline__ void hop_site_with(const Geom& g, const int c[4], const typename S::schunk* __restrict__ in,
+                                              int sstride, Links&& links, cx<typename S::real> acc[12]) {
+  hop_dir<S, DAG, 0>(g, c, in, sstride, links, acc);   // assigns acc
+  hop_dir<S, DAG, 1>(g, c, in, sstride, links, acc);
+  hop_dir<S, DAG, 2>(g, c, in, sstride, links, acc);
+  hop_dir<S, DAG, 3>(g, c, in, sstride, links, acc);
 }
 
 template <class S, int DAG>
@@ -212,10 +230,7 @@ __device__ __forceinline__ void hop_site(const Geom& g, int ih, const int c[4],
                                          const typename S::lchunk* __restrict__ Uin, int lstride,
                                          const typename S::schunk* __restrict__ in, int sstride,
                                          cx<typename S::real> acc[12]) {
-  hop_dir<S, DAG, 0>(g, ih, c, Uout, Uin, lstride, in, sstride, acc);   // assigns acc
-  hop_dir<S, DAG, 1>(g, ih, c, Uout, Uin, lstride, in, sstride, acc);
-  hop_dir<S, DAG, 2>(g, ih, c, Uout, Uin, lstride, in, sstride, acc);
-  hop_dir<S, DAG, 3>(g, ih, c, Uout, Uin, lstride, in, sstride, acc);
+  hop_site_with<S, DAG>(g, c, in, sstride, GlobalLinks<S>{Uout, Uin, lstride, ih}, acc);
 }
 
 // ------------------------------------------------------------- generic hop kernel
@@ -263,6 +278,56 @@ constexpr int HOP_NT = 128;
 template <class S> struct HopMinBlocks { static constexpr int value = 6; };
 template <> struct HopMinBlocks<F64> { static constexpr int value = 1; };
 
+// epilogue of one output site of one right-hand side, acc = H psi on entry:
+// out = ts q, q = base + to (ac tc center + ah acc); returns <q, q> (HOP_NORM)
+template <class S, int MODE>
+__device__ __forceinline__ typename S::real hop_epilogue(const HopArgs<S>& a, size_t off, int ih,
+                                                         cx<typename S::real> acc[12]) {
+  using R = typename S::real;
+  constexpr bool FP32 = sizeof(R) == 4;
+  R part = 0;
+  if constexpr (FP32) {
+    // q = (to ah) acc + (to tc ac) center with the combined factors
+    apply_twist(a.fto_ah, acc);
+    if constexpr (MODE & HOP_CENTER) {
+      cx<R> v[12];
+      load_spinor<S>(a.center + off, a.sstride, ih, v);
+      apply_twist(a.fto_tc_ac, v);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[k] = acc[k] + v[k];
+    }
+  } else {
+    const R ah = (R)a.ah;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = ah * acc[k];
+    if constexpr (MODE & HOP_CENTER) {
+      cx<R> v[12];
+      load_spinor<S>(a.center + off, a.sstride, ih, v);
+      apply_twist(a.tc, v);
+      const R ac = (R)a.ac;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[k] = acc[k] + ac * v[k];
+    }
+    apply_twist(a.to, acc);
+  }
+  if constexpr (MODE & HOP_BASE) {
+    cx<R> v[12];
+    load_spinor<S>(a.base + off, a.sstride, ih, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = acc[k] + v[k];
+  }
+  if constexpr (MODE & HOP_NORM) {
+    R s = 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s += norm2(acc[k]);
+    part = s;
+  }
+  if constexpr (FP32) apply_twist(a.fts, acc);
+  else apply_twist(a.ts, acc);
+  store_spinor<S>(a.out + off, a.sstride, ih, acc);
+  return part;
+}
+
 template <class S, int DAG, int MODE>
 __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) hop_kernel(const HopArgs<S> a) {
   using R = typename S::real;
@@ -276,46 +341,7 @@ __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) hop_kernel(con
     site_coords(a.g, a.p_out, ih, c);
     cx<R> acc[12];
     hop_site<S, DAG>(a.g, ih, c, a.Uout, a.Uin, a.lstride, a.in + off, a.sstride, acc);
-    constexpr bool FP32 = sizeof(R) == 4;
-    if constexpr (FP32) {
-      // q = (to ah) acc + (to tc ac) center with the combined factors
-      apply_twist(a.fto_ah, acc);
-      if constexpr (MODE & HOP_CENTER) {
-        cx<R> v[12];
-        load_spinor<S>(a.center + off, a.sstride, ih, v);
-        apply_twist(a.fto_tc_ac, v);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) acc[k] = acc[k] + v[k];
-      }
-    } else {
-      const R ah = (R)a.ah;
-#pragma unroll
-      for (int k = 0; k < 12; ++k) acc[k] = ah * acc[k];
-      if constexpr (MODE & HOP_CENTER) {
-        cx<R> v[12];
-        load_spinor<S>(a.center + off, a.sstride, ih, v);
-        apply_twist(a.tc, v);
-        const R ac = (R)a.ac;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) acc[k] = acc[k] + ac * v[k];
-      }
-      apply_twist(a.to, acc);
-    }
-    if constexpr (MODE & HOP_BASE) {
-      cx<R> v[12];
-      load_spinor<S>(a.base + off, a.sstride, ih, v);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) acc[k] = acc[k] + v[k];
-    }
-    if constexpr (MODE & HOP_NORM) {
-      R s = 0;
-#pragma unroll
-      for (int k = 0; k < 12; ++k) s += norm2(acc[k]);
-      part = s;
-    }
-    if constexpr (FP32) apply_twist(a.fts, acc);
-    else apply_twist(a.ts, acc);
-    store_spinor<S>(a.out + off, a.sstride, ih, acc);
+    part = hop_epilogue<S, MODE>(a, off, ih, acc);
   }
   if constexpr (MODE & HOP_NORM) {
     double total;
@@ -349,10 +375,42 @@ struct CGUpdArgs {
   RedSlot red;
 };
 
+// epilogue of one even site of one right-hand side: acc = (H^dag)_eo t on
+// entry; v = A(-mu) w - kappa^2 acc, r -= alpha v, x += alpha p; returns <r, r>
+template <class S, class SA>
+__device__ __forceinline__ typename SA::real cg_update_epilogue(const CGUpdArgs<S, SA>& a, const CGState* st,
+                                                                size_t off, size_t offa, int ih,
+                                                                cx<typename S::real> acc[12]) {
+  using R = typename S::real;
+  using RA = typename SA::real;
+  cx<R> v[12];
+  load_spinor<S>(a.w + off, a.sstride, ih, v);
+  constexpr bool FP32 = sizeof(R) == 4;
+  if constexpr (FP32) apply_twist(a.ftw, v);
+  else apply_twist(a.tw, v);
+  const R k2 = FP32 ? (R)a.fkappa2 : (R)a.kappa2;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = v[k] - k2 * acc[k];
+  const RA alpha = sizeof(RA) == 4 ? (RA)st->alpha_f : (RA)st->alpha;
+  cx<RA> rv[12], xv[12];
+  load_spinor<SA>(a.r + offa, a.sstride, ih, rv);
+  load_spinor<SA>(a.x + offa, a.sstride, ih, xv);
+  load_spinor<S>(a.p + off, a.sstride, ih, v);
+  RA s = 0;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    rv[k] = rv[k] - alpha * cx<RA>{(RA)acc[k].re, (RA)acc[k].im};
+    xv[k] = xv[k] + alpha * cx<RA>{(RA)v[k].re, (RA)v[k].im};
+    s += norm2(rv[k]);
+  }
+  store_spinor<SA>(a.r + offa, a.sstride, ih, rv);
+  store_spinor<SA>(a.x + offa, a.sstride, ih, xv);
+  return s;
+}
+
 template <class S, class SA>
 __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) cg_update_kernel(const CGUpdArgs<S, SA> a) {
   using R = typename S::real;
-  using RA = typename SA::real;
   const int rhs = rhs_slot(a.active);
   CGState* st = a.st + rhs;
   if (st->done) return;
@@ -362,33 +420,159 @@ __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) cg_update_kern
   if (ih < a.g.Vh) {
     int c[4];
     site_coords(a.g, 0, ih, c);
-    cx<R> acc[12], v[12];
+    cx<R> acc[12];
     hop_site<S, 1>(a.g, ih, c, a.Ue, a.Uo, a.lstride, a.t + off, a.sstride, acc);
-    load_spinor<S>(a.w + off, a.sstride, ih, v);
-    constexpr bool FP32 = sizeof(R) == 4;
-    if constexpr (FP32) apply_twist(a.ftw, v);
-    else apply_twist(a.tw, v);
-    const R k2 = FP32 ? (R)a.fkappa2 : (R)a.kappa2;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = v[k] - k2 * acc[k];
-    const RA alpha = sizeof(RA) == 4 ? (RA)st->alpha_f : (RA)st->alpha;
-    cx<RA> rv[12], xv[12];
-    load_spinor<SA>(a.r + offa, a.sstride, ih, rv);
-    load_spinor<SA>(a.x + offa, a.sstride, ih, xv);
-    load_spinor<S>(a.p + off, a.sstride, ih, v);
-    RA s = 0;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      rv[k] = rv[k] - alpha * cx<RA>{(RA)acc[k].re, (RA)acc[k].im};
-      xv[k] = xv[k] + alpha * cx<RA>{(RA)v[k].re, (RA)v[k].im};
-      s += norm2(rv[k]);
-    }
-    part = s;
-    store_spinor<SA>(a.r + offa, a.sstride, ih, rv);
-    store_spinor<SA>(a.x + offa, a.sstride, ih, xv);
+    part = cg_update_epilogue<S, SA>(a, st, off, offa, ih, acc);
   }
   double total;
   if (grid_sum<HOP_NT>(part, a.red, rhs, &total) && threadIdx.x == 0) post_action(st, POST_RR, total);
+}
+
+// ------------------------------------------------------------- link-sharing stencil
+// The FP16 tier's hop kernels (K1-K3 of its CG): blocks of LT_SITES
+// consecutive output sites x up to LT_RHS right-hand sides (threadIdx.x =
+// site, threadIdx.y = right-hand side of the block, one warp each).  The
+// block's 8 x LT_SITES links are read, widened to FP32 and completed with row
+// 2 once, kept in shared memory, and read from there by every right-hand side
+// of the block: 5 shared loads per link and source instead of 3 global loads,
+// 12 conversions and the 24-FMA row rebuild.  Per-link and per-site
+// arithmetic does not depend on how many right-hand sides share a block, nor
+// do the reductions (a warp per right-hand side and block, then a fixed
+// virtual-lane order over the blocks), so batched and single-source results
+// agree bit for bit.
+constexpr int LT_SITES = 32;
+constexpr int LT_RHS = 4;
+
+struct LinkTile {
+  float4 v[8][5][LT_SITES];   // [hop 2 mu + backward][pair of complex][site]: rows 0..2, then a zero
+};
+
+template <class S>
+__device__ __forceinline__ void stage_link(const typename S::lchunk* __restrict__ U, int lstride, int dir, int site,
+                                           float4* dst) {
+  cx<float> r[9];
+  load_link<S>(U, lstride, dir, site, r);
+  if constexpr (!S::full_links) third_row(r, r + 6);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) dst[k * LT_SITES] = make_float4(r[2 * k].re, r[2 * k].im, r[2 * k + 1].re, r[2 * k + 1].im);
+  dst[4 * LT_SITES] = make_float4(r[8].re, r[8].im, 0.f, 0.f);
+}
+
+__device__ __forceinline__ int backward_index(const Geom& g, const int c[4], int mu) {
+  int x = c[0], y = c[1], z = c[2], t = c[3];
+  if (mu == 0) x = (x == 0) ? g.L[0] - 1 : x - 1;
+  else if (mu == 1) y = (y == 0) ? g.L[1] - 1 : y - 1;
+  else if (mu == 2) z = (z == 0) ? g.L[2] - 1 : z - 1;
+  else t = (t == 0) ? g.L[3] - 1 : t - 1;
+  return half_index(g, x, y, z, t);
+}
+
+// the block's links: thread (site, w) stages directions w, w + blockDim.y, ...
+template <class S>
+__device__ __forceinline__ void stage_tile(const Geom& g, int ih, const int c[4],
+                                           const typename S::lchunk* __restrict__ Uout,
+                                           const typename S::lchunk* __restrict__ Uin, int lstride, LinkTile& T) {
+  if (ih >= g.Vh) return;
+  const int s = threadIdx.x;
+  for (int mu = threadIdx.y; mu < 4; mu += blockDim.y) {
+    stage_link<S>(Uout, lstride, mu, ih, &T.v[2 * mu][0][s]);
+    stage_link<S>(Uin, lstride, mu, backward_index(g, c, mu), &T.v[2 * mu + 1][0][s]);
+  }
+}
+
+struct TileLinks {
+  const LinkTile& t;
+  int s;
+  __device__ __forceinline__ void operator()(int h, int, cx<float> r[9]) const {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const float4 q = t.v[h][k][s];
+      r[2 * k] = {q.x, q.y};
+      if (k < 4) r[2 * k + 1] = {q.z, q.w};
+    }
+  }
+};
+
+// per-right-hand-side sums of a link-sharing launch (grid.y = site blocks):
+// the block partial of a right-hand side is its warp's sum; the last block of
+// a right-hand side adds the partials over LT_VLANES virtual lanes (virtual
+// lane v: blocks v, v + LT_VLANES, ... in order), then the virtual lanes'
+// sums in a fixed tree.  The threads of the block share the virtual lanes
+// out, so the order is the same whatever the block's width.
+constexpr int LT_VLANES = 128;
+
+__device__ __forceinline__ void tile_grid_sum(float part, int rhs, RedSlot slot, CGState* st, int post) {
+  __shared__ int last_rhs[LT_RHS];
+  __shared__ double vsum[LT_VLANES];
+  const int w = threadIdx.y, lane = threadIdx.x, nthr = LT_SITES * blockDim.y, tid = w * LT_SITES + lane;
+  float v = part;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) {
+    int last = -1;
+    if (rhs >= 0) {
+      slot.partials[(size_t)rhs * slot.stride + blockIdx.y] = (double)v;
+      __threadfence();
+      const unsigned int ticket = atomicAdd(slot.counter + rhs, 1u);
+      if (ticket == gridDim.y - 1) last = rhs;
+    }
+    last_rhs[w] = last;
+  }
+  __syncthreads();
+  for (int j = 0; j < (int)blockDim.y; ++j) {
+    const int r = last_rhs[j];   // the same in every thread
+    if (r < 0) continue;
+    __threadfence();
+    const double* partials = slot.partials + (size_t)r * slot.stride;
+    for (int vl = tid; vl < LT_VLANES; vl += nthr) {
+      double acc = 0.0;
+      for (int b = vl; b < (int)gridDim.y; b += LT_VLANES) acc += __ldcg(partials + b);
+      vsum[vl] = acc;
+    }
+    __syncthreads();
+    if (w == 0) {
+      double acc = 0.0;
+#pragma unroll
+      for (int q = 0; q < LT_VLANES / 32; ++q) acc += vsum[lane + 32 * q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) {
+        if (st != nullptr) post_action(st + r, post, acc);
+        slot.counter[r] = 0u;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// right-hand side of thread (site, w) from the launch's list, -1 past it
+__device__ __forceinline__ int tile_rhs(const int* active, int nrhs) {
+  const int k = blockIdx.x * blockDim.y + threadIdx.y;
+  if (k >= nrhs) return -1;
+  return active != nullptr ? active[k] : k;
+}
+
+template <class S, int DAG, int MODE>
+__global__ void __launch_bounds__(LT_SITES * LT_RHS, HopMinBlocks<S>::value) hop_tile_kernel(const HopArgs<S> a,
+                                                                                           int nrhs) {
+  __shared__ LinkTile tile;
+  using R = typename S::real;
+  int rhs = tile_rhs(a.active, nrhs);
+  if (rhs >= 0 && a.skip != nullptr && (a.skip_rel ? !a.skip[rhs].need_rel : a.skip[rhs].done)) rhs = -1;
+  if (!__syncthreads_or(rhs >= 0)) return;   // every right-hand side of the block is idle
+  const int ih = blockIdx.y * LT_SITES + threadIdx.x;
+  int c[4] = {0, 0, 0, 0};
+  if (ih < a.g.Vh) site_coords(a.g, a.p_out, ih, c);
+  stage_tile<S>(a.g, ih, c, a.Uout, a.Uin, a.lstride, tile);
+  __syncthreads();
+  R part = 0;
+  if (rhs >= 0 && ih < a.g.Vh) {
+    const size_t off = rhs_offset<S>(rhs, a.sstride);
+    cx<R> acc[12];
+    hop_site_with<S, DAG>(a.g, c, a.in + off, a.sstride, TileLinks{tile, (int)threadIdx.x}, acc);
+    part = hop_epilogue<S, MODE>(a, off, ih, acc);
+  }
+  if constexpr (MODE & HOP_NORM) tile_grid_sum(part, rhs, a.red, a.st, a.post);
 }
 
 // p = r + beta p   (grid: x = right-hand side, y = blocks of 256 sites)

@@ -44,9 +44,17 @@ int launch_hop(Ctx& c, const HopArgs<S>& a0, int dag, int mode, int prof_kind, i
   const double bytes = (double)a.g.Vh *
       (lb + nrhs * sb * (2 + ((mode & HOP_CENTER) ? 1 : 0) + ((mode & HOP_BASE) ? 1 : 0)));
   TimedLaunch tl(c, 4 * S::id + kind, bytes);
-  const dim3 grid(nrhs, nb);
-#define TSM_HOP_CASE(D, M) \
-  if (dag == (D) && mode == (M)) hop_kernel<S, (D), (M)><<<grid, HOP_NT, 0, c.stream>>>(a);
+  // FP16 tier: link-sharing blocks of LT_SITES sites x up to LT_RHS sources;
+  // others: one thread per (source, site), blocks of HOP_NT sites
+  constexpr bool TILE = S::id == F16::id;
+  const int rpb = nrhs < LT_RHS ? nrhs : LT_RHS;
+  const dim3 grid = TILE ? dim3((nrhs + rpb - 1) / rpb, blocks_for(a.g.Vh, LT_SITES)) : dim3(nrhs, nb);
+  const dim3 block = TILE ? dim3(LT_SITES, rpb) : dim3(HOP_NT);
+#define TSM_HOP_CASE(D, M)                                                              \
+  if (dag == (D) && mode == (M)) {                                                      \
+    if constexpr (TILE) hop_tile_kernel<S, (D), (M)><<<grid, block, 0, c.stream>>>(a, nrhs); \
+    else hop_kernel<S, (D), (M)><<<grid, block, 0, c.stream>>>(a);                      \
+  }
   TSM_HOP_CASE(0, 0)
   else TSM_HOP_CASE(0, HOP_CENTER)
   else TSM_HOP_CASE(0, HOP_CENTER | HOP_NORM)
@@ -74,6 +82,8 @@ int launch_cg_update(Ctx& c, const CGUpdArgs<S, SA>& a0, int nrhs) {
   a.ftw = to_float(a.tw);
   const double sb = spinor_site_bytes(S::id), lb = link_site_bytes(S::id), sa = spinor_site_bytes(SA::id);
   TimedLaunch tl(c, 4 * S::id + PK_HOP_UPDATE, (double)a.g.Vh * (lb + nrhs * (3 * sb + 4 * sa)));
+  // one thread per (source, site) for every tier: the update is memory-bound,
+  // and link sharing measured slower here (534 against 511 us per launch)
   cg_update_kernel<S, SA><<<dim3(nrhs, nb), HOP_NT, 0, c.stream>>>(a);
   tl.done();
   c.launches++;
