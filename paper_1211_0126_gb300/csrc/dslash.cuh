@@ -263,10 +263,8 @@ struct HopArgs {
   CGState* st;                             // states receiving the HOP_NORM post action
   RedSlot red;                             // HOP_NORM
   int post;                                // PostOp for HOP_NORM
-  float fac, fah;                          // ac, ah, tc, to, ts rounded on the host
-  TwistF ftc, fto, fts;                    // (set by launch_hop)
-  TwistF fto_ah, fto_tc_ac;                // FP32 kernels: to * ah and to * tc * ac, formed in FP64
-                                           // on the host and rounded once (set by launch_hop)
+  TwistF fto_ah, fto_tc_ac, fts;           // FP32 kernels: to * ah, to * tc * ac and ts, formed in
+                                           // FP64 on the host and rounded once (set by launch_hop)
 };
 
 constexpr int HOP_NT = 128;

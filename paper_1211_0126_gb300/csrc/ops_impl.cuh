@@ -22,10 +22,6 @@ int launch_hop(Ctx& c, const HopArgs<S>& a0, int dag, int mode, int prof_kind, i
   const int nb = blocks_for(a0.g.Vh, HOP_NT);
   if (nb == 0 || nrhs == 0) return TSM_OK;
   HopArgs<S> a = a0;
-  a.fac = (float)a.ac;
-  a.fah = (float)a.ah;
-  a.ftc = to_float(a.tc);
-  a.fto = to_float(a.to);
   a.fts = to_float(a.ts);
   {
     Twist toah, totc;
