@@ -79,7 +79,10 @@ typedef enum {
  *   TSM_F32  FP32 storage and arithmetic; in solves optionally with FP64
  *            reliable updates (tm_stop.reliable).
  *   TSM_BF16, TSM_F16  16-bit storage of links and Krylov/operator vectors,
- *            FP32 arithmetic; residual and solution kept in FP32. */
+ *            FP32 arithmetic.  TSM_F16 keeps the CG residual and iterate in
+ *            FP16 as well (relative precision 2^-11, below the truncation of
+ *            an LP solve); TSM_BF16 keeps them in FP32.  Sources and solutions
+ *            are exchanged in FP32 for both. */
 typedef enum { TSM_F64 = 0, TSM_F32 = 1, TSM_BF16 = 2, TSM_F16 = 3 } tsm_prec;
 
 typedef struct {
@@ -145,7 +148,8 @@ int tsm_create(int device, void* cuda_stream, tsm_ctx** out);
 int tsm_destroy(tsm_ctx* ctx);
 
 /* Load the gauge field: canonical FP64 links (host or device), converted to the
- * library's even/odd two-row (12 real) storage in FP64, FP32, FP16 and BF16.
+ * library's even/odd storage: FP64 all three rows, FP32, FP16 and BF16 rows 0
+ * and 1 (12 reals; row 2 = conj(row0 x row1) is rebuilt in the stencil).
  * Checks every link for SU(3) (unitary rows, row 3 = conj(row1 x row2)) to
  * 1e-8 and returns TSM_ERR_NOT_UNITARY otherwise; extents must be even >= 2.
  * The boundary sign is applied inside the operator, never folded into links. */
