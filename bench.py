@@ -38,7 +38,7 @@ N_HP, N_LP = 8, 256
 HP_TOL, LP_TOL, LP_MAXIT, HP_MAXIT = 1e-10, 5e-3, 60, 20000
 RELIABLE_DELTA = 1e-5        # FP64 residual replacement whenever ||r|| fell by 10^5
 TIERS = {0: "f64", 1: "f32", 2: "bf16", 3: "f16"}
-FP32_PEAK = 69.1             # TFLOP/s, register-resident FFMA loop on this machine's GB300 (2 flop per FMA)
+FP32_PEAK = 69.1             # TFLOP/s, register-resident FFMA loop measured on a GB300 (2 flop per FMA)
 KINDS = ("K1_hop", "K2_hop_xpay_norm", "K3_hop_dag", "K4_hop_dag_cg_update")
 N_GAMMA, N_Q = 16, 7
 METRIC = "TSM sources/sec at 24^3x48 and Dslash HBM GB/s, vs plain FP64 at equal loop error"
@@ -437,7 +437,7 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": alg_per_launch,
                 "alu": {"flop_per_source_site": 1320, "achieved_tflops": alu_tflops, "peak_tflops": FP32_PEAK,
                         "frac": (alu_tflops / FP32_PEAK) if alu_tflops else None,
-                        "peak_source": "measured FP32 FMA loop on this pool (nominal 80.5)"},
+                        "peak_source": "measured FP32 FMA loop on a GB300 (nominal 80.5)"},
                 "kernel": "FP16 half-Dslash family K1-K4 of the LP solves (batch %d)" % args.batch,
                 "peak_source": ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                                 else "fallback 6.8 TB/s"),
