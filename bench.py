@@ -16,7 +16,8 @@ clocks seen during the timed region and the kernel-launch count.
 
 --impl reference runs the CPU oracle (the only other implementation of this
 method here) on the same workload: each step is a bounded sample (one CG
-iteration of the oracle at 24^3 x 48), scaled to sources/s.
+iteration of the oracle at 24^3 x 48 on every host core at once, one spawned
+worker process per core), scaled to sources/s and summed over the cores.
 """
 import argparse
 import hashlib
