@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) cg_update_kern
 }
 
 // ------------------------------------------------------------- link-sharing stencil
-// The FP16 tier's hop kernels (K1-K3 of its CG): blocks of LT_SITES
+// The 16-bit tiers' hop kernels (K1-K3 of their CG): blocks of LT_SITES
 // consecutive output sites x up to LT_RHS right-hand sides (threadIdx.x =
 // site, threadIdx.y = right-hand side of the block, one warp each).  The
 // block's 8 x LT_SITES links are read, widened to FP32 and completed with row

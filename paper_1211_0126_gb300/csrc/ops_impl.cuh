@@ -40,9 +40,9 @@ int launch_hop(Ctx& c, const HopArgs<S>& a0, int dag, int mode, int prof_kind, i
   const double bytes = (double)a.g.Vh *
       (lb + nrhs * sb * (2 + ((mode & HOP_CENTER) ? 1 : 0) + ((mode & HOP_BASE) ? 1 : 0)));
   TimedLaunch tl(c, 4 * S::id + kind, bytes);
-  // FP16 tier: link-sharing blocks of LT_SITES sites x up to LT_RHS sources;
-  // others: one thread per (source, site), blocks of HOP_NT sites
-  constexpr bool TILE = S::id == F16::id;
+  // 16-bit tiers: link-sharing blocks of LT_SITES sites x up to LT_RHS
+  // sources; others: one thread per (source, site), blocks of HOP_NT sites
+  constexpr bool TILE = S::id == F16::id || S::id == BF16::id;
   const int rpb = nrhs < LT_RHS ? nrhs : LT_RHS;
   const dim3 grid = TILE ? dim3((nrhs + rpb - 1) / rpb, blocks_for(a.g.Vh, LT_SITES)) : dim3(nrhs, nb);
   const dim3 block = TILE ? dim3(LT_SITES, rpb) : dim3(HOP_NT);
