@@ -39,6 +39,8 @@ N_HP, N_LP = 8, 256
 HP_TOL, LP_TOL, LP_MAXIT, HP_MAXIT = 1e-10, 5e-3, 60, 20000
 RELIABLE_DELTA = 1e-5        # FP64 residual replacement whenever ||r|| fell by 10^5
 TIERS = {0: "f64", 1: "f32", 2: "bf16", 3: "f16"}
+REAL_BYTES = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
+NAIVE_REALS = {"f64": 8 * 18 + 8 * 24 + 24, "f32": 312, "bf16": 312, "f16": 312}
 FP32_PEAK = 69.1             # TFLOP/s, register-resident FFMA loop measured on a GB300 (2 flop per FMA)
 KINDS = ("K1_hop", "K2_hop_xpay_norm", "K3_hop_dag", "K4_hop_dag_cg_update")
 N_GAMMA, N_Q = 16, 7
@@ -585,8 +587,12 @@ def dslash_gbs(ctx, S, tsm, flush, peak):
         ms, cnt, by = ctx.profile_read()
         tsm.tsm_profile(ctx.h, False)
         gbs = by.sum() / (ms.sum() * 1e-3) / 1e9
-        res[name] = {"us_per_launch": 1e3 * ms.sum() / cnt.sum(), "algorithmic_gbs": gbs, "frac": gbs / peak,
-                     "bytes_per_site": by.sum() / cnt.sum() / (np.prod(DIMS) // 2)}
+        t_launch = ms.sum() * 1e-3 / cnt.sum()
+        res[name] = {"us_per_launch": 1e6 * t_launch, "algorithmic_gbs": gbs, "frac": gbs / peak,
+                     "bytes_per_site": by.sum() / cnt.sum() / (np.prod(DIMS) // 2),
+                     # labelled "naive" count (no spinor reuse): 8 links + 8 neighbour spinors + 1
+                     # output per site, 312 reals (the FP64 tier stores 18-real links: 360)
+                     "naive_gbs": NAIVE_REALS[name] * REAL_BYTES[name] * (np.prod(DIMS) // 2) / t_launch / 1e9}
     return res
 
 
