@@ -29,8 +29,8 @@ loops   local loop contraction, exact loops from a dense inverse, TSM combine
 
 Pins: every function is checked in ``tests/test_oracle_*.py`` against things
 other than itself (closed forms, algebraic identities, dense inversion,
-exact variance formulas, statistics).  The Philox bit stream is the one
-function whose exact bits the paper does not fix; it is pinned by the
-distribution properties of Eq. (2.1) and by avalanche/collision statistics,
-not by published known-answer vectors (none are available offline).
+exact variance formulas, statistics).  The Philox bit stream, whose exact
+bits the paper does not fix, is pinned by the generator's published
+known-answer vectors (Salmon et al., SC'11, Random123 distribution) and by
+the distribution properties of Eq. (2.1).
 """

@@ -21,9 +21,11 @@ Re(eta_a) negative, bit 2a+1 set makes Im(eta_a) negative.  Z4 entries are
 (+-1 +- i)/sqrt(2) (unit modulus, as Eq. 2.1 needs); Z2 entries are +-1 from
 bit 2a alone.
 
-Parity status: the exact bit stream is pinned by distribution statistics and
-structural properties only (the published known-answer vectors are not
-available offline); the method itself needs only the moments of Eq. 2.1.
+Pins: the round function is checked against the known-answer vectors that
+Salmon et al. publish with their Random123 distribution for philox4x32-10
+(counter and key all zero, all ones, and the digits of pi); the noise map
+(seed -> key, site/source -> counter, word-0 bits -> signs) against a
+hand-decoded site; the moments of Eq. 2.1 by statistics.
 """
 import numpy as np
 
