@@ -432,12 +432,13 @@ long long tsm_launch_count(tsm_ctx* ctx);
  *            current CUDA device.
  * Scratch: a fixed 1 MiB device array compiled into the library (one per
  * device, held until the library is unloaded) stores the phase tables and the
- * block partial sums; requests that need more return TSM_ERR_TOO_LARGE.  The
- * first call on a device looks up that array's device address (once per
- * device) -- make that first call before any stream capture.  Every call
- * shares the array: calls whose work overlaps on the GPU race and must be
- * serialised by the caller.  Nothing in the array needs clearing: each call
- * writes every entry it reads. */
+ * block partial sums; requests that need more return TSM_ERR_TOO_LARGE.  Each
+ * call looks up that array's device address on the current device
+ * (cudaGetSymbolAddress, no allocation; TSM_ERR_CUDA if it fails); the first
+ * call on a device also loads the library's device code there -- make that
+ * first call before any stream capture.  Every call shares the array: calls
+ * whose work overlaps on the GPU race and must be serialised by the caller.
+ * Nothing in the array needs clearing: each call writes every entry it reads. */
 int tsm_contract_noalloc(const tm_lattice* lat, uint64_t seed, int kind, uint32_t source,
                          const double* s_dev, const int* gammas, int n_gamma, const int* moms, int n_q,
                          double* out_dev, void* cuda_stream);

@@ -16,6 +16,12 @@
 // between calls.  All calls on a device share the one array: two calls whose
 // kernels overlap on the GPU (different streams without ordering, or several
 // host threads) race on it and must be serialised by the caller.
+//
+// The host only knows the array by its symbol; its device address is looked
+// up with cudaGetSymbolAddress on every call, with the caller's device
+// current.  The lookup allocates nothing, and a fresh one per call stays
+// right after a device reset, when the module is loaded again and the array
+// may sit at another address.
 #include <mutex>
 
 #include "contract.h"
@@ -24,7 +30,6 @@ namespace tsm {
 
 // capacity of the scratch array: 1 MiB per device
 constexpr int kNoallocEntries = 65536;
-constexpr int kNoallocMaxDevices = 64;
 constexpr int kNoallocNT = 128;
 
 static __device__ __align__(256) double2 g_noalloc_scratch[kNoallocEntries];
@@ -142,7 +147,6 @@ static __global__ void noalloc_reduce_kernel(const double2* __restrict__ partial
 
 namespace {
 std::mutex g_noalloc_mutex;
-double2* g_noalloc_ptr[kNoallocMaxDevices] = {};
 // host staging of the phase tables (a fixed host array: no heap allocation)
 double2 g_noalloc_phase[CT_MAXQ * 3 * 1024];
 }  // namespace
@@ -202,19 +206,15 @@ extern "C" int tsm_contract_noalloc(const tm_lattice* lat, uint64_t seed, int ki
   if (rc != TSM_OK) return rc;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  int dev = 0;
-  TSM_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kNoallocMaxDevices) {
-    set_error("tsm_contract_noalloc: device index %d above %d", dev, kNoallocMaxDevices);
-    return TSM_ERR_ARG;
+  // device address of the scratch array on the current device (the symbol
+  // itself is a host-side stand-in that no kernel may be given)
+  void* sym = nullptr;
+  const cudaError_t se = cudaGetSymbolAddress(&sym, g_noalloc_scratch);
+  if (se != cudaSuccess || sym == nullptr) {
+    set_error("tsm_contract_noalloc: cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(se));
+    return TSM_ERR_CUDA;
   }
-  if (g_noalloc_ptr[dev] == nullptr) {
-    // set-up once per device (the device current): device address of the scratch array
-    void* p = nullptr;
-    TSM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = static_cast<double2*>(p);
-  }
-  double2* scratch = g_noalloc_ptr[dev];
+  double2* scratch = static_cast<double2*>(sym);
   const double twopi = 2.0 * std::acos(-1.0);
   int off = 0;
   for (int ax = 0; ax < 3; ++ax)

@@ -3,14 +3,21 @@
 It serves callers that cannot allocate device memory where they need a
 contraction (a foreign allocator owns the device, cudaMalloc's implicit
 synchronisation is not acceptable, or there is no library context).  The GPU
-test calls it through the C ABI twice in a row -- the second call with other
+test calls it through the C ABI three times in a row -- each call with other
 arguments, so stale scratch contents would show -- and compares each result
-with the existing tsm_contract (FP64) at the tolerance of the other FP64
-contraction tests.  The file name makes pytest collect it last.
+with the existing tsm_contract (FP64) and with the oracle's local loops at the
+tolerance of the other FP64 contraction tests.  The third call runs on a
+16x16x20x8 lattice with 16 Gammas x 13 momenta (208 outputs per timeslice):
+the scratch limit then lowers the number of blocks per timeslice to 38, so
+every block sums two chunks of sites and holds two outputs per thread, and
+the reduction adds 38 block partials.  The file name makes pytest collect it
+last.
 """
 import numpy as np
 import pytest
 
+from oracle import loops as oloops
+from oracle import philox
 from paper_1211_0126_gb300 import synthetic as S
 from paper_1211_0126_gb300 import tsm
 
@@ -36,22 +43,24 @@ def test_rejects_requests_beyond_the_scratch_limit(libtsm):
 
 
 @pytest.mark.gpu
-def test_noalloc_contraction_matches_tsm_contract_twice(ctx):
+def test_noalloc_contraction_matches_tsm_contract_and_oracle(ctx):
     import torch
-    dims = (6, 4, 4, 8)
-    lat = tsm.lattice(dims, 0.124, 0.01)
-    ctx.load_gauge(S.gauge_field(dims, 0.0, 0), dims, 0.124, 0.01)
     stream = torch.cuda.current_stream().cuda_stream
     calls = [
-        (2024, 4, 3, list(range(16)), S.default_momenta(7)),
-        (7, 2, 11, [5, 0, 12], S.default_momenta(13)),
+        ((6, 4, 4, 8), 2024, 4, 3, list(range(16)), S.default_momenta(7)),
+        ((6, 4, 4, 8), 7, 2, 11, [5, 0, 12], S.default_momenta(13)),
+        ((16, 16, 20, 8), 31, 4, 5, list(range(16)), S.default_momenta(13)),
     ]
-    for k, (seed, kind, source, gam, moms) in enumerate(calls):
+    for k, (dims, seed, kind, source, gam, moms) in enumerate(calls):
+        lat = tsm.lattice(dims, 0.124, 0.01)
+        ctx.load_gauge(S.gauge_field(dims, 0.0, 0), dims, 0.124, 0.01)
         s = S.random_spinor(dims, 100 + k)
         want = ctx.contract(seed, source, s, gam, moms, kind=kind, prec=tsm.TSM_F64)
+        ref = oloops.local_loops(philox.noise(seed, source, dims, kind), s, dims, gam, moms)
         s_dev = torch.from_numpy(s).to("cuda")
         out = torch.full((len(gam), len(moms), dims[3]), complex("nan"), dtype=torch.complex128, device="cuda")
         tsm.tsm_contract_noalloc(lat, seed, kind, source, s_dev, gam, moms, out, stream)
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         assert np.abs(got - want).max() < 1e-12 * np.abs(want).max(), k
+        assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max(), k
