@@ -211,12 +211,16 @@ int tsm_contract_gen_one_end(tsm_ctx* ctx, int prec, const double* s_a, const do
                              double* out, int on_device);
 
 /* Local loops of one canonical solution at every spatial momentum (the paper
- * Fourier-transforms with CUFFT, Sec. 3):
+ * Fourier-transforms the loops, Sec. 3):
  *   out[g][t][n_z][n_y][n_x] = sum_{x: x_4 = t} e^{+2 pi i (n_x x/Lx + n_y y/Ly + n_z z/Lz)}
  *                              eta_j(x)^dag Gamma_g (s_a - s_b)(x),  n_i in [0, L_i)
- * (momentum -n is index L - n).  Per-site densities in FP64 or FP32 (prec)
- * and one batched 3-D cuFFT transform of n_gamma * T slices.  Host or device
- * pointers per on_device; errors as tsm_contract. */
+ * (momentum -n is index L - n).  Per-site densities and the transform in FP64
+ * or FP32 (prec): the library's own mixed-radix FFT, the x and y axes of each
+ * (t, z) plane in one shared-memory pass and the z axis in a second.  Even
+ * extents whose prime factors are at most 13; TSM_ERR_TOO_LARGE otherwise or
+ * if an Lx x Ly plane of the tier's complex type does not fit in 200 KB of
+ * shared memory (FP64: Lx * Ly <= 12800).  Host or device pointers per
+ * on_device; errors as tsm_contract. */
 int tsm_contract_fft(tsm_ctx* ctx, int prec, uint64_t seed, int kind, uint32_t source,
                      const double* s_a, const double* s_b, const int* gammas, int n_gamma,
                      double* out, int on_device);
@@ -262,8 +266,9 @@ typedef struct {
                                insertion block along mu (see tsm_contract_deriv) after
                                the local block in every output and per-source array */
   int all_momenta;          /* 1 (estimator 0, no derivatives, eager only): every spatial
-                               momentum through one batched 3-D FFT per source (see
-                               tsm_contract_fft); moms / n_q are ignored, outputs are
+                               momentum through the library's 3-D FFT per source (see
+                               tsm_contract_fft; same size limit); moms / n_q are ignored,
+                               outputs are
                                [n_gamma][T][Lz][Ly][Lx], per_corr / per_lp must be NULL
                                (means and variances are accumulated in source order) */
   int hp_warm_start;        /* 1: each HP solve of tier FP32 with FP64 reliable updates starts

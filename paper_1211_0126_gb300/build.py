@@ -81,7 +81,7 @@ def build(verbose=False, force=False, ptxas_verbose=False):
         with cf.ThreadPoolExecutor(workers) as ex:
             list(ex.map(lambda j: _compile(j[0], j[1], extra, verbose or ptxas_verbose), jobs))
     if jobs or not os.path.exists(LIB):
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcufft", "-lcudart"] + _rpath()
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart"] + _rpath()
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), res.stderr))

@@ -48,7 +48,7 @@ struct EOField {
 enum HopKind { PK_HOP = 0, PK_HOP_XPAY = 1, PK_HOP_DAG = 2, PK_HOP_UPDATE = 3 };
 // profile buckets after the 16 hop buckets: local contraction passes (kernel +
 // fixed-order reduction, every estimator), derivative-insertion passes, the
-// all-momenta FFT projection (densities, cuFFT, running moments), the Wilson
+// all-momenta FFT projection (densities, the transform, running moments), the Wilson
 // application of the generalised one-end estimator
 enum ProfContract { PB_CONTRACT = 16, PB_DERIV = 17, PB_FFT = 18, PB_WILSON = 19 };
 
