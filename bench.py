@@ -15,9 +15,11 @@ ABI with host buffers, the oracle's CPU throughput on a bounded sample, the
 clocks seen during the timed region and the kernel-launch count.
 
 --impl reference runs the CPU oracle (the only other implementation of this
-method here) on the same workload: each step is a bounded sample (one CG
-iteration of the oracle at 24^3 x 48 on every host core at once, one spawned
-worker process per core), scaled to sources/s and summed over the cores.
+method here) on the same workload, on every host core at once (one spawned
+worker process per core): a warm-up step runs one complete LP source per
+worker (LP iteration count and per-source time), each further step one
+application of the Schur operator at 24^3 x 48 per worker; scaled to
+sources/s and summed over the cores.
 """
 import argparse
 import hashlib
@@ -384,6 +386,20 @@ def _oracle_lp_worker(source):
     return oracle_lp_source(_WORKER_U, source)
 
 
+def oracle_schur_apply(U):
+    """One application of the oracle's Schur operator Dhat at 24^3 x 48 (half
+    of a CG iteration, which applies Dhat and Dhat^dag); seconds."""
+    from oracle import dirac, philox
+    p = dirac.even_mask(DIMS) * philox.noise(1000, 0, DIMS, 4)
+    t0 = time.perf_counter()
+    dirac.schur(U, p, DIMS, KAPPA, MU)
+    return time.perf_counter() - t0
+
+
+def _oracle_schur_worker(_):
+    return oracle_schur_apply(_WORKER_U)
+
+
 def base_config():
     """The workload both arms run (the reference arm's line carries the same dict)."""
     return {"workload": WORKLOAD, "lattice": list(DIMS), "n_hp_per_gpu": N_HP, "n_lp_per_gpu": N_LP,
@@ -395,11 +411,12 @@ def run_reference(args):
     """The CPU oracle on the workload, on every host core at once.  Warm-up
     step 0: every worker runs one complete LP source (a different noise
     source each), which measures the LP iteration count and the time of one
-    LP source.  Every other step: every worker times one CG iteration of the
-    workload.  sources/s = 264 sources / (264 LP sources + 8 HP solves, an HP
-    solve being an LP source plus HP_ITERS_FP64_CG - LP iterations more),
-    summed over the workers; ms_per_step is the wall time of one timed step
-    (one CG iteration on every core)."""
+    LP source.  Every other step: every worker times one application of the
+    Schur operator of the workload; one CG iteration = two of them (Dhat,
+    Dhat^dag; the vector updates are a small fraction).  sources/s = 264
+    sources / (264 LP sources + 8 HP solves, an HP solve being an LP source
+    plus HP_ITERS_FP64_CG - LP iterations more), summed over the workers;
+    ms_per_step is the wall time of one timed step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -420,22 +437,27 @@ def run_reference(args):
     ncores = len(lp)
     t_lp = np.array([t for t, _ in lp])
     lp_iters = float(np.mean([it for _, it in lp]))
-    times, walls = [], []   # per timed step: every worker's iteration time, and the step's wall time
+    def one_step():
+        if pool is None:
+            return [oracle_schur_apply(U)]
+        futs = [pool.ex.submit(_oracle_schur_worker, w) for w in range(ncores)]
+        return [f.result(timeout=pool.timeout) for f in futs]
+
+    times, walls = [], []   # per timed step: every worker's Schur time, and the step's wall time
     try:
         for k in range(1, args.warmup + args.steps):
             t0 = time.perf_counter()
-            res = pool.sample(t_src_too=False) if pool is not None else [oracle_sample(U, False)]
+            res = one_step()
             if k >= args.warmup:
-                times.append([ti for ti, _ in res])
+                times.append(res)
                 walls.append(time.perf_counter() - t0)
     except Exception as e:   # a worker lost mid-run: report the steps that completed
         print("oracle step failed (%s)" % type(e).__name__, file=sys.stderr)
     if not times:
-        res = pool.sample(t_src_too=False) if pool is not None else [oracle_sample(U, False)]
-        times.append([ti for ti, _ in res])
+        times.append(one_step())
     if pool is not None:
         pool.close()
-    t_it = np.mean(np.asarray(times), axis=0)   # per worker
+    t_it = 2.0 * np.mean(np.asarray(times), axis=0)   # per worker: Dhat + Dhat^dag
     rate = []
     for w in range(ncores):
         t_hp = t_lp[w] + max(HP_ITERS_FP64_CG - lp_iters, 0.0) * t_it[w]
@@ -444,7 +466,8 @@ def run_reference(args):
     ms_step = 1e3 * float(np.mean(walls)) if walls else None
     sample = ("warm-up: one complete oracle LP source (Schur source, CGNR to %g, reconstruction, 16x7 "
               "contraction) on each of %d worker processes at once: %.1f s, %.2f CG iterations (mean); "
-              "each step: one oracle CG iteration at 24^3x48 on every worker (mean %.2f s); HP solve = LP "
+              "each step: one oracle Schur application at 24^3x48 on every worker, a CG iteration being two "
+              "(mean iteration %.2f s); HP solve = LP "
               "source + %d - %.2f more iterations (FP64 CG count of this system); summed over the workers "
               "(extrapolated from the measured per-source and per-iteration times)"
               % (LP_TOL, ncores, float(np.mean(t_lp)), lp_iters, float(np.mean(t_it)), HP_ITERS_FP64_CG,
@@ -543,6 +566,7 @@ def run_ours(args):
     tsm.tsm_profile(ctx.h, True)
     launches0 = ctx.launch_count()
     times, stats = [], []
+    pooled = PooledMoments()
     for k in range(args.steps):
         flush.zero_()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -552,6 +576,7 @@ def run_ours(args):
         ev1.record(stream)
         barrier()
         times.append(ev0.elapsed_time(ev1))
+        pooled.add(d_pc, d_pl)   # after the step's end event: per-source moments of every timed step
     launches = ctx.launch_count() - launches0
     prof_ms, prof_cnt, prof_bytes = ctx.profile_read()
     tsm.tsm_profile(ctx.h, False)
@@ -604,21 +629,23 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "sources/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lattice": list(DIMS), "n_hp_per_gpu": N_HP, "n_lp_per_gpu": N_LP,
-                       "batch": args.batch, "reliable_delta": rdelta,
-                       "hp_start": "lp-solution" if args.hp_warm_start else "zero",
-                       "mode": args.mode,
-                       "l2": "flushed between steps (256 MB write)",
-                       "lp_iters_per_source": st.lp_iters / float(N_HP + N_LP),
-                       "hp_iters_per_source": st.hp_iters / float(N_HP),
-                       "hp_max_true_res_warmup": (warm.hp_max_true_res if warm is not None else None)},
+            "config": base_config(),
+            "run": {"batch": args.batch, "reliable_delta": rdelta,
+                    "hp_start": "lp-solution" if args.hp_warm_start else "zero",
+                    "mode": args.mode,
+                    "lp_iters_per_source": st.lp_iters / float(N_HP + N_LP),
+                    "hp_iters_per_source": st.hp_iters / float(N_HP),
+                    "hp_max_true_res_warmup": (warm.hp_max_true_res if warm is not None else None)},
             "roofline": roofline, "clocks": clk, "gpu_launches": int(launches)}
 
     if rank == 0 and not args.no_extras:
         line["dslash"] = dslash_gbs(ctx, S, tsm, flush, peak)
         line["e2e"] = e2e_leg(ctx, tsm, U_pinned, lp_stop, hp_stop, gam, moms, stream, hp_range, lp_range,
                               batch=args.batch, warm=args.hp_warm_start)
-        line["equal_error"] = equal_error(ctx, tsm, S, d_pc, d_pl, step_ms, stream)
+        line["precision_vs_fp64"] = precision_leg(ctx, tsm, gam, moms, 20_000 + args.steps - 1, d_loops, d_err,
+                                                  hp_range, lp_range, args.batch, stream)
+        line["equal_error"] = equal_error(ctx, tsm, gam, moms, pooled, step_ms, stream, args.batch, hp_stop,
+                                          lp_stop)
         res, pool = oracle_on_host(U, t_src_too=True)
         if pool is not None:
             pool.close()
@@ -692,43 +719,157 @@ def e2e_leg(ctx, tsm, U_pinned, lp_stop, hp_stop, gam, moms, stream, hp_range, l
             "ms_per_step": t}
 
 
-def equal_error(ctx, tsm, S, d_pc, d_pl, step_ms, stream):
-    """Plain FP64 path vs TSM at equal loop error.  Plain: every source solved
-    to 1e-10 in FP64 (standard estimator), cost t_P per source (one solve
-    timed here); its per-source variance is that of the LP-set loops (the LP
-    solution differs from the exact one by the truncation only).  TSM error^2
-    = Var_corr/N_HP + Var_LP/N_LP from this run's per-source loops."""
+class PooledMoments:
+    """Per-entry sums of x and |x|^2 of the per-source loops of every timed
+    step (each step draws fresh noise, so the sources of all steps are
+    independent samples): HP-set corrections and LP-set loops, per entry and
+    summed over t."""
+
+    def __init__(self):
+        self.n = [0, 0]
+        self.s1 = [None, None]
+        self.s2 = [None, None]
+        self.t1 = [None, None]
+        self.t2 = [None, None]
+
+    def add(self, pc, pl):
+        for k, x in enumerate((pc, pl)):
+            xt = x.sum(-1)
+            parts = (x.sum(0), (x.abs() ** 2).sum(0), xt.sum(0), (xt.abs() ** 2).sum(0))
+            if self.s1[k] is None:
+                self.s1[k], self.s2[k], self.t1[k], self.t2[k] = parts
+            else:
+                self.s1[k] += parts[0]
+                self.s2[k] += parts[1]
+                self.t1[k] += parts[2]
+                self.t2[k] += parts[3]
+            self.n[k] += x.shape[0]
+
+    def var(self, k, summed_t):
+        """unbiased complex sample variance per entry (numpy)"""
+        a, b = (self.t1[k], self.t2[k]) if summed_t else (self.s1[k], self.s2[k])
+        n = self.n[k]
+        return ((b - a.abs() ** 2 / n) / (n - 1)).cpu().numpy()
+
+
+def precision_leg(ctx, tsm, gam, moms, seed, d_loops, d_err, hp_range, lp_range, batch, stream):
+    """Each loop's error against the FP64 path: the last timed step again with
+    every solve in FP64 (HP to 1e-10, LP with the same truncation rule), the
+    same seed, hence the same noise; |L_mixed - L_FP64| / sigma_FP64 per entry."""
     import torch
-    pc = d_pc.cpu().numpy()
-    pl = d_pl.cpu().numpy()
-    out = {}
-    # plain FP64 solve of one source, timed with events
-    b = np.zeros((DIMS[3], DIMS[2], DIMS[1], DIMS[0], 4, 3), dtype=np.complex128)
-    tsm.tsm_noise(ctx.h, 777, 4, 0, b)
-    s = np.zeros_like(b)
+    ref_loops, ref_err = torch.zeros_like(d_loops), torch.zeros_like(d_err)
+    p = tsm.params(seed, 4, hp_range, lp_range, tsm.stop(HP_TOL, HP_MAXIT, tsm.TSM_F64),
+                   tsm.stop(LP_TOL, LP_MAXIT, tsm.TSM_F64), list(gam), moms, batch=batch)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    st, iters, tres = tsm.tm_solve_batch(ctx.h, b, s, tsm.stop(HP_TOL, HP_MAXIT, tsm.TSM_F64))
-    t_p = time.perf_counter() - t0
-    out["plain_fp64"] = {"s_per_source": t_p, "iters": int(iters[0]), "true_res": float(tres[0])}
-    sel = {"Gamma=1,q=0,sum_t": (0, 0), "Gamma=gamma3gamma5,q=0,sum_t": (8, 0)}
-    for name, (g, q) in sel.items():
-        c = pc[:, g, q, :].sum(-1)
-        lv = pl[:, g, q, :].sum(-1)
-        var_c = np.var(c.real, ddof=1) + np.var(c.imag, ddof=1)
-        var_l = np.var(lv.real, ddof=1) + np.var(lv.imag, ddof=1)
-        eps2 = var_c / len(c) + var_l / len(lv)
-        n_eq = var_l / eps2
-        eff = n_eq / (step_ms * 1e-3)
-        out[name] = {"tsm_err": float(np.sqrt(eps2)), "plain_sources_for_equal_error": float(n_eq),
-                     "tsm_effective_sources_per_s": float(eff), "plain_sources_per_s": 1.0 / t_p,
-                     "ratio_vs_plain_fp64": float(eff * t_p)}
-    # median over all entries
-    var_c = np.var(pc.real, axis=0, ddof=1) + np.var(pc.imag, axis=0, ddof=1)
-    var_l = np.var(pl.real, axis=0, ddof=1) + np.var(pl.imag, axis=0, ddof=1)
-    ok = var_l > 0
-    ratio = (var_l[ok] / (var_c[ok] / pc.shape[0] + var_l[ok] / pl.shape[0])) / (step_ms * 1e-3) * t_p
-    out["median_all_entries_ratio_vs_plain_fp64"] = float(np.median(ratio))
+    tsm.tsm_loops(ctx.h, p, ref_loops, ref_err)
+    torch.cuda.synchronize()
+    t_fp64 = time.perf_counter() - t0
+    dz = ((d_loops - ref_loops).abs() / ref_err).cpu().numpy()
+    rel = ((d_loops - ref_loops).abs() / ref_loops.abs().max()).cpu().numpy()
+    return {"seed": seed, "reference": "the same TSM step with FP64 HP (1e-10) and FP64 LP (same truncation)",
+            "max_abs_diff_over_sigma": float(dz.max()), "median_abs_diff_over_sigma": float(np.median(dz)),
+            "max_abs_diff_over_sigma_per_gamma": [float(dz[g].max()) for g in range(dz.shape[0])],
+            "max_abs_diff_rel_to_max_loop": float(rel.max()), "bar": 0.1, "fp64_step_s": t_fp64}
+
+
+def equal_error(ctx, tsm, gam, moms, pooled, step_ms, stream, batch, hp_stop, lp_stop, n_plain=64):
+    """TSM against the plain FP64 path at equal loop error (the synthetic
+    analogue of the paper's HP/LP tuning, Sec. 2.2 and Fig. 1).
+
+    Plain path: every source solved to 1e-10 in FP64, standard estimator.  Its
+    per-source variance sigma_P^2 comes from n_plain plain FP64 solves and its
+    per-source cost t_P from single-source solves (tsm_loops with an empty HP
+    set, FP64 LP rule 1e-10, batch 1).  TSM: sigma_corr^2 and sigma_LP^2 pooled
+    over every timed step; t_LP from an LP-only step (256 sources) and t_HP =
+    (step - 264 t_LP) / 8.  With r = N_LP / N_HP = sqrt((sigma_LP^2 / t_LP) /
+    (sigma_corr^2 / (t_HP + t_LP))), the cost of error eps is T_TSM = (sigma_corr^2
+    + sigma_LP^2 / r) (t_HP + t_LP + r t_LP) / eps^2 against T_P = sigma_P^2 t_P
+    / eps^2.  One direct run confirms it: a TSM run sized by r for the plain
+    run's error on Gamma = 1, q = 0, sum_t, timed, its wall time scaled to
+    exactly that error."""
+    import torch
+    E = N_GAMMA * N_Q * DIMS[3]
+    shape = (N_GAMMA, N_Q, DIMS[3])
+    out = {}
+    # plain FP64 path: n_plain sources, single-source solves
+    plain64 = tsm.stop(HP_TOL, HP_MAXIT, tsm.TSM_F64)
+    pl_plain = torch.zeros((n_plain,) + shape, dtype=torch.complex128, device="cuda")
+    l_plain, e_plain = torch.zeros(shape, dtype=torch.complex128, device="cuda"), \
+        torch.zeros(shape, dtype=torch.float64, device="cuda")
+    p = tsm.params(40_000, 4, (0, 0), (0, n_plain), plain64, plain64, list(gam), moms, batch=1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = tsm.tsm_loops(ctx.h, p, l_plain, e_plain, None, None, None, pl_plain)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    T_plain = e0.elapsed_time(e1) * 1e-3
+    t_p = T_plain / n_plain
+    out["plain_fp64"] = {"sources": n_plain, "s_per_source": t_p, "iters": st.lp_iters / float(n_plain)}
+    # LP-only step for t_LP
+    lp_only = tsm.params(40_100, 4, (0, 0), (0, N_LP), hp_stop, lp_stop, list(gam), moms, batch=batch)
+    tsm.tsm_loops(ctx.h, lp_only, l_plain, e_plain)   # warm
+    torch.cuda.synchronize()
+    e0.record(stream)
+    tsm.tsm_loops(ctx.h, lp_only, l_plain, e_plain)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_lp = e0.elapsed_time(e1) * 1e-3 / N_LP
+    t_hp = max((step_ms * 1e-3 - (N_HP + N_LP) * t_lp) / N_HP, 1e-9)
+    out["tsm_costs"] = {"t_lp_s": t_lp, "t_hp_s": t_hp, "pooled_hp_sources": pooled.n[0],
+                        "pooled_lp_sources": pooled.n[1]}
+    xp = pl_plain.cpu().numpy()
+
+    def var_np(x):
+        return np.var(x.real, axis=0, ddof=1) + np.var(x.imag, axis=0, ddof=1)
+
+    vp_all, vp_t = var_np(xp), var_np(xp.sum(-1))
+    vc_all, vc_t = pooled.var(0, False), pooled.var(0, True)
+    vl_all, vl_t = pooled.var(1, False), pooled.var(1, True)
+
+    def ratio(vp, vc, vl):
+        r = np.sqrt((vl / t_lp) / (vc / (t_hp + t_lp)))
+        t_tsm = (vc + vl / r) * (t_hp + t_lp + r * t_lp)   # x eps^2
+        fixed = (vc / N_HP + vl / N_LP) * (step_ms * 1e-3)   # x eps^2 with this run's allocation
+        return r, vp * t_p / t_tsm, vp * t_p / fixed, vp / t_tsm
+
+    sel = {"Gamma=1,q=0,sum_t": 0, "Gamma=gamma3gamma5,q=0,sum_t": 8}
+    for name, g in sel.items():
+        r, rat, rat_fixed, eff = ratio(vp_t[g, 0], vc_t[g, 0], vl_t[g, 0])
+        out[name] = {"sigma2_plain": float(vp_t[g, 0]), "sigma2_corr": float(vc_t[g, 0]),
+                     "sigma2_lp": float(vl_t[g, 0]), "optimal_n_lp_over_n_hp": float(r),
+                     "ratio_vs_plain_fp64": float(rat), "ratio_at_this_runs_allocation": float(rat_fixed),
+                     "tsm_effective_sources_per_s": float(eff), "plain_sources_per_s": 1.0 / t_p}
+    ok = (vl_all > 0) & (vc_all > 0) & (vp_all > 0)
+    r_all = np.sqrt((vl_all[ok] / t_lp) / (vc_all[ok] / (t_hp + t_lp)))
+    rat_all = vp_all[ok] * t_p / ((vc_all[ok] + vl_all[ok] / r_all) * (t_hp + t_lp + r_all * t_lp))
+    out["median_all_entries_ratio_vs_plain_fp64"] = float(np.median(rat_all))
+    # direct confirmation on Gamma = 1, q = 0, sum_t at the plain run's error
+    g = 0
+    eps_p = float(np.sqrt(vp_t[g, 0] / n_plain))
+    r = out["Gamma=1,q=0,sum_t"]["optimal_n_lp_over_n_hp"]
+    n_hp = max(2, int(np.ceil((vc_t[g, 0] + vl_t[g, 0] / r) / eps_p ** 2)))
+    n_lp = max(2, int(round(r * n_hp)))
+    d_l = torch.zeros(shape, dtype=torch.complex128, device="cuda")
+    d_c = torch.zeros((n_hp,) + shape, dtype=torch.complex128, device="cuda")
+    d_p = torch.zeros((n_lp,) + shape, dtype=torch.complex128, device="cuda")
+    pd = tsm.params(50_000, 4, (0, n_hp), (n_hp, n_hp + n_lp), hp_stop, lp_stop, list(gam), moms, batch=batch)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    tsm.tsm_loops(ctx.h, pd, d_l, None, None, None, d_c, d_p)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    T_tsm = e0.elapsed_time(e1) * 1e-3
+    c = d_c.cpu().numpy().sum(-1)[:, g, 0]
+    lv = d_p.cpu().numpy().sum(-1)[:, g, 0]
+    eps_tsm = float(np.sqrt((np.var(c.real, ddof=1) + np.var(c.imag, ddof=1)) / n_hp +
+                            (np.var(lv.real, ddof=1) + np.var(lv.imag, ddof=1)) / n_lp))
+    T_tsm_eq = T_tsm * (eps_tsm / eps_p) ** 2
+    out["direct_confirmation"] = {"loop": "Gamma=1,q=0,sum_t", "plain_sources": n_plain, "plain_s": T_plain,
+                                  "plain_error": eps_p, "tsm_n_hp": n_hp, "tsm_n_lp": n_lp, "tsm_s": T_tsm,
+                                  "tsm_error": eps_tsm, "tsm_s_at_plain_error": T_tsm_eq,
+                                  "ratio_vs_plain_fp64": T_plain / T_tsm_eq}
     return out
 
 

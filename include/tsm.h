@@ -335,6 +335,17 @@ int tsm_umma_gemm(const void* A, const void* B, float* C, int M, int N, int K, i
 int tsm_umma_gemm_ex(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M, int N, int K,
                      int beta, int splits, int* used_splits, void* cuda_stream);
 
+/* Fault injection for tests of the bounded tensor-core waits (the paper has
+ * no counterpart).  withhold = 1: the following TMA-fed tensor-core GEMM
+ * launches of this process (tsm_umma_gemm*, the network's layers) issue no
+ * operand copies and give their stage waits a limit of 4096 polls instead of
+ * 2^26, so the MMA thread's first wait -- on a stage nothing fills -- runs
+ * out; nothing is in flight, every CTA frees its tensor memory and returns,
+ * and the call reports TSM_ERR_TIMEOUT with the context still usable.
+ * Launches whose operands the TMA cannot address (base not 16-byte aligned)
+ * run normally.  withhold = 0 restores normal operation.  Returns TSM_OK. */
+int tsm_umma_inject_timeout(int withhold);
+
 /* ---- learned LP preconditioner (the paper has no network; this is the
  * project's extension of the LP solves of Sec. 2.2: because the HP - LP
  * correction of Eq. 2.4 removes any LP bias, it may change the variance per

@@ -2,6 +2,7 @@
 // network object (forward, backward, Adam), training-pair generation from
 // the method's own FP32 solves, and the C ABI of the network.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -61,6 +62,7 @@ bool make_tensor_map(CUtensorMap* m, const void* base, int rows, int cols, int l
 }
 
 bool g_umma_tma = true;   // TMA-fed kernel when the operands allow it
+std::atomic<int> g_umma_withhold{0};   // fault injection (tsm_umma_inject_timeout)
 
 template <int BN>
 int umma_launch_any(cudaStream_t stream, dim3 grid, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int M,
@@ -71,7 +73,8 @@ int umma_launch_any(cudaStream_t stream, dim3 grid, const __nv_bfloat16* A, cons
     if (cudaFuncSetAttribute(umma_tma_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
       return TSM_ERR_CUDA;
-    umma_tma_gemm_kernel<BN><<<grid, UMMA_THREADS, smem, stream>>>(ta, tb, C, M, N, K, ldc, beta, error, kchunk, czs);
+    umma_tma_gemm_kernel<BN><<<grid, UMMA_THREADS, smem, stream>>>(ta, tb, C, M, N, K, ldc, beta, error, kchunk, czs,
+                                                                   g_umma_withhold.load());
     return cudaGetLastError() == cudaSuccess ? TSM_OK : TSM_ERR_CUDA;
   }
   return umma_launch<BN>(stream, grid, A, B, C, M, N, K, ldc, beta, error, lda, ldb, kchunk, czs);
@@ -408,6 +411,11 @@ extern "C" int tsm_umma_gemm_ex(const void* A, int lda, const void* B, int ldb, 
     return rc;
   }
   if (herr) return nbad(TSM_ERR_TIMEOUT, "tsm_umma_gemm: a tensor-core wait timed out");
+  return TSM_OK;
+}
+
+extern "C" int tsm_umma_inject_timeout(int withhold) {
+  g_umma_withhold.store(withhold ? 1 : 0);
   return TSM_OK;
 }
 

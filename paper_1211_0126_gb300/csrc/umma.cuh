@@ -34,6 +34,9 @@ template <int BN> __host__ __device__ constexpr int umma_smem_bytes() {
   return umma_stages<BN>() * umma_stage_bytes<BN>() + 1024;
 }
 constexpr long long UMMA_SPIN_LIMIT = 1ll << 26;   // bounded mbarrier wait
+// stage-wait limit of a launch with withheld operand copies (fault injection
+// for tests of the timeout path): the wait is on a barrier nothing arrives on
+constexpr long long UMMA_INJECT_LIMIT = 4096;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -62,9 +65,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 }
 
 // bounded wait for the phase `parity` of an mbarrier; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = UMMA_SPIN_LIMIT) {
   const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < UMMA_SPIN_LIMIT; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -260,7 +263,11 @@ __global__ void __launch_bounds__(UMMA_THREADS) umma_gemm_kernel(const __nv_bflo
 // stage to the producer; a last commit signals the accumulator to the
 // epilogue.  No thread-wide barrier inside the K loop.  Every wait is bounded;
 // on timeout the CTA records the error, waits (bounded) for the copies it
-// issued and for its MMAs, frees TMEM and returns.
+// issued and for its MMAs, frees TMEM and returns.  withhold = 1 (fault
+// injection for tests) issues no copies and gives the stage waits a limit of
+// UMMA_INJECT_LIMIT polls: the MMA thread's first wait, on a stage nothing
+// fills, runs out; no copy and no MMA is in flight, so the done and clean-up
+// waits (full limit) end at once.
 namespace tsm {
 
 constexpr int UMMA_TMA_BOX_K = UMMA_BK;   // columns per TMA box: 64 BF16 = one 128-byte swizzle span
@@ -299,7 +306,7 @@ __global__ void __launch_bounds__(UMMA_THREADS) umma_tma_gemm_kernel(const __gri
                                                                      const __grid_constant__ CUtensorMap tb,
                                                                      float* __restrict__ C, int M, int N, int K,
                                                                      int ldc, int beta, int* __restrict__ error,
-                                                                     int kchunk, long long czstride) {
+                                                                     int kchunk, long long czstride, int withhold) {
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "BN must be a multiple of 16 in [16, 256]");
   constexpr int TMEM_COLS = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
   constexpr int ST = umma_tma_stages<BN>();
@@ -338,11 +345,12 @@ __global__ void __launch_bounds__(UMMA_THREADS) umma_tma_gemm_kernel(const __gri
   const int kend = min(K, kbeg + kchunk);
   const int ktiles = kend > kbeg ? (kend - kbeg + UMMA_BK - 1) / UMMA_BK : 0;
   C += (size_t)blockIdx.z * (size_t)czstride;
+  const long long stage_limit = withhold ? UMMA_INJECT_LIMIT : UMMA_SPIN_LIMIT;
   if (threadIdx.x == 0) {
     // producer
-    for (int kt = 0; kt < ktiles; ++kt) {
+    for (int kt = 0; kt < ktiles && !withhold; ++kt) {
       const int s = kt % ST;
-      if (kt >= ST && !mbar_wait(&empty[s], (uint32_t)(((kt / ST) - 1) & 1))) {
+      if (kt >= ST && !mbar_wait(&empty[s], (uint32_t)(((kt / ST) - 1) & 1), stage_limit)) {
         atomicExch(&timed_out, 1);
         break;
       }
@@ -358,7 +366,7 @@ __global__ void __launch_bounds__(UMMA_THREADS) umma_tma_gemm_kernel(const __gri
     // MMA issuer
     for (int kt = 0; kt < ktiles; ++kt) {
       const int s = kt % ST;
-      if (!mbar_wait(&full[s], (uint32_t)((kt / ST) & 1))) {
+      if (!mbar_wait(&full[s], (uint32_t)((kt / ST) & 1), stage_limit)) {
         atomicExch(&timed_out, 1);
         break;
       }

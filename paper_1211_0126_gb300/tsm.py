@@ -87,6 +87,7 @@ _SIGS = {
                                        ctypes.POINTER(TsmLoopStats)]),
     "tsm_tune_batch": (ctypes.c_int, [_P, ctypes.POINTER(TmStop), ctypes.POINTER(ctypes.c_int), _P]),
     "tsm_umma_gemm": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "tsm_umma_inject_timeout": (ctypes.c_int, [ctypes.c_int]),
     "tsm_umma_gemm_ex": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int), _P]),
@@ -476,6 +477,10 @@ def tsm_net_loss(n, group):
 
 def tsm_set_precond(h, n):
     _check(library().tsm_set_precond(h, n), "tsm_set_precond")
+
+
+def tsm_umma_inject_timeout(withhold):
+    return _check(library().tsm_umma_inject_timeout(1 if withhold else 0), "tsm_umma_inject_timeout")
 
 
 def tsm_umma_gemm_ex(A, B, C, splits=1, beta=0, stream=None):

@@ -8,6 +8,11 @@
 * A batch wider than the number of sources equals single-source solves bit
   for bit.
 * Lattices with an odd or too small extent are rejected on the host.
+* Faults injected on the host: a NaN in a host source makes tm_solve_batch
+  return TSM_ERR_NONFINITE in every tier; twist and hopping parameters whose
+  operator overflows (finite kappa = 1e200) make tsm_loops return
+  TSM_ERR_NONFINITE; in both cases the next call on the same context, with
+  clean inputs, succeeds.
 """
 import numpy as np
 import pytest
@@ -83,3 +88,30 @@ def test_bad_lattices_rejected(ctx, dims):
     U = np.zeros((max(dims[3], 1), max(dims[2], 1), max(dims[1], 1), max(dims[0], 1), 4, 3, 3), dtype=np.complex128)
     with pytest.raises(tsm.TsmError):
         ctx.load_gauge(U, dims, KAPPA, MU)
+
+
+@pytest.mark.parametrize("prec", [tsm.TSM_F64, tsm.TSM_F32, tsm.TSM_F16, tsm.TSM_BF16])
+def test_nan_in_host_source_reports_nonfinite(ctx, field, prec):
+    ctx.load_gauge(field, DIMS, KAPPA, MU)
+    b = S.random_spinor(DIMS, 5)
+    b[1, 2, 3, 0, 2, 1] = complex(float("nan"), 0.0)
+    s = np.zeros_like(b)
+    stop = tsm.stop(1e-8, 200, prec, reliable=(prec == tsm.TSM_F32))
+    with pytest.raises(tsm.TsmError) as e:
+        tsm.tm_solve_batch(ctx.h, b, s, stop)
+    assert e.value.status == -5   # TSM_ERR_NONFINITE
+    # the context stays usable
+    clean = S.random_spinor(DIMS, 6)
+    sol, iters, tres, st = ctx.solve(clean, tsm.stop(1e-8, 2000, tsm.TSM_F64))
+    assert st == 0 and tres[0] < 1e-7
+
+
+def test_overflowing_operator_reports_nonfinite_in_tsm_loops(ctx, field):
+    ctx.load_gauge(field, DIMS, 1e200, MU)   # finite, so accepted; kappa^2 overflows
+    hp, lp = _stops()
+    with pytest.raises(tsm.TsmError) as e:
+        ctx.loops(3, 4, 2, 4, hp, lp, list(range(16)), S.default_momenta(4))
+    assert e.value.status == -5   # TSM_ERR_NONFINITE
+    ctx.load_gauge(field, DIMS, KAPPA, MU)
+    got = ctx.loops(3, 4, 2, 4, hp, lp, list(range(16)), S.default_momenta(4))
+    assert np.isfinite(got["loops"]).all()

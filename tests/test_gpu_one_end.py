@@ -70,8 +70,10 @@ def test_one_end_tsm_against_dense_and_mixed(ctx, field):
     assert np.median(z) < 1.5 and z.max() < 6.0
     mixed = ctx.loops(77, 4, 8, 96, tsm.stop(1e-10, 5000, tsm.TSM_F32, reliable=True),
                       tsm.stop(1e-2, 60, tsm.TSM_F16), GAM, MOMS, batch=8, estimator=1)
-    zm = np.abs(mixed["loops"] - ref["loops"]) / np.sqrt(mixed["err"] ** 2 + ref["err"] ** 2 + 1e-300)
-    assert np.median(zm) < 1.0 and zm.max() < 5.0
+    # same noise on both sides: every entry within 0.1 of the FP64 path's error
+    zm = np.abs(mixed["loops"] - ref["loops"]) / ref["err"]
+    print("one-end mixed: |L_mixed - L_FP64| / sigma_FP64: max %.3g, median %.3g" % (zm.max(), np.median(zm)))
+    assert zm.max() <= 0.1
 
 
 # ---- generalised one-end trick (Eq. 2.6): isoscalar u + d

@@ -179,14 +179,35 @@ def test_learned_tsm_unbiased(ctx):
     ctx.set_precond(net)
     gam, moms = list(range(16)), S.default_momenta(4)
     hp = tsm.stop(1e-10, 5000, tsm.TSM_F32, reliable=True)
-    got = ctx.loops(11, 4, 8, 64, hp, tsm.stop(1e-2, 200, tsm.TSM_F16, precond=True, restart=8), gam, moms)
+    got = ctx.loops(11, 4, 8, 64, hp, tsm.stop(1e-2, 200, tsm.TSM_F16, precond=True, restart=8), gam, moms,
+                    per_source=True)
     ref = ctx.loops(11, 4, 8, 64, tsm.stop(1e-12, 5000, tsm.TSM_F64), tsm.stop(1e-2, 5000, tsm.TSM_F64),
-                    gam, moms)
+                    gam, moms, per_source=True)
     ctx.set_precond(None)
     net.close()
     assert got["stats"]["hp_not_converged"] == 0
-    z = np.abs(got["loops"] - ref["loops"]) / np.sqrt(got["err"] ** 2 + ref["err"] ** 2 + 1e-300)
-    assert np.median(z) < 1.0 and z.max() < 5.0
+    # Same noise on both sides, but the learned LP map (flexible GMRES with the
+    # network, truncated in the Schur residual) is another solver than FP64 CG:
+    # per source the LP values differ by d_j = L_LP^learned - L_LP^FP64, and
+    # the two estimates by mean_LP(d) - mean_HP(d) (the HP solutions agree),
+    # which has zero expectation iff the learned estimate is unbiased.  Its
+    # standard error comes from the per-source differences themselves.
+    d_lp = got["per_lp"] - ref["per_lp"]
+    d_hp = ref["per_corr"] - got["per_corr"]
+
+    def var(x):
+        return np.var(x.real, axis=0, ddof=1) + np.var(x.imag, axis=0, ddof=1)
+
+    se = np.sqrt(var(d_lp) / d_lp.shape[0] + var(d_hp) / d_hp.shape[0])
+    diff = got["loops"] - ref["loops"]
+    assert np.abs(diff - (d_lp.mean(0) - d_hp.mean(0))).max() <= 1e-6 * np.abs(ref["loops"]).max()
+    zd = np.abs(diff) / se
+    z = np.abs(diff) / ref["err"]
+    print("learned: |L_learned - L_FP64| / sigma_FP64: max %.3g, median %.3g; / its own standard error: "
+          "max %.3g, median %.3g" % (z.max(), np.median(z), zd.max(), np.median(zd)))
+    assert np.median(zd) < 1.2 and zd.max() < 4.5
+    # and within the FP64 path's own stochastic error
+    assert z.max() < 1.0
 
 
 def test_trained_network_cuts_fgmres_iterations(libtsm):

@@ -78,24 +78,37 @@ def test_split_source_ranges_bit_identical(ctx, field):
 
 
 @pytest.mark.parametrize("tiers", ["mixed16", "mixedbf16", "fp32"])
-def test_mixed_precision_tsm_unbiased(ctx, field, tiers):
-    """HP: FP32 + FP64 reliable updates to 1e-10; LP: 16-bit storage at 5e-3.
-    The estimate agrees with the FP64 path within its stochastic error, and the
-    HP - LP correction of each source agrees with the FP64 one to the LP error."""
+def test_mixed_precision_tsm_within_tenth_sigma(ctx, field, tiers):
+    """HP: FP32 + FP64 reliable updates to 1e-10; LP: 16-bit (or FP32)
+    storage at 5e-3.  Against the FP64 path with the same seed and the same
+    stopping rules:
+    * every entry of the estimate within 0.1 of the FP64 path's stochastic
+      error (the bar the precision tiers must meet): both runs use the same
+      noise, so the difference is the precision effect alone,
+      mean_LP(dL) - mean_HP(dL) for the per-source LP differences dL;
+    * every source's HP loop L(s_HP) = corr + L(s_LP) equal to the FP64 one
+      to the HP tolerance (the LP loops of the HP-set sources come from a call
+      whose LP set is those sources: the LP map does not depend on the set)."""
     ctx.load_gauge(field, DIMS, KAPPA, MU)
     lp_prec = {"mixed16": tsm.TSM_F16, "mixedbf16": tsm.TSM_BF16, "fp32": tsm.TSM_F32}[tiers]
     hp = tsm.stop(1e-10, 5000, tsm.TSM_F32, reliable=True)
     lp = tsm.stop(5e-3, 60, lp_prec)
+    hp64, lp64 = tsm.stop(1e-12, 5000, tsm.TSM_F64), tsm.stop(5e-3, 60, tsm.TSM_F64)
     got = ctx.loops(11, 4, 8, 64, hp, lp, GAM, MOMS, per_source=True)
-    ref = ctx.loops(11, 4, 8, 64, tsm.stop(1e-12, 5000, tsm.TSM_F64), tsm.stop(5e-3, 60, tsm.TSM_F64),
-                    GAM, MOMS, per_source=True)
+    ref = ctx.loops(11, 4, 8, 64, hp64, lp64, GAM, MOMS, per_source=True)
     assert got["stats"]["hp_not_converged"] == 0
     assert got["stats"]["hp_max_true_res"] < 1e-8
-    # HP solutions agree: L(s_HP) = corr + L(s_LP) per source
-    hp_got = got["per_corr"][:, 0, 0] + 0
-    z = np.abs(got["loops"] - ref["loops"]) / np.sqrt(got["err"] ** 2 + ref["err"] ** 2 + 1e-300)
-    assert np.median(z) < 1.0 and z.max() < 5.0
-    assert np.isfinite(hp_got).all()
+    dz = np.abs(got["loops"] - ref["loops"]) / ref["err"]
+    print("%s: |L_mixed - L_FP64| / sigma_FP64: max %.3g, median %.3g" % (tiers, dz.max(), np.median(dz)))
+    assert dz.max() <= 0.1
+    # HP loops per source
+    lp_of_hp = ctx.loops(11, 4, 0, 0, hp, lp, GAM, MOMS, hp_range=(0, 0), lp_range=(0, 8), per_source=True)
+    lp_of_hp64 = ctx.loops(11, 4, 0, 0, hp64, lp64, GAM, MOMS, hp_range=(0, 0), lp_range=(0, 8), per_source=True)
+    l_hp = got["per_corr"] + lp_of_hp["per_lp"]
+    l_hp64 = ref["per_corr"] + lp_of_hp64["per_lp"]
+    assert np.abs(l_hp - l_hp64).max() <= 1e-5 * np.abs(l_hp64).max()
+    # and the per-source LP loops of the LP set agree to the LP precision
+    assert np.abs(got["per_lp"] - ref["per_lp"]).max() <= 0.05 * np.abs(ref["per_lp"]).max()
 
 
 @pytest.mark.parametrize("batch", [3, 8])

@@ -54,3 +54,26 @@ def test_umma_split_k_and_leading_dims(libtsm, m, n, k, splits):
         lo, hi = z * chunk, min(k, (z + 1) * chunk)
         pz = A[:, lo:hi].float() @ B[:, lo:hi].float().T
         assert (C[z] - pz).abs().max().item() <= 2e-5 * scale * max(1.0, np.sqrt(k / 64))
+
+
+def test_umma_wait_timeout_reports_and_recovers(libtsm):
+    """The bounded stage wait of the tensor-core kernel runs out on a stage
+    that nothing fills (operand copies withheld by the fault-injection switch,
+    nothing in flight): the call returns TSM_ERR_TIMEOUT, and the next call
+    on the same device computes the product again."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(7)
+    A = torch.randn(256, 256, generator=g, device="cuda").to(torch.bfloat16)
+    B = torch.randn(64, 256, generator=g, device="cuda").to(torch.bfloat16)
+    C = torch.zeros(256, 64, device="cuda")
+    tsm.tsm_umma_inject_timeout(True)
+    try:
+        with pytest.raises(tsm.TsmError) as e:
+            tsm.tsm_umma_gemm(A, B, C)
+        assert e.value.status == -6   # TSM_ERR_TIMEOUT
+    finally:
+        tsm.tsm_umma_inject_timeout(False)
+    C.fill_(float("nan"))
+    tsm.tsm_umma_gemm(A, B, C)
+    ref = A.float() @ B.float().T
+    assert (C - ref).abs().max().item() <= 2e-5 * ref.abs().max().item() * 2
