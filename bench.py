@@ -43,7 +43,6 @@ RELIABLE_DELTA = 1e-5        # FP64 residual replacement whenever ||r|| fell by 
 TIERS = {0: "f64", 1: "f32", 2: "bf16", 3: "f16"}
 REAL_BYTES = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
 NAIVE_REALS = {"f64": 8 * 18 + 8 * 24 + 24, "f32": 312, "bf16": 312, "f16": 312}
-FP32_PEAK = 69.1             # TFLOP/s, register-resident FFMA loop measured on a GB300 (2 flop per FMA)
 KINDS = ("K1_hop", "K2_hop_xpay_norm", "K3_hop_dag", "K4_hop_dag_cg_update")
 N_GAMMA, N_Q = 16, 7
 METRIC = "TSM sources/sec at 24^3x48 and Dslash HBM GB/s, vs plain FP64 at equal loop error"
@@ -610,6 +609,8 @@ def run_ours(args):
     streams = {0: 2 * sb, 1: 3 * sb, 2: 2 * sb, 3: 3 * sb + 4 * sb}   # the FP16 tier keeps r and x in FP16
     site_rhs = sum((prof_bytes[12 + k] / vh - prof_cnt[12 + k] * lb) / streams[k] * vh for k in range(4))
     alu_tflops = 1320.0 * site_rhs / (tot_ms * 1e-3) / 1e12 if tot_ms > 0 else None
+    # FP32 FMA peak of this GPU, measured now by the library's register-resident FMA loop
+    fp32_peak = tsm.tsm_measure_fma_peak(local, tsm.TSM_F32)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": (traffic["dram_over_algorithmic"] * alg_per_launch
@@ -617,9 +618,10 @@ def run_ours(args):
                 "traffic_source": ("ncu DRAM/algorithmic ratio of the same kernels at 16^3x32 x 32 sources, "
                                    "scaled to this launch" if traffic else "no capture for this kernel source"),
                 "algorithmic_bytes_per_launch": alg_per_launch,
-                "alu": {"flop_per_source_site": 1320, "achieved_tflops": alu_tflops, "peak_tflops": FP32_PEAK,
-                        "frac": (alu_tflops / FP32_PEAK) if alu_tflops else None,
-                        "peak_source": "measured FP32 FMA loop on a GB300 (nominal 80.5)"},
+                "alu": {"flop_per_source_site": 1320, "achieved_tflops": alu_tflops, "peak_tflops": fp32_peak,
+                        "frac": (alu_tflops / fp32_peak) if alu_tflops else None,
+                        "peak_source": "measured in this run: tsm_measure_fma_peak (FP32 FMA loop, 2 flop per "
+                                       "FMA; nominal 152 SMs x 128 lanes x 2 x 2.07 GHz = 80.5)"},
                 "kernel": "FP16 half-Dslash family K1-K4 of the LP solves (batch %d)" % args.batch,
                 "peak_source": ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                                 else "fallback 6.8 TB/s"),
@@ -693,6 +695,14 @@ def dslash_gbs(ctx, S, tsm, flush, peak):
                      # labelled "naive" count (no spinor reuse): 8 links + 8 neighbour spinors + 1
                      # output per site, 312 reals (the FP64 tier stores 18-real links: 360)
                      "naive_gbs": NAIVE_REALS[name] * REAL_BYTES[name] * (np.prod(DIMS) // 2) / t_launch / 1e9}
+    # the FP64 stencil is bound by the FP64 pipe on GB300: its arithmetic rate
+    # (1320 flop per site) against the FP64 FMA peak measured now
+    import torch
+    p64 = tsm.tsm_measure_fma_peak(torch.cuda.current_device(), tsm.TSM_F64)
+    f64_tflops = 1320.0 * (np.prod(DIMS) // 2) / (res["f64"]["us_per_launch"] * 1e-6) / 1e12
+    res["f64"]["alu"] = {"bound": "alu", "achieved_tflops": f64_tflops, "peak_tflops": p64,
+                         "frac": f64_tflops / p64, "unit": "TFLOP/s",
+                         "peak_source": "measured in this run: tsm_measure_fma_peak (FP64 FMA loop)"}
     return res
 
 

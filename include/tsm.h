@@ -431,6 +431,15 @@ int tsm_profile_read(tsm_ctx* ctx, double ms[16], long long count[16], double by
 int tsm_profile_read_ex(tsm_ctx* ctx, int n, double* ms, long long* count, double* bytes);
 long long tsm_launch_count(tsm_ctx* ctx);
 
+/* Measured arithmetic peak of CUDA device `device` (instrumentation: the
+ * denominator of the FP32 and FP64 arithmetic rooflines).  A register-resident
+ * kernel runs 8 independent FMA chains per thread on every resident thread of
+ * every SM; *tflops receives 2 flop per FMA over the best of three timed
+ * launches (after a warm-up).  prec: TSM_F32 or TSM_F64.  Allocates a small
+ * device buffer and its own stream; the calling thread's current device is
+ * restored on return. */
+int tsm_measure_fma_peak(int device, int prec, double* tflops);
+
 /* Contraction for callers that cannot allocate device memory.
  *
  * The paper has no counterpart: this entry point exists for callers that

@@ -547,10 +547,12 @@ int tm_dslash(tsm_ctx* h, int prec, int op, int dagger, const double* in, double
   TSM_TRY(eo_fields(c, "ds_out", prec, &fo));
   TSM_TRY(pack_eo(c, prec, din, fi));
   c.prof_this_launch = c.profile;
+  c.hop_per_site = true;   // one field: the per-site stencil (no link sharing to exploit)
   int rc = dispatch_prec(prec, [&](auto tag) {
     using S = decltype(tag);
     return apply_operator<S>(c, op, dagger ? 1 : 0, fi, fo);
   });
+  c.hop_per_site = false;
   c.prof_this_launch = false;
   TSM_TRY(rc);
   TSM_TRY(unpack_eo(c, prec, fo, dout));

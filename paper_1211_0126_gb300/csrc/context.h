@@ -105,6 +105,9 @@ struct Ctx {
   long long prof_cnt[kProfBuckets] = {};
   double prof_bytes[kProfBuckets] = {};
   bool prof_this_launch = false;   // solver sets it for the instrumented iteration
+  // single-source operator applications outside the solvers (tm_dslash): the
+  // 16-bit tiers use the one-thread-per-site stencil instead of link sharing
+  bool hop_per_site = false;
   long long launches = 0;
 
   // device buffer by name, (re)allocated when too small; contents undefined

@@ -88,6 +88,7 @@ _SIGS = {
     "tsm_tune_batch": (ctypes.c_int, [_P, ctypes.POINTER(TmStop), ctypes.POINTER(ctypes.c_int), _P]),
     "tsm_umma_gemm": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "tsm_umma_inject_timeout": (ctypes.c_int, [ctypes.c_int]),
+    "tsm_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "tsm_umma_gemm_ex": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int), _P]),
@@ -477,6 +478,13 @@ def tsm_net_loss(n, group):
 
 def tsm_set_precond(h, n):
     _check(library().tsm_set_precond(h, n), "tsm_set_precond")
+
+
+def tsm_measure_fma_peak(device, prec):
+    """Measured FMA peak of the device in TFLOP/s (prec TSM_F32 or TSM_F64)."""
+    v = ctypes.c_double(0.0)
+    _check(library().tsm_measure_fma_peak(int(device), int(prec), ctypes.byref(v)), "tsm_measure_fma_peak")
+    return v.value
 
 
 def tsm_umma_inject_timeout(withhold):
