@@ -610,7 +610,11 @@ def run_ours(args):
     site_rhs = sum((prof_bytes[12 + k] / vh - prof_cnt[12 + k] * lb) / streams[k] * vh for k in range(4))
     alu_tflops = 1320.0 * site_rhs / (tot_ms * 1e-3) / 1e12 if tot_ms > 0 else None
     # FP32 FMA peak of this GPU, measured now by the library's register-resident FMA loop
-    fp32_peak = tsm.tsm_measure_fma_peak(local, tsm.TSM_F32)
+    try:
+        fp32_peak = tsm.tsm_measure_fma_peak(local, tsm.TSM_F32)
+    except tsm.TsmError as e:
+        print("FMA peak not measured: %s" % e, file=sys.stderr)
+        fp32_peak = None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": (traffic["dram_over_algorithmic"] * alg_per_launch
@@ -619,7 +623,7 @@ def run_ours(args):
                                    "scaled to this launch" if traffic else "no capture for this kernel source"),
                 "algorithmic_bytes_per_launch": alg_per_launch,
                 "alu": {"flop_per_source_site": 1320, "achieved_tflops": alu_tflops, "peak_tflops": fp32_peak,
-                        "frac": (alu_tflops / fp32_peak) if alu_tflops else None,
+                        "frac": (alu_tflops / fp32_peak) if (alu_tflops and fp32_peak) else None,
                         "peak_source": "measured in this run: tsm_measure_fma_peak (FP32 FMA loop, 2 flop per "
                                        "FMA; nominal 152 SMs x 128 lanes x 2 x 2.07 GHz = 80.5)"},
                 "kernel": "FP16 half-Dslash family K1-K4 of the LP solves (batch %d)" % args.batch,

@@ -87,6 +87,8 @@ int Ctx::harvest_events() {
       prof_ms[r.kind] += ms;
       prof_cnt[r.kind] += 1;
       prof_bytes[r.kind] += r.bytes;
+    } else {
+      (void)cudaGetLastError();   // an untimed pair: leave no error behind for the caller
     }
     ev_free.push_back(r);
   }

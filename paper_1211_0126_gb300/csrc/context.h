@@ -190,7 +190,8 @@ struct TimedLaunch {
   bool on = false;
   // any_launch: time it whenever instrumentation is on (contraction buckets)
   TimedLaunch(Ctx& cc, int kind, double bytes, bool any_launch = false) : c(cc) {
-    if (!c.profile || !(c.prof_this_launch || any_launch)) return;
+    // under stream capture an event record becomes a dependency, not a time
+    if (!c.profile || c.capturing || !(c.prof_this_launch || any_launch)) return;
     if (c.ev_free.empty()) {
       Ctx::EvRec r{};
       if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;

@@ -48,30 +48,38 @@ int measure_on(int device, double* tflops) {
   T* sink = nullptr;
   cudaStream_t s = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  int rc = TSM_OK;
-  if (cudaMalloc(&sink, (size_t)blocks * PEAK_NT * sizeof(T)) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
-      cudaEventCreate(&e1) != cudaSuccess)
-    rc = TSM_ERR_CUDA;
-  float best = 0.f;
-  for (int rep = 0; rc == TSM_OK && rep < 4; ++rep) {   // rep 0 is the warm-up
-    cudaEventRecord(e0, s);
-    fma_loop_kernel<T><<<blocks, PEAK_NT, 0, s>>>(iters, (T)1, (T)0, sink);
-    cudaEventRecord(e1, s);
-    if (cudaEventSynchronize(e1) != cudaSuccess) {
-      rc = TSM_ERR_CUDA;
-      break;
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (rep > 0 && (best == 0.f || ms < best)) best = ms;
+  (void)cudaGetLastError();   // errors below are this routine's own
+  cudaError_t e = cudaMalloc(&sink, (size_t)blocks * PEAK_NT * sizeof(T));
+  const char* what = "cudaMalloc";
+  if (e == cudaSuccess) {
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    what = "cudaStreamCreateWithFlags";
   }
-  if (rc == TSM_OK && cudaGetLastError() != cudaSuccess) rc = TSM_ERR_CUDA;
-  if (rc == TSM_OK) {
+  if (e == cudaSuccess) {
+    e = cudaEventCreate(&e0);
+    what = "cudaEventCreate";
+  }
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 0.f;
+  for (int rep = 0; e == cudaSuccess && rep < 4; ++rep) {   // rep 0 is the warm-up
+    what = "timed launch";
+    e = cudaEventRecord(e0, s);
+    if (e != cudaSuccess) break;
+    fma_loop_kernel<T><<<blocks, PEAK_NT, 0, s>>>(iters, (T)1, (T)0, sink);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && rep > 0 && (best == 0.f || ms < best)) best = ms;
+  }
+  int rc = TSM_OK;
+  if (e == cudaSuccess && best > 0.f) {
     const double flop = 2.0 * PEAK_CHAINS * (double)iters * (double)blocks * PEAK_NT;
     *tflops = flop / (best * 1e-3) / 1e12;
   } else {
-    set_error("tsm_measure_fma_peak: %s", cudaGetErrorString(cudaGetLastError()));
+    set_error("tsm_measure_fma_peak: %s: %s", what, cudaGetErrorString(e));
+    rc = TSM_ERR_CUDA;
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
