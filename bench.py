@@ -56,7 +56,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / equal-error / cpu-baseline legs")
-    ap.add_argument("--batch", type=int, default=32, help="sources solved together (multi-RHS kernels)")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="sources solved together (multi-RHS kernels); default: the autotuner's choice (tsm_tune: "
+                         "batch width and sources per link-sharing block of the FP16 stencil)")
     ap.add_argument("--reliable-delta", type=float, default=None, help="override the HP reliable-update delta")
     ap.add_argument("--hp-warm-start", action="store_true",
                     help="HP solves start from their source's LP solution instead of zero")
@@ -538,6 +540,14 @@ def run_ours(args):
     hp_stop = tsm.stop(HP_TOL, HP_MAXIT, tsm.TSM_F32, reliable=True, reliable_delta=rdelta)
     lp_stop = tsm.stop(LP_TOL, LP_MAXIT, tsm.TSM_F16)
     hp_range, lp_range = replicas.source_ranges(N_HP, N_LP, rank, world)
+    # launch shape: autotuned (untimed, before the warm-up) unless a batch width is given
+    tune = None
+    if args.batch is None:
+        best, tile, ttimes = tsm.tsm_tune(ctx.h, lp_stop)
+        args.batch = best
+        tune = {"batch": best, "tile_sources": tile,
+                "ms_per_source": {"w%d" % w: {"t%d" % t: float(ttimes[i, j]) for j, t in enumerate((2, 4, 8))}
+                                  for i, w in enumerate((8, 16, 32, 64))}}
     E = N_GAMMA * N_Q * DIMS[3]
     shape = (N_GAMMA, N_Q, DIMS[3])
     d_loops = torch.zeros(shape, dtype=torch.complex128, device=dev)
@@ -636,7 +646,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": base_config(),
-            "run": {"batch": args.batch, "reliable_delta": rdelta,
+            "run": {"batch": args.batch, "autotuner": tune, "reliable_delta": rdelta,
                     "hp_start": "lp-solution" if args.hp_warm_start else "zero",
                     "mode": args.mode,
                     "lp_iters_per_source": st.lp_iters / float(N_HP + N_LP),
@@ -907,11 +917,13 @@ def run_three_lattice(args):
     for k, dims in enumerate(lattices):
         ctx = tsm.Context(0)
         ctx.load_gauge(S.gauge_field(dims, EPS, 100 + k), dims, KAPPA, MU)
-        best, times = tsm.tsm_tune_batch(ctx.h, lp)
+        best, tile, times = tsm.tsm_tune(ctx.h, lp)
         ctxs.append(ctx)
         widths.append(best)
-        tune["x".join(map(str, dims))] = {"batch": best, "ms_per_source": dict(zip(["8", "16", "32", "64"],
-                                                                                  [float(t) for t in times]))}
+        tune["x".join(map(str, dims))] = {"batch": best, "tile_sources": tile,
+                                          "ms_per_source": {"w%d" % w: {"t%d" % t: float(times[i, j])
+                                                                        for j, t in enumerate((2, 4, 8))}
+                                                            for i, w in enumerate((8, 16, 32, 64))}}
     outs = [torch.zeros((len(gam), len(moms), d[3]), dtype=torch.complex128, device="cuda") for d in lattices]
 
     def plist(seed):
@@ -1142,7 +1154,7 @@ def run_estimators(args):
         d_err = torch.zeros(shape, dtype=torch.float64, device=dev)
 
         def step(seed):
-            p = tsm.params(seed, 4, (0, N_HP), (N_HP, N_HP + N_LP), hp_stop, lp_stop, gam, mom, batch=args.batch,
+            p = tsm.params(seed, 4, (0, N_HP), (N_HP, N_HP + N_LP), hp_stop, lp_stop, gam, mom, batch=args.batch or 32,
                            **kw)
             return tsm.tsm_loops(ctx.h, p, d_loops, d_err, None, None, pc, pl)
 

@@ -316,6 +316,26 @@ int tsm_loops_graph(tsm_ctx** ctxs, const tsm_params* params, int n, double** lo
  * the 4 measured times per source in milliseconds. */
 int tsm_tune_batch(tsm_ctx* ctx, const tm_stop* stop, int* best, double* times_ms);
 
+/* Autotuner of the whole multi-RHS launch shape: the batch width as above
+ * and, for the 16-bit tiers, the sources per block of their link-sharing
+ * stencil (blocks of 32 sites x 2, 4 or 8 sources, one warp per source; the
+ * block's links are widened once and shared).  Times one batched solve of
+ * scratch noise sources per (width, block shape) pair and keeps the pair with
+ * the lowest time per source: *best_batch, *best_tile (may be NULL; 1 for
+ * tiers without that stencil).  The block shape is then used by every later
+ * solve of that tier on this context; the results do not depend on it (per-site
+ * arithmetic and reduction order are independent of the block shape).  Cached
+ * per context, lattice and stopping rule.  times_ms (may be NULL): 12 entries,
+ * [width k][shape q] = ms per source for widths {8, 16, 32, 64} and shapes
+ * {2, 4, 8} (0 where a shape does not apply).  tsm_tune_batch runs the same
+ * search and reports, per width, the best time over the shapes. */
+int tsm_tune(tsm_ctx* ctx, const tm_stop* stop, int* best_batch, int* best_tile, double* times_ms);
+
+/* Set the sources per block (2, 4 or 8) of the link-sharing stencil of tier
+ * prec (TSM_F16 or TSM_BF16) for this context's later solves, as tsm_tune
+ * does; 4 by default.  TSM_ERR_ARG for other tiers or values. */
+int tsm_set_tile(tsm_ctx* ctx, int prec, int tile_sources);
+
 
 /* Tensor-core GEMM of the learned preconditioner's channel mixing (the dense
  * contraction of the parallel-transport layers; the paper has no network --

@@ -956,8 +956,8 @@ int tsm_combine(tsm_ctx* h, const double* per_corr, int n_hp, const double* per_
   return TSM_OK;
 }
 
-int tsm_tune_batch(tsm_ctx* h, const tm_stop* stop, int* best, double* times_ms) {
-  if (h == nullptr || best == nullptr) return bad(TSM_ERR_ARG, "null argument");
+int tsm_tune(tsm_ctx* h, const tm_stop* stop, int* best_batch, int* best_tile, double* times_ms) {
+  if (h == nullptr || best_batch == nullptr) return bad(TSM_ERR_ARG, "null argument");
   TSM_TRY(check_stop(stop));
   Ctx& c = h->c;
   if (!c.has_gauge) return bad(TSM_ERR_NO_GAUGE, "no gauge field loaded");
@@ -966,9 +966,17 @@ int tsm_tune_batch(tsm_ctx* h, const tm_stop* stop, int* best, double* times_ms)
   snprintf(key, sizeof(key), "%dx%dx%dx%d/p%d/r%d/t%g/m%d", c.lat.L[0], c.lat.L[1], c.lat.L[2], c.lat.L[3],
            stop->prec, stop->reliable, stop->rel_tol, stop->max_iter);
   const int cand[4] = {8, 16, 32, 64};
-  auto it = c.tuned_batch.find(key);
-  if (it != c.tuned_batch.end() && times_ms == nullptr) {
-    *best = it->second;
+  const int tiles[3] = {2, 4, 8};
+  // the 16-bit tiers' link-sharing stencil has a block shape to choose; the
+  // other tiers run one thread per (source, site)
+  const bool tiled = stop->prec == TSM_F16 || stop->prec == TSM_BF16;
+  const int ntile = tiled ? 3 : 1;
+  auto ib = c.tuned_batch.find(key);
+  auto it = c.tuned_rpb.find(key);
+  if (ib != c.tuned_batch.end() && it != c.tuned_rpb.end() && times_ms == nullptr) {
+    *best_batch = ib->second;
+    if (best_tile) *best_tile = it->second;
+    if (tiled) c.tile_rpb[stop->prec] = it->second;
     return TSM_OK;
   }
   const int sp = solution_prec(*stop);
@@ -983,7 +991,8 @@ int tsm_tune_batch(tsm_ctx* h, const tm_stop* stop, int* best, double* times_ms)
   TSM_CUDA(cudaEventCreate(&e1));
   std::vector<SolveResult> res(cand[3]);
   double best_t = 1e300;
-  int best_w = cand[0];
+  int best_w = cand[0], best_r = tiled ? c.tile_rpb[stop->prec] : 1;
+  const int saved_rpb = tiled ? c.tile_rpb[stop->prec] : 0;
   int rc = TSM_OK;
   for (int k = 0; k < 4 && rc == TSM_OK; ++k) {
     const int w = cand[k];
@@ -992,28 +1001,64 @@ int tsm_tune_batch(tsm_ctx* h, const tm_stop* stop, int* best, double* times_ms)
       TSM_TRY(launch_noise<S>(c, 0, ns, 0, fb.e, w));
       return launch_noise<S>(c, 1, ns, 0, fb.o, w);
     });
-    if (rc != TSM_OK) break;
-    // one untimed solve to settle caches and clocks, then one timed
-    rc = solve_batch(c, *stop, 0, w, fb, fs, res.data());
-    if (rc != TSM_OK) break;
-    if (cudaEventRecord(e0, c.stream) != cudaSuccess) rc = TSM_ERR_CUDA;
-    if (rc == TSM_OK) rc = solve_batch(c, *stop, 0, w, fb, fs, res.data());
-    if (rc == TSM_OK && cudaEventRecord(e1, c.stream) != cudaSuccess) rc = TSM_ERR_CUDA;
-    if (rc == TSM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = TSM_ERR_CUDA;
-    float ms = 0.f;
-    if (rc == TSM_OK) cudaEventElapsedTime(&ms, e0, e1);
-    const double per = ms / w;
-    if (times_ms) times_ms[k] = per;
-    if (per < best_t) {
-      best_t = per;
-      best_w = w;
+    for (int q = 0; q < ntile && rc == TSM_OK; ++q) {
+      if (tiled) c.tile_rpb[stop->prec] = tiles[q];
+      // one untimed solve to settle caches and clocks, then one timed
+      rc = solve_batch(c, *stop, 0, w, fb, fs, res.data());
+      if (rc != TSM_OK) break;
+      if (cudaEventRecord(e0, c.stream) != cudaSuccess) rc = TSM_ERR_CUDA;
+      if (rc == TSM_OK) rc = solve_batch(c, *stop, 0, w, fb, fs, res.data());
+      if (rc == TSM_OK && cudaEventRecord(e1, c.stream) != cudaSuccess) rc = TSM_ERR_CUDA;
+      if (rc == TSM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = TSM_ERR_CUDA;
+      float ms = 0.f;
+      if (rc == TSM_OK) cudaEventElapsedTime(&ms, e0, e1);
+      const double per = ms / w;
+      if (times_ms) times_ms[3 * k + q] = per;
+      if (per < best_t) {
+        best_t = per;
+        best_w = w;
+        best_r = tiled ? tiles[q] : 1;
+      }
     }
+    if (times_ms && !tiled) times_ms[3 * k + 1] = times_ms[3 * k + 2] = 0.0;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (rc != TSM_OK) return rc;
+  if (rc != TSM_OK) {
+    if (tiled) c.tile_rpb[stop->prec] = saved_rpb;
+    return rc;
+  }
   c.tuned_batch[key] = best_w;
-  *best = best_w;
+  c.tuned_rpb[key] = best_r;
+  if (tiled) c.tile_rpb[stop->prec] = best_r;
+  *best_batch = best_w;
+  if (best_tile) *best_tile = best_r;
+  return TSM_OK;
+}
+
+int tsm_set_tile(tsm_ctx* h, int prec, int tile_sources) {
+  if (h == nullptr) return bad(TSM_ERR_ARG, "null context");
+  if (prec != TSM_F16 && prec != TSM_BF16) return bad(TSM_ERR_ARG, "only the 16-bit tiers have a block shape");
+  if (tile_sources != 2 && tile_sources != 4 && tile_sources != 8)
+    return bad(TSM_ERR_ARG, "sources per block must be 2, 4 or 8");
+  h->c.tile_rpb[prec] = tile_sources;
+  return TSM_OK;
+}
+
+int tsm_tune_batch(tsm_ctx* h, const tm_stop* stop, int* best, double* times_ms) {
+  if (best == nullptr) return bad(TSM_ERR_ARG, "null argument");
+  double t[12];
+  int tile = 0;
+  TSM_TRY(tsm_tune(h, stop, best, &tile, times_ms ? t : nullptr));
+  if (times_ms) {
+    // per width: the best over the block shapes
+    for (int k = 0; k < 4; ++k) {
+      double m = 1e300;
+      for (int q = 0; q < 3; ++q)
+        if (t[3 * k + q] > 0.0 && t[3 * k + q] < m) m = t[3 * k + q];
+      times_ms[k] = m;
+    }
+  }
   return TSM_OK;
 }
 

@@ -91,6 +91,10 @@ struct Ctx {
   int next_guard = 0;
   std::vector<std::pair<int, int>> cap_lp, cap_hp;   // (first state, count) of captured solves
   std::map<std::string, int> tuned_batch;            // autotuner cache: lattice + tier -> batch width
+  std::map<std::string, int> tuned_rpb;              // autotuner cache: lattice + tier -> sources per tile
+  // sources per link-sharing block of the 16-bit stencil, per tier id (2, 4 or
+  // 8; the autotuner sets it, the results do not depend on it)
+  int tile_rpb[4] = {LT_RHS, LT_RHS, LT_RHS, LT_RHS};
   // instrumentation
   bool profile = false;
   struct EvRec {

@@ -428,8 +428,9 @@ __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) cg_update_kern
 
 // ------------------------------------------------------------- link-sharing stencil
 // The 16-bit tiers' hop kernels (K1-K3 of their CG): blocks of LT_SITES
-// consecutive output sites x up to LT_RHS right-hand sides (threadIdx.x =
-// site, threadIdx.y = right-hand side of the block, one warp each).  The
+// consecutive output sites x up to RPB right-hand sides (threadIdx.x =
+// site, threadIdx.y = right-hand side of the block, one warp each; RPB = 2, 4
+// or 8, chosen per tier by the autotuner, LT_RHS by default).  The
 // block's 8 x LT_SITES links are read, widened to FP32 and completed with row
 // 2 once, kept in shared memory, and read from there by every right-hand side
 // of the block: 5 shared loads per link and source instead of 3 global loads,
@@ -439,7 +440,11 @@ __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) cg_update_kern
 // virtual-lane order over the blocks), so batched and single-source results
 // agree bit for bit.
 constexpr int LT_SITES = 32;
-constexpr int LT_RHS = 4;
+constexpr int LT_RHS = 4;   // default right-hand sides per block
+
+// resident blocks per SM the tile kernels are compiled for: 768 threads, the
+// register budget (80) of the per-site stencil at six blocks of 128
+template <int RPB> struct TileMinBlocks { static constexpr int value = 24 / RPB; };
 
 struct LinkTile {
   float4 v[8][5][LT_SITES];   // [hop 2 mu + backward][pair of complex][site]: rows 0..2, then a zero
@@ -499,8 +504,9 @@ struct TileLinks {
 // out, so the order is the same whatever the block's width.
 constexpr int LT_VLANES = 128;
 
+template <int RPB>
 __device__ __forceinline__ void tile_grid_sum(float part, int rhs, RedSlot slot, CGState* st, int post) {
-  __shared__ int last_rhs[LT_RHS];
+  __shared__ int last_rhs[RPB];
   __shared__ double vsum[LT_VLANES];
   const int w = threadIdx.y, lane = threadIdx.x, nthr = LT_SITES * blockDim.y, tid = w * LT_SITES + lane;
   float v = part;
@@ -550,9 +556,9 @@ __device__ __forceinline__ int tile_rhs(const int* active, int nrhs) {
   return active != nullptr ? active[k] : k;
 }
 
-template <class S, int DAG, int MODE>
-__global__ void __launch_bounds__(LT_SITES * LT_RHS, HopMinBlocks<S>::value) hop_tile_kernel(const HopArgs<S> a,
-                                                                                           int nrhs) {
+template <class S, int DAG, int MODE, int RPB>
+__global__ void __launch_bounds__(LT_SITES * RPB, TileMinBlocks<RPB>::value) hop_tile_kernel(const HopArgs<S> a,
+                                                                                            int nrhs) {
   __shared__ LinkTile tile;
   using R = typename S::real;
   int rhs = tile_rhs(a.active, nrhs);
@@ -570,7 +576,7 @@ __global__ void __launch_bounds__(LT_SITES * LT_RHS, HopMinBlocks<S>::value) hop
     hop_site_with<S, DAG>(a.g, c, a.in + off, a.sstride, TileLinks{tile, (int)threadIdx.x}, acc);
     part = hop_epilogue<S, MODE>(a, off, ih, acc);
   }
-  if constexpr (MODE & HOP_NORM) tile_grid_sum(part, rhs, a.red, a.st, a.post);
+  if constexpr (MODE & HOP_NORM) tile_grid_sum<RPB>(part, rhs, a.red, a.st, a.post);
 }
 
 // p = r + beta p   (grid: x = right-hand side, y = blocks of 256 sites)

@@ -40,23 +40,28 @@ int launch_hop(Ctx& c, const HopArgs<S>& a0, int dag, int mode, int prof_kind, i
   const double bytes = (double)a.g.Vh *
       (lb + nrhs * sb * (2 + ((mode & HOP_CENTER) ? 1 : 0) + ((mode & HOP_BASE) ? 1 : 0)));
   TimedLaunch tl(c, 4 * S::id + kind, bytes);
-  // 16-bit tiers: link-sharing blocks of LT_SITES sites x up to LT_RHS
-  // sources (every solve, whatever its batch width, so that a source's
-  // iterates do not depend on its batch); others, and single-source operator
-  // applications outside the solvers (c.hop_per_site): one thread per
-  // (source, site), blocks of HOP_NT sites
+  // 16-bit tiers: link-sharing blocks of LT_SITES sites x up to RPB sources
+  // (RPB = c.tile_rpb, 2, 4 or 8 from the autotuner; every solve, whatever its
+  // batch width, so that a source's iterates do not depend on its batch);
+  // others, and single-source operator applications outside the solvers
+  // (c.hop_per_site): one thread per (source, site), blocks of HOP_NT sites
   constexpr bool TILE16 = S::id == F16::id || S::id == BF16::id;
   const bool tile = TILE16 && !(c.hop_per_site && nrhs == 1);
-  const int rpb = nrhs < LT_RHS ? nrhs : LT_RHS;
+  const int RPB = c.tile_rpb[S::id];
+  const int rpb = nrhs < RPB ? nrhs : RPB;
   const dim3 grid = tile ? dim3((nrhs + rpb - 1) / rpb, blocks_for(a.g.Vh, LT_SITES)) : dim3(nrhs, nb);
   const dim3 block = tile ? dim3(LT_SITES, rpb) : dim3(HOP_NT);
-#define TSM_HOP_CASE(D, M)                                                               \
-  if (dag == (D) && mode == (M)) {                                                       \
-    if (tile) {                                                                          \
-      if constexpr (TILE16) hop_tile_kernel<S, (D), (M)><<<grid, block, 0, c.stream>>>(a, nrhs); \
-    } else {                                                                             \
-      hop_kernel<S, (D), (M)><<<grid, block, 0, c.stream>>>(a);                          \
-    }                                                                                    \
+#define TSM_HOP_CASE(D, M)                                                                        \
+  if (dag == (D) && mode == (M)) {                                                                \
+    if (tile) {                                                                                   \
+      if constexpr (TILE16) {                                                                     \
+        if (RPB == 2) hop_tile_kernel<S, (D), (M), 2><<<grid, block, 0, c.stream>>>(a, nrhs);     \
+        else if (RPB == 8) hop_tile_kernel<S, (D), (M), 8><<<grid, block, 0, c.stream>>>(a, nrhs); \
+        else hop_tile_kernel<S, (D), (M), 4><<<grid, block, 0, c.stream>>>(a, nrhs);              \
+      }                                                                                           \
+    } else {                                                                                      \
+      hop_kernel<S, (D), (M)><<<grid, block, 0, c.stream>>>(a);                                   \
+    }                                                                                             \
   }
   TSM_HOP_CASE(0, 0)
   else TSM_HOP_CASE(0, HOP_CENTER)

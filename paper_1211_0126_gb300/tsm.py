@@ -86,6 +86,9 @@ _SIGS = {
     "tsm_loops_graph": (ctypes.c_int, [_P, ctypes.POINTER(TsmParams), ctypes.c_int, _P, _P, _P, _P,
                                        ctypes.POINTER(TsmLoopStats)]),
     "tsm_tune_batch": (ctypes.c_int, [_P, ctypes.POINTER(TmStop), ctypes.POINTER(ctypes.c_int), _P]),
+    "tsm_tune": (ctypes.c_int, [_P, ctypes.POINTER(TmStop), ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int), _P]),
+    "tsm_set_tile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "tsm_umma_gemm": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "tsm_umma_inject_timeout": (ctypes.c_int, [ctypes.c_int]),
     "tsm_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -399,6 +402,22 @@ def tsm_tune_batch(h, stp):
     _check(library().tsm_tune_batch(h, ctypes.byref(stp), ctypes.byref(best), ctypes.c_void_p(times.ctypes.data)),
            "tsm_tune_batch")
     return best.value, times
+
+
+def tsm_tune(h, stp):
+    """Autotuned launch shape for the loaded lattice and tier: returns (best
+    batch width, best sources per link-sharing block, per-source ms [4][3] for
+    widths 8, 16, 32, 64 x block shapes 2, 4, 8)."""
+    best = ctypes.c_int(0)
+    tile = ctypes.c_int(0)
+    times = np.zeros(12)
+    _check(library().tsm_tune(h, ctypes.byref(stp), ctypes.byref(best), ctypes.byref(tile),
+                              ctypes.c_void_p(times.ctypes.data)), "tsm_tune")
+    return best.value, tile.value, times.reshape(4, 3)
+
+
+def tsm_set_tile(h, prec, tile_sources):
+    return _check(library().tsm_set_tile(h, int(prec), int(tile_sources)), "tsm_set_tile")
 
 
 def tsm_umma_gemm(A, B, C, beta=0, stream=None):
