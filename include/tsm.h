@@ -409,6 +409,24 @@ int tsm_net_gradient(tsm_net* net, tsm_ctx* ctx, int nb, const double* x, const 
  * The pairs stay in device memory (2 x 96 V bytes each) until the network is
  * destroyed; the context must outlive the network's use of them. */
 int tsm_net_add_pairs(tsm_net* net, tsm_ctx* ctx, int n, uint64_t seed, const tm_stop* stop, int* group);
+/* Make training pairs from the method's own solves: for the Z4 noise sources
+ * eta_j of `seed` (j = 0 .. n_sources-1, as tsm_loops draws them) the converged
+ * solution x* of Dhat x = bhat_j (stop: TSM_F32, no reliable updates) and the
+ * CGNR iterates x_k after k = iters[q] >= 0 iterations from zero (the first
+ * k iterations of the same solve; k = 0: x_0 = 0, the pair (Dhat x*, x*)
+ * of the source itself) give n_sources * n_iters pairs
+ *   t = x* - x_k,   r = Dhat t   (= bhat - Dhat x_k up to x*'s tolerance):
+ * the Krylov residuals of those solves with their exact targets Dhat^-1 r.
+ * Pairs are stored batch by batch (batches of up to 64 consecutive
+ * sources): in the batch of m sources starting at j0, the pair of source j
+ * and iteration count iters[q] has index j0 * n_iters + q * m + (j - j0).
+ * TSM_ERR_ARG if an iterate equals x* (k too large).  The pairs stay in
+ * device memory until the network is destroyed. */
+int tsm_net_add_solve_pairs(tsm_net* net, tsm_ctx* ctx, int n_sources, uint64_t seed, const int* iters, int n_iters,
+                            const tm_stop* stop, int* group);
+/* Host copies of pair `index` of `group`: r and t as canonical spinors
+ * (24 V doubles each; odd sites zero). */
+int tsm_net_get_pair(tsm_net* net, int group, int index, double* r, double* t);
 /* Adam (lr; betas 0.9, 0.999) on the mean over a minibatch of the relative
  * loss |net(r) - t|^2 / |t|^2 over even sites; step k uses groups[k mod
  * n_groups] and `batch` consecutive pairs of it.  loss (may be NULL) receives

@@ -672,6 +672,148 @@ extern "C" int tsm_net_add_pairs(tsm_net* h, tsm_ctx* ch, int n_pairs, uint64_t 
   return TSM_OK;
 }
 
+namespace tsm {
+namespace {
+
+// out = a - b over n float4 words (batches of FP32 parity fields)
+__global__ void sub_f4_kernel(long long n, const float4* __restrict__ a, const float4* __restrict__ b,
+                              float4* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 x = a[i], y = b[i];
+  out[i] = make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
+}
+
+// out_e = Dhat in_e for m even-site FP32 fields (odd scratch u):
+// u = A^-1 H_oe in, out = A^-1 (A in - kappa^2 H_eo u)
+int schur_f32(Ctx& c, PField in, PField u, PField out, int m) {
+  const double k = c.lat.kappa, mu = c.lat.mu;
+  HopArgs<F32> h = hop_args<F32>(c, 1);
+  h.in = in.as<F32>();
+  h.out = u.as<F32>();
+  h.to = twist_Ainv(k, mu);
+  TSM_TRY(launch_hop<F32>(c, h, 0, 0, -1, m));
+  h = hop_args<F32>(c, 0);
+  h.in = u.as<F32>();
+  h.center = in.as<F32>();
+  h.tc = twist_A(k, mu);
+  h.ac = 1.0;
+  h.ah = -k * k;
+  h.to = twist_Ainv(k, mu);
+  h.out = out.as<F32>();
+  return launch_hop<F32>(c, h, 0, HOP_CENTER, -1, m);
+}
+
+}  // namespace
+}  // namespace tsm
+
+extern "C" int tsm_net_add_solve_pairs(tsm_net* h, tsm_ctx* ch, int n_sources, uint64_t seed, const int* iters,
+                                       int n_iters, const tm_stop* stop, int* group) {
+  if (h == nullptr || stop == nullptr || iters == nullptr) return nbad(TSM_ERR_ARG, "null argument");
+  if (n_sources < 1 || n_iters < 1) return nbad(TSM_ERR_ARG, "n_sources and n_iters must be >= 1");
+  if (stop->prec != TSM_F32 || stop->reliable || stop->precond)
+    return nbad(TSM_ERR_ARG, "training solves are plain FP32 CG (prec TSM_F32, no reliable updates)");
+  for (int q = 0; q < n_iters; ++q)
+    if (iters[q] < 0) return nbad(TSM_ERR_ARG, "iteration counts must be >= 0");
+  Net& n = h->n;
+  TSM_TRY(check_ctx(ch, n));
+  Ctx& c = ch->c;
+  const int V = c.g.V;
+  const int n_pairs = n_sources * n_iters;
+  PairGroup G;
+  G.ctx = &c;
+  G.n = n_pairs;
+  TSM_TRY(dalloc(&G.R, (size_t)n_pairs * 3 * V * 8));
+  TSM_TRY(dalloc(&G.T, (size_t)n_pairs * 3 * V * 8));
+  TSM_TRY(dalloc(&G.den, n_pairs));
+  TSM_CUDA(cudaMemsetAsync(G.den, 0, n_pairs * sizeof(double), c.stream));
+  const int width = std::min(n_sources, Ctx::kMaxBatch);
+  c.batch_cap = std::max(c.batch_cap, width);
+  PField bo, be, xe, xo, ke, ko, te, ue, re;
+  TSM_TRY(c.field("sp_be", TSM_F32, &be, c.batch_cap));
+  TSM_TRY(c.field("sp_bo", TSM_F32, &bo, c.batch_cap));
+  TSM_TRY(c.field("sp_xe", TSM_F32, &xe, c.batch_cap));
+  TSM_TRY(c.field("sp_xo", TSM_F32, &xo, c.batch_cap));
+  TSM_TRY(c.field("sp_ke", TSM_F32, &ke, c.batch_cap));
+  TSM_TRY(c.field("sp_ko", TSM_F32, &ko, c.batch_cap));
+  TSM_TRY(c.field("sp_te", TSM_F32, &te, c.batch_cap));
+  TSM_TRY(c.field("sp_ue", TSM_F32, &ue, c.batch_cap));
+  TSM_TRY(c.field("sp_re", TSM_F32, &re, c.batch_cap));
+  const NoiseSpec ns = make_noise(seed, 4);
+  std::vector<SolveResult> res(width);
+  for (int j0 = 0; j0 < n_sources; j0 += width) {
+    const int m = std::min(width, n_sources - j0);
+    // sources eta_j as tsm_loops draws them; the converged solution x*
+    TSM_TRY(launch_noise<F32>(c, 0, ns, (uint32_t)j0, be, m));
+    TSM_TRY(launch_noise<F32>(c, 1, ns, (uint32_t)j0, bo, m));
+    TSM_TRY(solve_batch(c, *stop, 0, m, EOField{be, bo}, EOField{xe, xo}, res.data()));
+    for (int r = 0; r < m; ++r)
+      if (res[r].status != TSM_OK) return nbad(TSM_ERR_NONFINITE, "a training solve met NaN/Inf");
+    for (int q = 0; q < n_iters; ++q) {
+      // the iterate after iters[q] CGNR iterations from zero (the first
+      // iterations of the same solve), t = x* - x_k, r = Dhat t
+      if (iters[q] == 0) {
+        TSM_TRY((launch_convert<F32, F32>(c, PField{}, ke, nullptr, m)));   // x_0 = 0: t = x*, r = bhat
+      } else {
+        const tm_stop sk{0.0, iters[q], TSM_F32, 0, 0.0, 0, 0};
+        TSM_TRY(solve_batch(c, sk, 0, m, EOField{be, bo}, EOField{ke, ko}, res.data()));
+      }
+      const long long n4 = (long long)m * F32::SN * c.sstride;
+      sub_f4_kernel<<<(unsigned)((n4 + 255) / 256), 256, 0, c.stream>>>(n4, xe.as<F32>(), ke.as<F32>(), te.as<F32>());
+      TSM_TRY(check_net_launch(c, "sub_f4_kernel"));
+      TSM_TRY(schur_f32(c, te, ue, re, m));
+      const size_t off = ((size_t)j0 * n_iters + (size_t)q * m) * 3 * V * 8;
+      const int p0 = j0 * n_iters + q * m;
+      pt_pack_even_kernel<<<dim3(grid1(V, NET_NT), m), NET_NT, 0, c.stream>>>(c.g, re.as<F32>(), c.sstride, G.R + off);
+      TSM_TRY(check_net_launch(c, "pt_pack_even_kernel"));
+      pt_pack_even_kernel<<<dim3(grid1(V, NET_NT), m), NET_NT, 0, c.stream>>>(c.g, te.as<F32>(), c.sstride, G.T + off);
+      TSM_TRY(check_net_launch(c, "pt_pack_even_kernel"));
+      pt_even_norm_kernel<<<dim3(grid1(V, NET_NT), m), NET_NT, 0, c.stream>>>(c.g, G.T + off, G.den + p0);
+      TSM_TRY(check_net_launch(c, "pt_even_norm_kernel"));
+    }
+  }
+  std::vector<double> den(n_pairs);
+  TSM_CUDA(cudaMemcpyAsync(den.data(), G.den, n_pairs * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  TSM_CUDA(cudaStreamSynchronize(c.stream));
+  for (int p = 0; p < n_pairs; ++p)
+    if (!(den[p] > 0.0)) {
+      dfree(G.R);
+      dfree(G.T);
+      dfree(G.den);
+      return nbad(TSM_ERR_ARG, "an iterate equals the converged solution (iteration count too large)");
+    }
+  n.groups.push_back(G);
+  if (group) *group = (int)n.groups.size() - 1;
+  return TSM_OK;
+}
+
+extern "C" int tsm_net_get_pair(tsm_net* h, int group, int index, double* r, double* t) {
+  if (h == nullptr || r == nullptr || t == nullptr) return nbad(TSM_ERR_ARG, "null argument");
+  Net& n = h->n;
+  if (group < 0 || group >= (int)n.groups.size()) return nbad(TSM_ERR_ARG, "no such pair group");
+  PairGroup& G = n.groups[group];
+  if (index < 0 || index >= G.n) return nbad(TSM_ERR_ARG, "pair index out of range");
+  Ctx& c = *G.ctx;
+  const int V = c.g.V;
+  double2* d = nullptr;
+  TSM_TRY(dalloc(&d, (size_t)2 * V * 12));
+  const size_t off = (size_t)index * 3 * V * 8;
+  int rc = TSM_OK;
+  for (int w = 0; w < 2 && rc == TSM_OK; ++w) {
+    pt_act_to_canon_kernel<<<dim3(grid1(V, NET_NT), 1), NET_NT, 0, c.stream>>>(V, 1, (w ? G.T : G.R) + off,
+                                                                              d + (size_t)w * V * 12);
+    rc = check_net_launch(c, "pt_act_to_canon_kernel");
+  }
+  if (rc == TSM_OK &&
+      (cudaMemcpyAsync(r, d, (size_t)V * 12 * sizeof(double2), cudaMemcpyDeviceToHost, c.stream) != cudaSuccess ||
+       cudaMemcpyAsync(t, d + (size_t)V * 12, (size_t)V * 12 * sizeof(double2), cudaMemcpyDeviceToHost, c.stream) !=
+           cudaSuccess ||
+       cudaStreamSynchronize(c.stream) != cudaSuccess))
+    rc = nbad(TSM_ERR_CUDA, "pair copy failed");
+  dfree(d);
+  return rc;
+}
+
 namespace {
 
 // one forward (+ loss, + backward when train) over pairs i0 .. i0+nb-1 of group g

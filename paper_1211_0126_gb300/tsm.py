@@ -104,6 +104,9 @@ _SIGS = {
     "tsm_net_gradient": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P, _P]),
     "tsm_net_add_pairs": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(TmStop),
                                          ctypes.POINTER(ctypes.c_int)]),
+    "tsm_net_add_solve_pairs": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_uint64, _P, ctypes.c_int,
+                                               ctypes.POINTER(TmStop), ctypes.POINTER(ctypes.c_int)]),
+    "tsm_net_get_pair": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "tsm_net_train": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P]),
     "tsm_net_loss": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "tsm_set_precond": (ctypes.c_int, [_P, _P]),
@@ -474,6 +477,20 @@ def tsm_net_gradient(n, h, nb, x, gy, gx, gw):
     _check(library().tsm_net_gradient(n, h, int(nb), px, pg, pgx, pgw), "tsm_net_gradient")
 
 
+def tsm_net_add_solve_pairs(n, h, n_sources, seed, iters, stp):
+    it = np.ascontiguousarray(np.asarray(iters, dtype=np.int32))
+    g = ctypes.c_int(-1)
+    _check(library().tsm_net_add_solve_pairs(n, h, int(n_sources), ctypes.c_uint64(seed),
+                                             ctypes.c_void_p(it.ctypes.data), len(it), ctypes.byref(stp),
+                                             ctypes.byref(g)), "tsm_net_add_solve_pairs")
+    return g.value
+
+
+def tsm_net_get_pair(n, group, index, r, t):
+    _check(library().tsm_net_get_pair(n, int(group), int(index), ctypes.c_void_p(r.ctypes.data),
+                                      ctypes.c_void_p(t.ctypes.data)), "tsm_net_get_pair")
+
+
 def tsm_net_add_pairs(n, h, count, seed, stp):
     g = ctypes.c_int(-1)
     _check(library().tsm_net_add_pairs(n, h, int(count), ctypes.c_uint64(seed), ctypes.byref(stp), ctypes.byref(g)),
@@ -762,6 +779,17 @@ class Network:
 
     def add_pairs(self, ctx, count, seed, stp):
         return tsm_net_add_pairs(self.h, ctx.h, count, seed, stp)
+
+    def add_solve_pairs(self, ctx, n_sources, seed, iters, stp):
+        """Pairs (r = Dhat t, t = x* - x_k) from the CGNR iterates x_k (k in
+        iters) of solves of the noise sources 0 .. n_sources-1 of seed."""
+        return tsm_net_add_solve_pairs(self.h, ctx.h, n_sources, seed, iters, stp)
+
+    def get_pair(self, group, index, spinor_shape):
+        r = np.zeros(spinor_shape, dtype=np.complex128)
+        t = np.zeros(spinor_shape, dtype=np.complex128)
+        tsm_net_get_pair(self.h, group, index, r, t)
+        return r, t
 
     def train(self, groups, steps, batch, lr):
         return tsm_net_train(self.h, groups, steps, batch, lr)

@@ -1,7 +1,8 @@
 """The learned LP preconditioner on the GPU against the oracle.
 
 * Forward of a parallel-transport network (FP32 transports, BF16 x BF16 -> FP32
-  channel mixing on the tensor cores) against oracle.ptnet in FP64.  Bound:
+  channel mixing on the tensor cores) against oracle.ptnet in FP64, up to the
+  24 channels of the learned-preconditioner workload.  Bound:
   normwise relative error below 4 L u, u = 2^-9 the BF16 unit roundoff (per
   layer one rounding of the gathered input and one of the weights, each
   bounded by u, summed with random signs; L layers compound).
@@ -10,7 +11,10 @@
 * Training pairs and loss: the network's mean relative loss on its pairs
   equals the oracle's on (Z4 noise on even sites from the oracle's Philox,
   Dhat^-1 r by the oracle's CG), within the forward bound.
-* Training lowers the loss on a held-out gauge field.
+* Pairs from the method's own solves (Krylov residuals r = bhat - Dhat x_k
+  of CGNR iterates with targets x* - x_k) against the oracle's iterates.
+* Training lowers the loss on a held-out gauge field; training on either
+  kind of pairs cuts flexible GMRES steps.
 * Flexible GMRES with the network solves D_tm s = eta (dense inverse as judge),
   honours the fixed-step rule, and hands a broken network (NaN weights planted
   on the host) to plain CG.
@@ -39,7 +43,7 @@ def _oracle_weights(net):
     return [net.get_weights(l) for l in range(len(net.channels) - 1)]
 
 
-@pytest.mark.parametrize("channels", [[1, 3, 2, 1], [1, 12, 12, 12, 1]])
+@pytest.mark.parametrize("channels", [[1, 3, 2, 1], [1, 12, 12, 12, 1], [1, 24, 24, 24, 1]])
 def test_forward_matches_oracle(ctx, channels):
     U = S.gauge_field(DIMS, 0.3, 3)
     ctx.load_gauge(U, DIMS, KAPPA, MU)
@@ -63,10 +67,10 @@ def test_weights_round_trip(ctx):
     assert np.array_equal(got.imag, W.imag.astype(np.float32).astype(np.float64))
 
 
-def test_gradients_match_oracle(ctx):
+@pytest.mark.parametrize("channels", [[1, 4, 3, 1], [1, 24, 24, 1]])
+def test_gradients_match_oracle(ctx, channels):
     U = S.gauge_field(DIMS, 0.3, 4)
     ctx.load_gauge(U, DIMS, KAPPA, MU)
-    channels = [1, 4, 3, 1]
     L = len(channels) - 1
     net = tsm.Network(channels, seed=6, init_scale=1.0)
     Ws = _oracle_weights(net)
@@ -104,6 +108,36 @@ def test_pairs_and_loss_match_oracle(ctx):
     want = float(np.mean(want))
     # |dL| <= 2 sqrt(L) |dy| / |t| with |dy| <= 4 L u |y| (L = 2 layers here)
     assert abs(got - want) <= 0.05 * want
+
+
+def test_solve_pairs_are_krylov_residuals(ctx):
+    """Pairs from the method's own solves: for source j and iteration count k,
+    t = x* - x_k with x_k the k-th CGNR iterate from zero and x* the converged
+    solution, r = Dhat t; against the oracle's FP64 CGNR iterates and Schur
+    operator: t to 1e-3 (FP32 iterates and an FP32 x* to 1e-7), r = Dhat t to
+    1e-5 (one FP32 application), and r is the Krylov residual bhat - Dhat x_k
+    up to x*'s tolerance."""
+    dims = (4, 4, 4, 4)
+    U = S.gauge_field(dims, 0.3, 9)
+    ctx.load_gauge(U, dims, KAPPA, MU)
+    net = tsm.Network([1, 4, 1], seed=10, init_scale=0.5)
+    seed, iters = 44, [2, 5]
+    g = net.add_solve_pairs(ctx, 3, seed, iters, tsm.stop(1e-7, 4000, tsm.TSM_F32))
+    shape = (dims[3], dims[2], dims[1], dims[0], 4, 3)
+    for j in range(3):
+        eta = philox.noise(seed, j, dims, 4)
+        bhat = dirac.schur_source(U, eta, dims, KAPPA, MU)
+        xs, _, _ = solver.cgnr(U, bhat, dims, KAPPA, MU, 1e-12, 5000)
+        for q, k in enumerate(iters):
+            xk, it, _ = solver.cgnr(U, bhat, dims, KAPPA, MU, 0.0, k)
+            assert it == k
+            r, t = net.get_pair(g, q * 3 + j, shape)   # one batch of 3 sources: index q * 3 + j
+            t_ref = xs - xk
+            assert _rel(t, t_ref) < 1e-3, (j, k)
+            assert _rel(r, dirac.schur(U, t, dims, KAPPA, MU)) < 1e-5, (j, k)
+            res_k = dirac.even_mask(dims) * (bhat - dirac.schur(U, xk, dims, KAPPA, MU))
+            assert _rel(r, res_k) < 1e-3, (j, k)
+    net.close()
 
 
 def test_training_lowers_heldout_loss(libtsm):
@@ -210,10 +244,12 @@ def test_learned_tsm_unbiased(ctx):
     assert z.max() < 1.0
 
 
-def test_trained_network_cuts_fgmres_iterations(libtsm):
+@pytest.mark.parametrize("pairs", ["noise", "solves"])
+def test_trained_network_cuts_fgmres_iterations(libtsm, pairs):
     """What training gains: on a held-out gauge field, flexible GMRES with the
     trained network needs fewer steps to 1e-6 than with the untrained
-    (near-identity) network, i.e. than plain GMRES."""
+    (near-identity) network, i.e. than plain GMRES; trained on white-noise
+    pairs or on the Krylov residuals of the training fields' own solves."""
     dims = (4, 4, 4, 4)
     stp = tsm.stop(1e-6, 4000, tsm.TSM_F32)
     fg = tsm.stop(1e-6, 400, tsm.TSM_F32, precond=True, restart=20)
@@ -222,7 +258,10 @@ def test_trained_network_cuts_fgmres_iterations(libtsm):
             c.load_gauge(S.gauge_field(dims, 0.3, seed), dims, KAPPA, MU)
         trained = tsm.Network([1, 4, 4, 1], seed=24, init_scale=0.1)
         plain = tsm.Network([1, 4, 4, 1], seed=24, init_scale=0.1)
-        groups = [trained.add_pairs(c, 48, 30 + k, stp) for k, c in enumerate((t1, t2))]
+        if pairs == "noise":
+            groups = [trained.add_pairs(c, 48, 30 + k, stp) for k, c in enumerate((t1, t2))]
+        else:
+            groups = [trained.add_solve_pairs(c, 12, 30 + k, [1, 2, 4, 8], stp) for k, c in enumerate((t1, t2))]
         trained.train(groups, steps=300, batch=4, lr=3e-3)
         b = np.stack([philox.noise(500, j, dims, 4) for j in range(4)])
         its = {}
