@@ -92,7 +92,51 @@ int make_gamma_tab(const int* gammas, int n, GammaTab* tab) {
         return TSM_ERR_ARG;
       }
     }
+    // the contraction kernels take the insertion from its compiled code
+    const uint32_t code = chiral_code(gi);
+    for (int row = 0; row < 4; ++row)
+      if (tab->col[k][row] != (int)(row ^ (code & 3u)) || tab->ph[k][row] != (int)((code >> (2 + 2 * row)) & 3u)) {
+        set_error("insertion %d: compiled chiral code disagrees with the gamma matrices", gi);
+        return TSM_ERR_ARG;
+      }
+    tab->idx[k] = (int8_t)gi;
   }
+  return TSM_OK;
+}
+
+int group_momenta(const int* L, const int* moms, int nq, CtMoments* m) {
+  if (nq < 1 || nq > CT_MAXQ) {
+    set_error("a contraction pass takes 1 to %d momenta", CT_MAXQ);
+    return TSM_ERR_ARG;
+  }
+  *m = CtMoments{};
+  int key[CT_MAXQ][3], neg[CT_MAXQ][3];
+  for (int q = 0; q < nq; ++q)
+    for (int ax = 0; ax < 3; ++ax) {
+      int k = moms[3 * q + ax] % L[ax];
+      if (k < 0) k += L[ax];
+      key[q][ax] = k;
+      neg[q][ax] = (L[ax] - k) % L[ax];
+    }
+  auto same = [](const int* x, const int* y) { return x[0] == y[0] && x[1] == y[1] && x[2] == y[2]; };
+  for (int q = 0; q < nq; ++q) {
+    int cls = -1, sg = 0;
+    for (int j = 0; j < m->ncls && cls < 0; ++j)
+      if (same(key[q], key[m->rep[j]])) cls = j, sg = 1;
+    for (int j = 0; j < m->ncls && cls < 0; ++j)
+      if (same(neg[q], key[m->rep[j]])) cls = j, sg = -1;
+    if (cls < 0) {
+      cls = m->ncls++;
+      m->rep[cls] = (int8_t)q;
+      m->nz[cls] = (int8_t)!(key[q][0] == 0 && key[q][1] == 0 && key[q][2] == 0);
+      m->ch[cls] = (int8_t)m->nch;
+      m->nch += 1 + m->nz[cls];
+      sg = 1;
+    }
+    m->qch[q] = m->ch[cls];
+    m->qsg[q] = (int8_t)(m->nz[cls] ? sg : 0);
+  }
+  m->ncp = (m->nch + 3) & ~3;
   return TSM_OK;
 }
 
@@ -105,6 +149,12 @@ int ContractPlan::prepare(Ctx& c, const int* gammas, int n_gamma, const int* mom
   n_q = n_q_;
   ng = n_gamma;
   const int* L = c.lat.L;
+  passes.clear();
+  for (int q0 = 0; q0 < n_q; q0 += CT_MAXQ) {
+    CtMoments m{};
+    TSM_TRY(group_momenta(L, moms + 3 * q0, std::min(CT_MAXQ, n_q - q0), &m));
+    passes.push_back(m);
+  }
   std::vector<double2> tab((size_t)n_q * (L[0] + L[1] + L[2]));
   const double twopi = 2.0 * std::acos(-1.0);
   size_t off = 0;
@@ -172,6 +222,7 @@ int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint3
       args.b[1] = b ? b->o.as<SB>() : nullptr;
       args.sstride = c.sstride;
       args.gam = plan.gam;
+      args.mom = plan.passes[q0 / CT_MAXQ];
       args.nq = nq;
       args.phx = plan.phx + (size_t)q0 * c.lat.L[0];
       args.phy = plan.phy + (size_t)q0 * c.lat.L[1];

@@ -26,11 +26,45 @@ namespace tsm {
 
 constexpr int CT_MAXG = 16;
 constexpr int CT_MAXQ = 16;
+constexpr int CT_MAXCH = 2 * CT_MAXQ;   // real weight channels of one pass
 
 struct GammaTab {
   int n;                       // insertions in use
   int8_t col[CT_MAXG][4];      // column of the non-zero in row a
   int8_t ph[CT_MAXG][4];       // its value i^ph (0: 1, 1: i, 2: -1, 3: -i)
+  int8_t idx[CT_MAXG];         // which of the 16 chiral-basis insertions (chiral_code)
+};
+
+// The 16 insertions in the chiral basis, each a signed permutation whose
+// non-zero in row a sits in column a ^ m: code bits 0-1 hold the mask m, bits
+// 2 + 2a the power of i of row a's entry.  Order: 1, gamma_1..gamma_4,
+// gamma_5, gamma_mu gamma_5 (mu = 1..4), sigma_{mu nu} = i/2 [gamma_mu,
+// gamma_nu] for (mu, nu) = (1,2), (1,3), (1,4), (2,3), (2,4), (3,4).  The host
+// checks every code against the matrices it builds from the gamma definitions
+// before a contraction runs.
+constexpr uint64_t kChiralCodes0 = 0x035e020b017f0000ull;   // insertions 0-3, 16 bits each
+constexpr uint64_t kChiralCodes1 = 0x0223015702800002ull;   // 4-7
+constexpr uint64_t kChiralCodes2 = 0x01dd0088002a0376ull;   // 8-11
+constexpr uint64_t kChiralCodes3 = 0x00a0035d02a90281ull;   // 12-15
+
+__host__ __device__ constexpr uint32_t chiral_code(int k) {
+  return (uint32_t)(((k < 4 ? kChiralCodes0 : k < 8 ? kChiralCodes1 : k < 12 ? kChiralCodes2 : kChiralCodes3) >>
+                     (16 * (k & 3))) & 0xffffu);
+}
+
+// The momenta of one pass grouped into classes {q, -q} (components mod L):
+// e^{-iqx} = conj(e^{iqx}), so with A = sum_x cos(qx) G(x) and
+// B = sum_x sin(qx) G(x) both members follow as A + i B and A - i B from two
+// real-weighted sums.  Zero momentum has the single weight 1.
+struct CtMoments {
+  int ncls;                    // classes
+  int nch;                     // real weight channels in use
+  int ncp;                     // channels padded to a multiple of 4
+  int8_t rep[CT_MAXQ];         // class -> momentum of the pass whose phase table it uses
+  int8_t ch[CT_MAXQ];          // class -> its cosine channel (sine: ch + 1 when nz)
+  int8_t nz[CT_MAXQ];          // class has a sine channel (non-zero momentum)
+  int8_t qch[CT_MAXQ];         // momentum -> cosine channel of its class
+  int8_t qsg[CT_MAXQ];         // momentum -> +1 / -1 (the class momentum or its negative), 0: zero momentum
 };
 
 template <class SA, class SB>
@@ -44,6 +78,7 @@ struct ContractArgs {
   const typename SB::schunk* wb[2];  // MODE 2: D_W b (when b is given)
   int sstride;
   GammaTab gam;
+  CtMoments mom;
   int nq;
   const double2* phx;   // [nq][Lx]
   const double2* phy;   // [nq][Ly]
@@ -83,24 +118,176 @@ __device__ __forceinline__ cx<R> times_ipow(cx<R> v, int p) {
   }
 }
 
-// sum over the block's sites of phase(q) x density(g): four interleaved
-// accumulators (sites s, s+4, ...) added pairwise at the end, so that the
-// dependent FMA chain is a quarter as long; a fixed order
-template <int NT, class R, int LD>
-__device__ __forceinline__ cx<R> block_phase_sum(const cx<R> (*Ps)[LD], const cx<R> (*Gs)[LD], int q, int gi) {
-  cx<R> a0 = {0, 0}, a1 = {0, 0}, a2 = {0, 0}, a3 = {0, 0};
-#pragma unroll 4
-  for (int s2 = 0; s2 < NT; s2 += 4) {
-    a0 = a0 + Ps[s2][q] * Gs[s2][gi];
-    a1 = a1 + Ps[s2 + 1][q] * Gs[s2 + 1][gi];
-    a2 = a2 + Ps[s2 + 2][q] * Gs[s2 + 2][gi];
-    a3 = a3 + Ps[s2 + 3][q] * Gs[s2 + 3][gi];
+// G_k = Tr[Gamma_k S^T] = sum_a Gamma_k[a][a ^ m_k] S[a][a ^ m_k] for all 16
+// chiral insertions; the loops unroll, so every column and power of i is a
+// constant and each trace is three complex additions
+template <class R>
+__device__ __forceinline__ void chiral_traces(const cx<R> (&S)[4][4], cx<R> (&G)[16]) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const uint32_t code = chiral_code(k);
+    const int m = (int)(code & 3u);
+    cx<R> v = times_ipow(S[0][m], (int)(code >> 2));
+#pragma unroll
+    for (int row = 1; row < 4; ++row) v = v + times_ipow(S[row][row ^ m], (int)(code >> (2 + 2 * row)));
+    G[k] = v;
   }
-  return (a0 + a1) + (a2 + a3);
 }
 
 template <class R> struct ContractNT { static constexpr int value = 128; };
 template <> struct ContractNT<double> { static constexpr int value = 64; };
+
+// Shared memory of a contraction block of NT sites, reused across phases:
+//   stage   Gs[NT][CT_GS] complex (the 16 traces of each site) | Ws[NT][ncp] (weights)
+//   reduce  red[NT][CT_RS] (each thread's tile) | chan[16][CT_CHS] complex (channel sums)
+constexpr int CT_GS = 17;            // complex row stride of Gs (16 + 1: no bank conflicts across sites)
+constexpr int CT_RS = 36;            // row stride of red (32 + 4, rows stay 16-byte aligned)
+constexpr int CT_CHS = CT_MAXCH + 1;
+template <class R, int NT>
+struct CtSmem {
+  static constexpr size_t gs = (size_t)NT * CT_GS * 2 * sizeof(R);
+  static constexpr size_t stage = gs + (size_t)NT * CT_MAXCH * sizeof(R);
+  static constexpr size_t red = (size_t)NT * CT_RS * sizeof(R);
+  static constexpr size_t reduce = red + (size_t)CT_MAXG * CT_CHS * 2 * sizeof(R);
+  static constexpr size_t bytes = stage > reduce ? stage : reduce;
+};
+
+// Stage one site of the block: its 16 traces and its weight channels (cos and
+// sin of each momentum class); sites past the end stage zeros.
+template <class R, int NT, class SA, class SB>
+__device__ __forceinline__ void ct_stage(const ContractArgs<SA, SB>& a, unsigned char* smem, bool valid,
+                                         const cx<R> (&S)[4][4], const int c[4]) {
+  R* gs = reinterpret_cast<R*>(smem) + (size_t)threadIdx.x * CT_GS * 2;
+  R* ws = reinterpret_cast<R*>(smem + CtSmem<R, NT>::gs) + (size_t)threadIdx.x * a.mom.ncp;
+  if (valid) {
+    cx<R> G[16];
+    chiral_traces(S, G);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      gs[2 * k] = G[k].re;
+      gs[2 * k + 1] = G[k].im;
+    }
+    for (int k = 0; k < a.mom.ncls; ++k) {
+      const cx<R> e = phase_at<R>(a, a.mom.rep[k], c);
+      const int ch = a.mom.ch[k];
+      ws[ch] = e.re;
+      if (a.mom.nz[k]) ws[ch + 1] = e.im;
+    }
+    for (int ch = a.mom.nch; ch < a.mom.ncp; ++ch) ws[ch] = (R)0;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) gs[k] = (R)0;
+    for (int ch = 0; ch < a.mom.ncp; ++ch) ws[ch] = (R)0;
+  }
+}
+
+template <class R> struct Vec4;
+template <> struct Vec4<float> {
+  static __device__ __forceinline__ void load(const float* p, float w[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+  }
+};
+template <> struct Vec4<double> {
+  static __device__ __forceinline__ void load(const double* p, double w[4]) {
+    const double2 v0 = reinterpret_cast<const double2*>(p)[0], v1 = reinterpret_cast<const double2*>(p)[1];
+    w[0] = v0.x; w[1] = v0.y; w[2] = v1.x; w[3] = v1.y;
+  }
+};
+template <class R> struct Vec2;
+template <> struct Vec2<float> {
+  static __device__ __forceinline__ cx<float> load(const float* p) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    return {v.x, v.y};
+  }
+};
+template <> struct Vec2<double> {
+  static __device__ __forceinline__ cx<double> load(const double* p) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    return {v.x, v.y};
+  }
+};
+
+// Reduce the staged block (after a __syncthreads) to its partial sums of every
+// requested (insertion, momentum).  Each thread owns a tile of 4 insertions x
+// 4 channels (32 accumulators) over a slice of the block's sites (sites
+// sl, sl + nsl, ...); the slices are then added in slice order in shared
+// memory, and each output is formed from its class's cosine and sine sums
+// (times f when MODE applies a factor).  A fixed order throughout.
+template <class R, int NT, bool FACTOR, class SA, class SB>
+__device__ __forceinline__ void ct_reduce(const ContractArgs<SA, SB>& a, unsigned char* smem, int t, int parity) {
+  const int tid = threadIdx.x;
+  const int ng = a.gam.n, ncp = a.mom.ncp;
+  const int gt_n = (ng + 3) >> 2, ct_n = ncp >> 2, types = gt_n * ct_n;
+  const int nsl = NT / types;
+  const int type = tid % types, sl = tid / types;
+  const bool active = sl < nsl;
+  R acc[4][4][2];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[r][u][0] = acc[r][u][1] = (R)0;
+  if (active) {
+    const R* Gs = reinterpret_cast<const R*>(smem);
+    const R* Ws = reinterpret_cast<const R*>(smem + CtSmem<R, NT>::gs);
+    const int gt = type % gt_n, ct = type / gt_n;
+    int go[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int gi = 4 * gt + r;
+      go[r] = 2 * (gi < ng ? (int)a.gam.idx[gi] : 0);
+    }
+    for (int s = sl; s < NT; s += nsl) {
+      const R* grow = Gs + (size_t)s * CT_GS * 2;
+      cx<R> gv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) gv[r] = Vec2<R>::load(grow + go[r]);
+      R w[4];
+      Vec4<R>::load(Ws + (size_t)s * ncp + 4 * ct, w);
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          acc[r][u][0] = fma(w[u], gv[r].re, acc[r][u][0]);
+          acc[r][u][1] = fma(w[u], gv[r].im, acc[r][u][1]);
+        }
+    }
+  }
+  __syncthreads();   // the staged block is consumed
+  R* red = reinterpret_cast<R*>(smem);
+  R* chan = reinterpret_cast<R*>(smem + CtSmem<R, NT>::red);   // [16][CT_CHS] complex
+  if (active) {
+    R* row = red + (size_t)tid * CT_RS;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        row[(r * 4 + u) * 2] = acc[r][u][0];
+        row[(r * 4 + u) * 2 + 1] = acc[r][u][1];
+      }
+  }
+  __syncthreads();
+  for (int x = tid; x < types * 32; x += NT) {
+    const int ty = x >> 5, e = x & 31;
+    R sum = (R)0;
+    for (int s2 = 0; s2 < nsl; ++s2) sum += red[(size_t)(s2 * types + ty) * CT_RS + e];
+    const int gi = 4 * (ty % gt_n) + (e >> 3), ch = 4 * (ty / gt_n) + ((e >> 1) & 3);
+    if (gi < ng) chan[(gi * CT_CHS + ch) * 2 + (e & 1)] = sum;
+  }
+  __syncthreads();
+  const int nout = ng * a.nq;
+  double2* dst = a.partial + ((size_t)(t * 2 + parity) * a.nbx + blockIdx.x) * nout;
+  for (int k = tid; k < nout; k += NT) {
+    const int gi = k % ng, q = k / ng;
+    const R* cs = chan + (gi * CT_CHS + a.mom.qch[q]) * 2;
+    cx<R> v = {cs[0], cs[1]};
+    const int sg = a.mom.qsg[q];
+    if (sg > 0) v = {cs[0] - cs[3], cs[1] + cs[2]};         // A + i B
+    else if (sg < 0) v = {cs[0] + cs[3], cs[1] - cs[2]};    // A - i B
+    if constexpr (FACTOR) v = (sizeof(R) == 4 ? cx<R>{(R)a.ffre, (R)a.ffim} : cx<R>{(R)a.fre, (R)a.fim}) * v;
+    dst[k] = make_double2((double)v.re, (double)v.im);
+  }
+}
 
 enum { CT_STANDARD = 0, CT_ONE_END = 1, CT_GEN_ONE_END = 2 };
 
@@ -108,17 +295,16 @@ template <class R, class SA, class SB, int MODE>
 __global__ void __launch_bounds__(ContractNT<R>::value) contract_kernel(const ContractArgs<SA, SB> a) {
   constexpr bool OE = MODE == CT_ONE_END;
   constexpr int NT = ContractNT<R>::value;
-  __shared__ cx<R> Gs[NT][CT_MAXG + 1];
-  __shared__ cx<R> Ps[NT][CT_MAXQ + 1];
+  __shared__ __align__(16) unsigned char smem[CtSmem<R, NT>::bytes];
   const int t = blockIdx.y, parity = blockIdx.z;
   const int vs2 = a.g.L[0] * a.g.L[1] * a.g.L[2] / 2;
   const int local = blockIdx.x * NT + threadIdx.x;
-  const int ng = a.gam.n, nq = a.nq;
-  if (local < vs2) {
+  const bool valid = local < vs2;
+  cx<R> S[4][4];
+  int c[4] = {0, 0, 0, 0};
+  if (valid) {
     const int ih = t * vs2 + local;
-    int c[4];
     site_coords(a.g, parity, ih, c);
-    cx<R> S[4][4];
     if constexpr (MODE == CT_GEN_ONE_END) {
       cx<typename SA::real> va[12], wa[12];
       load_spinor<SA>(a.a[parity], a.sstride, ih, va);
@@ -232,38 +418,10 @@ __global__ void __launch_bounds__(ContractNT<R>::value) contract_kernel(const Co
         S[3][y] = (R)(-1) * S[3][y];
       }
     }
-    for (int k = 0; k < ng; ++k) {
-      cx<R> v = {0, 0};
-#pragma unroll
-      for (int row = 0; row < 4; ++row) {
-        const int col = a.gam.col[k][row];
-        cx<R> sv;
-        switch (col) {   // keep S in registers: no dynamic indexing
-          case 0: sv = S[row][0]; break;
-          case 1: sv = S[row][1]; break;
-          case 2: sv = S[row][2]; break;
-          default: sv = S[row][3]; break;
-        }
-        v = v + times_ipow(sv, a.gam.ph[k][row]);
-      }
-      if constexpr (MODE != CT_STANDARD)
-        v = (sizeof(R) == 4 ? cx<R>{(R)a.ffre, (R)a.ffim} : cx<R>{(R)a.fre, (R)a.fim}) * v;
-      Gs[threadIdx.x][k] = v;
-    }
-    for (int q = 0; q < nq; ++q) Ps[threadIdx.x][q] = phase_at<R>(a, q, c);
-  } else {
-    for (int k = 0; k < ng; ++k) Gs[threadIdx.x][k] = {0, 0};
-    for (int q = 0; q < nq; ++q) Ps[threadIdx.x][q] = {0, 0};
   }
+  ct_stage<R, NT>(a, smem, valid, S, c);
   __syncthreads();
-  // one (g, q) output per thread: sum over the block's sites in site order
-  const int nout = ng * nq;
-  double2* dst = a.partial + ((size_t)(t * 2 + parity) * a.nbx + blockIdx.x) * nout;
-  for (int k = threadIdx.x; k < nout; k += NT) {
-    const int gi = k % ng, q = k / ng;
-    const cx<R> acc = block_phase_sum<NT>(Ps, Gs, q, gi);
-    dst[k] = make_double2((double)acc.re, (double)acc.im);
-  }
+  ct_reduce<R, NT, MODE != CT_STANDARD>(a, smem, t, parity);
 }
 
 // ---------------------------------------------------------------- one-derivative insertions
@@ -318,16 +476,16 @@ template <class R, class SA, class SB, class LS>
 __global__ void __launch_bounds__(ContractNT<R>::value) deriv_contract_kernel(const DerivArgs<SA, SB, LS> d) {
   constexpr int NT = ContractNT<R>::value;
   const ContractArgs<SA, SB>& a = d.base;
-  __shared__ cx<R> Gs[NT][CT_MAXG + 1];
-  __shared__ cx<R> Ps[NT][CT_MAXQ + 1];
+  __shared__ __align__(16) unsigned char smem[CtSmem<R, NT>::bytes];
   const int t = blockIdx.y, parity = blockIdx.z;
   const int vs2 = a.g.L[0] * a.g.L[1] * a.g.L[2] / 2;
   const int local = blockIdx.x * NT + threadIdx.x;
-  const int ng = a.gam.n, nq = a.nq;
+  const bool valid = local < vs2;
   const int mu = d.mu;
-  if (local < vs2) {
+  cx<R> S[4][4];
+  int c[4] = {0, 0, 0, 0};
+  if (valid) {
     const int ih = t * vs2 + local;
-    int c[4];
     site_coords(a.g, parity, ih, c);
     const Geom& g = a.g;
     const uint32_t lex = (uint32_t)(((c[3] * g.L[2] + c[2]) * g.L[1] + c[1]) * g.L[0] + c[0]);
@@ -372,7 +530,6 @@ __global__ void __launch_bounds__(ContractNT<R>::value) deriv_contract_kernel(co
     colour_mul<true>(ub, f, sb, tmp);
 #pragma unroll
     for (int k = 0; k < 12; ++k) de[k] = de[k] - tmp[k];
-    cx<R> S[4][4];
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -383,35 +540,10 @@ __global__ void __launch_bounds__(ContractNT<R>::value) deriv_contract_kernel(co
           acc = acc + cjmul(eta[3 * x + cc], ds[3 * y + cc]) - cjmul(de[3 * x + cc], s[3 * y + cc]);
         S[x][y] = (R)0.25 * acc;
       }
-    for (int k = 0; k < ng; ++k) {
-      cx<R> v = {0, 0};
-#pragma unroll
-      for (int row = 0; row < 4; ++row) {
-        const int col = a.gam.col[k][row];
-        cx<R> sv;
-        switch (col) {
-          case 0: sv = S[row][0]; break;
-          case 1: sv = S[row][1]; break;
-          case 2: sv = S[row][2]; break;
-          default: sv = S[row][3]; break;
-        }
-        v = v + times_ipow(sv, a.gam.ph[k][row]);
-      }
-      Gs[threadIdx.x][k] = v;
-    }
-    for (int q = 0; q < nq; ++q) Ps[threadIdx.x][q] = phase_at<R>(a, q, c);
-  } else {
-    for (int k = 0; k < ng; ++k) Gs[threadIdx.x][k] = {0, 0};
-    for (int q = 0; q < nq; ++q) Ps[threadIdx.x][q] = {0, 0};
   }
+  ct_stage<R, NT>(a, smem, valid, S, c);
   __syncthreads();
-  const int nout = ng * nq;
-  double2* dst = a.partial + ((size_t)(t * 2 + parity) * a.nbx + blockIdx.x) * nout;
-  for (int k = threadIdx.x; k < nout; k += NT) {
-    const int gi = k % ng, q = k / ng;
-    const cx<R> acc = block_phase_sum<NT>(Ps, Gs, q, gi);
-    dst[k] = make_double2((double)acc.re, (double)acc.im);
-  }
+  ct_reduce<R, NT, false>(a, smem, t, parity);
 }
 
 // sum the block partials of one timeslice in fixed order into the output

@@ -19,6 +19,7 @@ struct ContractPlan {
                                   // 2: generalised one-end trick (Eq. 2.6): 2 s^dag g5 Gamma g5 D_W s
   int local = 1;                  // the local block (standard or one-end values)
   int deriv_mask = 0;             // bit mu: one-derivative insertion block along mu (standard estimator)
+  std::vector<CtMoments> passes;  // the momenta of each pass of at most CT_MAXQ, in +-q classes
   int prepare(Ctx& c, const int* gammas, int n_gamma, const int* moms, int n_q);
   int blocks() const {
     int n = local;
@@ -31,6 +32,8 @@ struct ContractPlan {
 };
 
 int make_gamma_tab(const int* gammas, int n, GammaTab* tab);
+// group nq momenta (integer n, 3 per momentum) of one pass into +-q classes on an L lattice
+int group_momenta(const int* L, const int* moms, int nq, CtMoments* m);
 NoiseSpec make_noise(uint64_t seed, int kind);
 
 // out[g][q][t] (device, complex) = sum_t-slice e^{iqx} eta^dag Gamma_g (a - b), or
