@@ -218,7 +218,7 @@ int prepare_run(Ctx& c, const tsm_params* p, TsmRun* run, bool branch = false) {
   }
   run->n_hp = (int)(p->hp_end - p->hp_begin);
   run->n_lp = (int)(p->lp_end - p->lp_begin);
-  run->sp_lp = solution_prec(p->lp);
+  run->sp_lp = loop_solution_prec(p->lp);
   run->sp_hp = solution_prec(p->hp);
   run->fp64_path = (p->lp.prec == TSM_F64 && p->hp.prec == TSM_F64);
   run->ns = make_noise(p->seed, p->noise);
@@ -236,7 +236,7 @@ int prepare_run(Ctx& c, const tsm_params* p, TsmRun* run, bool branch = false) {
   TSM_TRY(eo_fields(c, "tsm_s_lp", run->sp_lp, &run->s_lp, c.batch_cap));
   TSM_TRY(eo_fields(c, "tsm_b_hp", run->sp_hp, &run->b_hp, c.batch_cap));
   TSM_TRY(eo_fields(c, "tsm_s_hp", run->sp_hp, &run->s_hp, c.batch_cap));
-  TSM_TRY(reserve_solver(c, p->lp));
+  TSM_TRY(reserve_solver(c, p->lp, run->sp_lp));
   TSM_TRY(reserve_solver(c, p->hp));
   TSM_TRY(reserve_contract(c));
   run->branch = branch && run->n_hp > 0 && run->n_lp > 0;
@@ -245,7 +245,7 @@ int prepare_run(Ctx& c, const tsm_params* p, TsmRun* run, bool branch = false) {
     c.ws_prefix = "branch1/";
     int rc = eo_fields(c, "tsm_b_lp", run->sp_lp, &run->b_lp1, c.batch_cap);
     if (rc == TSM_OK) rc = eo_fields(c, "tsm_s_lp", run->sp_lp, &run->s_lp1, c.batch_cap);
-    if (rc == TSM_OK) rc = reserve_solver(c, p->lp);
+    if (rc == TSM_OK) rc = reserve_solver(c, p->lp, run->sp_lp);
     if (rc == TSM_OK) rc = reserve_contract(c);
     c.ws_prefix.clear();
     TSM_TRY(rc);
@@ -297,11 +297,15 @@ int record_run(Ctx& c, const tsm_params* p, TsmRun& run, tsm_loop_stats* st) {
       }
     }
     if (run.fp64_path) return launch_contract<double, F64, F64>(c, plan, ns, j, a, b, out, pwa, pwb);
-    if (pa == TSM_F64 && (b == nullptr || pb == TSM_F64))
-      return launch_contract<float, F64, F64>(c, plan, ns, j, a, b, out, pwa, pwb);
-    if (pa == TSM_F64) return launch_contract<float, F64, F32>(c, plan, ns, j, a, b, out, pwa, pwb);
-    if (b == nullptr || pb == TSM_F32) return launch_contract<float, F32, F32>(c, plan, ns, j, a, b, out, pwa, pwb);
-    return launch_contract<float, F32, F64>(c, plan, ns, j, a, b, out, pwa, pwb);
+    if (b == nullptr) pb = pa;
+    if (pa == TSM_F64 && pb == TSM_F64) return launch_contract<float, F64, F64>(c, plan, ns, j, a, b, out, pwa, pwb);
+    if (pa == TSM_F64 && pb == TSM_F32) return launch_contract<float, F64, F32>(c, plan, ns, j, a, b, out, pwa, pwb);
+    if (pa == TSM_F64 && pb == TSM_F16) return launch_contract<float, F64, F16>(c, plan, ns, j, a, b, out, pwa, pwb);
+    if (pa == TSM_F32 && pb == TSM_F32) return launch_contract<float, F32, F32>(c, plan, ns, j, a, b, out, pwa, pwb);
+    if (pa == TSM_F32 && pb == TSM_F64) return launch_contract<float, F32, F64>(c, plan, ns, j, a, b, out, pwa, pwb);
+    if (pa == TSM_F32 && pb == TSM_F16) return launch_contract<float, F32, F16>(c, plan, ns, j, a, b, out, pwa, pwb);
+    if (pa == TSM_F16 && pb == TSM_F16) return launch_contract<float, F16, F16>(c, plan, ns, j, a, b, out, pwa, pwb);
+    return bad(TSM_ERR_ARG, "no contraction for these field tiers");
   };
   // value of source j for set 0 (HP-set corrections) or 1 (LP set), idx-th of its set
   auto contract = [&](uint32_t j, EOField a, int pa, const EOField* b, int pb, int set, int idx) -> int {
@@ -309,11 +313,15 @@ int record_run(Ctx& c, const tsm_params* p, TsmRun& run, tsm_loop_stats* st) {
     FftProjector& f = run.fftp;
     const GammaTab& gam = run.plan.gam;
     if (run.fp64_path) return f.accumulate<double, F64, F64>(c, gam, ns, j, a, b, set, idx + 1);
-    if (pa == TSM_F64 && (b == nullptr || pb == TSM_F64))
-      return f.accumulate<float, F64, F64>(c, gam, ns, j, a, b, set, idx + 1);
-    if (pa == TSM_F64) return f.accumulate<float, F64, F32>(c, gam, ns, j, a, b, set, idx + 1);
-    if (b == nullptr || pb == TSM_F32) return f.accumulate<float, F32, F32>(c, gam, ns, j, a, b, set, idx + 1);
-    return f.accumulate<float, F32, F64>(c, gam, ns, j, a, b, set, idx + 1);
+    if (b == nullptr) pb = pa;
+    if (pa == TSM_F64 && pb == TSM_F64) return f.accumulate<float, F64, F64>(c, gam, ns, j, a, b, set, idx + 1);
+    if (pa == TSM_F64 && pb == TSM_F32) return f.accumulate<float, F64, F32>(c, gam, ns, j, a, b, set, idx + 1);
+    if (pa == TSM_F64 && pb == TSM_F16) return f.accumulate<float, F64, F16>(c, gam, ns, j, a, b, set, idx + 1);
+    if (pa == TSM_F32 && pb == TSM_F32) return f.accumulate<float, F32, F32>(c, gam, ns, j, a, b, set, idx + 1);
+    if (pa == TSM_F32 && pb == TSM_F64) return f.accumulate<float, F32, F64>(c, gam, ns, j, a, b, set, idx + 1);
+    if (pa == TSM_F32 && pb == TSM_F16) return f.accumulate<float, F32, F16>(c, gam, ns, j, a, b, set, idx + 1);
+    if (pa == TSM_F16 && pb == TSM_F16) return f.accumulate<float, F16, F16>(c, gam, ns, j, a, b, set, idx + 1);
+    return bad(TSM_ERR_ARG, "no momentum projection for these field tiers");
   };
   // state slots: fixed in eager mode, one fresh range per solve under capture
   auto slots = [&](int n, std::vector<std::pair<int, int>>& log) {
@@ -341,7 +349,8 @@ int record_run(Ctx& c, const tsm_params* p, TsmRun& run, tsm_loop_stats* st) {
     for (uint32_t j0 = p->lp_begin; j0 < p->lp_end && rc == TSM_OK; j0 += B) {
       const int n = (int)std::min<uint32_t>(B, p->lp_end - j0);
       rc = gen(sp_lp, j0, run.b_lp1, n);
-      if (rc == TSM_OK) rc = solve_batch(c, p->lp, slots(n, c.cap_lp), n, run.b_lp1, run.s_lp1, r_lp.data());
+      if (rc == TSM_OK)
+        rc = solve_batch(c, p->lp, slots(n, c.cap_lp), n, run.b_lp1, run.s_lp1, r_lp.data(), nullptr, -1, sp_lp);
       for (int r = 0; r < n && rc == TSM_OK; ++r)
         rc = contract(j0 + r, eo_at(run.s_lp1, sp_lp, c.g.Vh, r), sp_lp, nullptr, sp_lp, 1,
                       (int)(j0 + r - p->lp_begin));
@@ -357,14 +366,14 @@ int record_run(Ctx& c, const tsm_params* p, TsmRun& run, tsm_loop_stats* st) {
   for (uint32_t j0 = p->hp_begin; j0 < p->hp_end; j0 += B) {
     const int n = (int)std::min<uint32_t>(B, p->hp_end - j0);
     TSM_TRY(gen(sp_lp, j0, run.b_lp, n));
-    TSM_TRY(solve_batch(c, p->lp, slots(n, c.cap_lp), n, run.b_lp, run.s_lp, r_lp.data()));
+    TSM_TRY(solve_batch(c, p->lp, slots(n, c.cap_lp), n, run.b_lp, run.s_lp, r_lp.data(), nullptr, -1, sp_lp));
     if (sp_hp != sp_lp) TSM_TRY(gen(sp_hp, j0, run.b_hp, n));
     EOField bh = (sp_hp != sp_lp) ? run.b_hp : run.b_lp;
     // optional warm start of the HP solves from the LP solutions (the LP map
     // itself is untouched, so both sets keep the same LP solver)
     const bool warm = p->hp_warm_start && p->hp.prec == TSM_F32 && p->hp.reliable && !p->hp.precond;
     TSM_TRY(solve_batch(c, p->hp, slots(n, c.cap_hp), n, bh, run.s_hp, r_hp.data(), warm ? &run.s_lp.e : nullptr,
-                        solution_prec(p->lp)));
+                        sp_lp));
     for (int r = 0; r < n; ++r) {
       if (!c.capturing) {
         if (r_lp[r].status != TSM_OK || r_hp[r].status != TSM_OK) return bad(TSM_ERR_NONFINITE, "NaN/Inf in a solve");
@@ -387,7 +396,7 @@ int record_run(Ctx& c, const tsm_params* p, TsmRun& run, tsm_loop_stats* st) {
     for (uint32_t j0 = p->lp_begin; j0 < p->lp_end; j0 += B) {
       const int n = (int)std::min<uint32_t>(B, p->lp_end - j0);
       TSM_TRY(gen(sp_lp, j0, bl, n));
-      TSM_TRY(solve_batch(c, p->lp, slots(n, c.cap_lp), n, bl, sl, r_lp.data()));
+      TSM_TRY(solve_batch(c, p->lp, slots(n, c.cap_lp), n, bl, sl, r_lp.data(), nullptr, -1, sp_lp));
       for (int r = 0; r < n; ++r) {
         if (!c.capturing) {
           if (r_lp[r].status != TSM_OK) return bad(TSM_ERR_NONFINITE, "NaN/Inf in a solve");
@@ -979,12 +988,12 @@ int tsm_tune(tsm_ctx* h, const tm_stop* stop, int* best_batch, int* best_tile, d
     if (tiled) c.tile_rpb[stop->prec] = it->second;
     return TSM_OK;
   }
-  const int sp = solution_prec(*stop);
+  const int sp = loop_solution_prec(*stop);   // the solves of the loop estimators
   c.batch_cap = std::max(c.batch_cap, cand[3]);
   EOField fb, fs;
   TSM_TRY(eo_fields(c, "tune_b", sp, &fb, c.batch_cap));
   TSM_TRY(eo_fields(c, "tune_s", sp, &fs, c.batch_cap));
-  TSM_TRY(reserve_solver(c, *stop));
+  TSM_TRY(reserve_solver(c, *stop, sp));
   const NoiseSpec ns = make_noise(0x7475ull, 4);   // scratch sources, not part of any estimate
   cudaEvent_t e0, e1;
   TSM_CUDA(cudaEventCreate(&e0));
@@ -1004,10 +1013,10 @@ int tsm_tune(tsm_ctx* h, const tm_stop* stop, int* best_batch, int* best_tile, d
     for (int q = 0; q < ntile && rc == TSM_OK; ++q) {
       if (tiled) c.tile_rpb[stop->prec] = tiles[q];
       // one untimed solve to settle caches and clocks, then one timed
-      rc = solve_batch(c, *stop, 0, w, fb, fs, res.data());
+      rc = solve_batch(c, *stop, 0, w, fb, fs, res.data(), nullptr, -1, sp);
       if (rc != TSM_OK) break;
       if (cudaEventRecord(e0, c.stream) != cudaSuccess) rc = TSM_ERR_CUDA;
-      if (rc == TSM_OK) rc = solve_batch(c, *stop, 0, w, fb, fs, res.data());
+      if (rc == TSM_OK) rc = solve_batch(c, *stop, 0, w, fb, fs, res.data(), nullptr, -1, sp);
       if (rc == TSM_OK && cudaEventRecord(e1, c.stream) != cudaSuccess) rc = TSM_ERR_CUDA;
       if (rc == TSM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = TSM_ERR_CUDA;
       float ms = 0.f;

@@ -294,6 +294,12 @@ template int launch_contract<double, F64, F32>(Ctx&, const ContractPlan&, const 
                                                const EOField*, double2*, const EOField*, const EOField*);
 template int launch_contract<float, F32, F64>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
                                               const EOField*, double2*, const EOField*, const EOField*);
+template int launch_contract<float, F64, F16>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
+                                              const EOField*, double2*, const EOField*, const EOField*);
+template int launch_contract<float, F32, F16>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
+                                              const EOField*, double2*, const EOField*, const EOField*);
+template int launch_contract<float, F16, F16>(Ctx&, const ContractPlan&, const NoiseSpec&, uint32_t, EOField,
+                                              const EOField*, double2*, const EOField*, const EOField*);
 
 int apply_wilson(Ctx& c, int prec, EOField in, EOField out) {
   return dispatch_prec(prec, [&](auto tag) -> int {

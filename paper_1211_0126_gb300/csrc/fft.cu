@@ -671,6 +671,9 @@ TSM_FFT_INST(float, F64, F64)
 TSM_FFT_INST(float, F32, F32)
 TSM_FFT_INST(float, F64, F32)
 TSM_FFT_INST(float, F32, F64)
+TSM_FFT_INST(float, F64, F16)
+TSM_FFT_INST(float, F32, F16)
+TSM_FFT_INST(float, F16, F16)
 #undef TSM_FFT_INST
 
 }  // namespace tsm

@@ -38,6 +38,11 @@ int solution_prec(const tm_stop& stop) {
   return TSM_F32;
 }
 
+int loop_solution_prec(const tm_stop& stop) {
+  if (stop.prec == TSM_F16 && !stop.precond) return TSM_F16;
+  return solution_prec(stop);
+}
+
 static int read_states(Ctx& c, int s0, int n, std::vector<CGState>& out) {
   TSM_CUDA(cudaMemcpyAsync(c.h_states + s0, c.states + s0, n * sizeof(CGState), cudaMemcpyDeviceToHost, c.stream));
   TSM_CUDA(cudaStreamSynchronize(c.stream));
@@ -256,6 +261,7 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
       // update's mixed precision, p = r; a source whose start already meets
       // the stopping rule stops here (rel_finish_kernel)
       if (x0_prec == TSM_F64) TSM_TRY((launch_convert<F64, F64>(c, *x0, x64, nullptr, nrhs)));
+      else if (x0_prec == TSM_F16) TSM_TRY((launch_convert<F16, F64>(c, *x0, x64, nullptr, nrhs)));
       else TSM_TRY((launch_convert<F32, F64>(c, *x0, x64, nullptr, nrhs)));
       warm_start_kernel<<<1, Ctx::kMaxBatch, 0, c.stream>>>(st, nrhs);
       c.launches++;
@@ -411,13 +417,14 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
 
 // allocate every field cg_solve uses for this tier (batch width c.batch_cap),
 // so that a later solve makes no allocation (required under stream capture)
-int reserve_solver(Ctx& c, const tm_stop& stop) {
+int reserve_solver(Ctx& c, const tm_stop& stop, int sol_prec) {
   int pS, pA, pP;
   switch (stop.prec) {
     case TSM_F64: pS = pA = pP = TSM_F64; break;
     case TSM_F32: pS = pA = TSM_F32; pP = stop.reliable ? TSM_F64 : TSM_F32; break;
     default: pS = stop.prec; pA = stop.prec == TSM_F16 ? TSM_F16 : TSM_F32; pP = TSM_F32; break;
   }
+  if (stop.prec == TSM_F16 && sol_prec == TSM_F16) pP = TSM_F16;
   const int nb = c.batch_cap;
   PField f;
   for (const char* name : {"cg_tmp_o", "cg_bhat", "cg_w0", "cg_t0", "cg_r0"}) TSM_TRY(c.field(name, pP, &f, nb));
@@ -431,7 +438,11 @@ int reserve_solver(Ctx& c, const tm_stop& stop) {
 }
 
 int solve_batch(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EOField s, SolveResult* res,
-                const PField* x0, int x0_prec) {
+                const PField* x0, int x0_prec, int sol_prec) {
+  if (sol_prec >= 0 && sol_prec != solution_prec(stop) && !(stop.prec == TSM_F16 && sol_prec == TSM_F16)) {
+    set_error("solution storage tier %d not available for solver tier %d", sol_prec, stop.prec);
+    return TSM_ERR_ARG;
+  }
   if (stop.precond) return fgmres_batch(c, stop, nrhs, b, s, res);
   if (nrhs < 1 || nrhs > c.batch_cap || s0 < 0 || s0 + nrhs > Ctx::kMaxStates - 4) {
     set_error("batch of %d right-hand sides at state %d exceeds the capacity (%d)", nrhs, s0, c.batch_cap);
@@ -441,16 +452,19 @@ int solve_batch(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EOFiel
     case TSM_F64: return cg_solve<F64, F64, F64, false>(c, stop, s0, nrhs, b, s, res, nullptr, -1);
     case TSM_F32:
       if (stop.reliable) {
-        if (x0 != nullptr && x0_prec != TSM_F32 && x0_prec != TSM_F64) {
-          set_error("starting guess of tier %d (FP32 or FP64 expected)", x0_prec);
+        if (x0 != nullptr && x0_prec != TSM_F16 && x0_prec != TSM_F32 && x0_prec != TSM_F64) {
+          set_error("starting guess of tier %d (FP16, FP32 or FP64 expected)", x0_prec);
           return TSM_ERR_ARG;
         }
         return cg_solve<F32, F32, F64, true>(c, stop, s0, nrhs, b, s, res, x0, x0_prec);
       }
       return cg_solve<F32, F32, F32, false>(c, stop, s0, nrhs, b, s, res, nullptr, -1);
     // FP16 tier: r and x in FP16 too (relative storage precision 2^-11, an order
-    // below the LP truncation; the memory-bound CG update moves 36 % fewer bytes)
-    case TSM_F16: return cg_solve<F16, F16, F32, false>(c, stop, s0, nrhs, b, s, res, nullptr, -1);
+    // below the LP truncation; the memory-bound CG update moves 36 % fewer bytes);
+    // source and solution in FP16 too when the caller asks for it
+    case TSM_F16:
+      if (sol_prec == TSM_F16) return cg_solve<F16, F16, F16, false>(c, stop, s0, nrhs, b, s, res, nullptr, -1);
+      return cg_solve<F16, F16, F32, false>(c, stop, s0, nrhs, b, s, res, nullptr, -1);
     case TSM_BF16: return cg_solve<BF16, F32, F32, false>(c, stop, s0, nrhs, b, s, res, nullptr, -1);
     default: set_error("unknown solver tier %d", stop.prec); return TSM_ERR_ARG;
   }

@@ -18,19 +18,29 @@ struct SolveResult {
 // tier and for FP32 with FP64 reliable updates, FP32 otherwise.
 int solution_prec(const tm_stop& stop);
 
-// Solve D_tm s_r = b_r for nrhs independent sources at once.  b and s are
-// batches of nrhs contiguous even/odd fields of tier solution_prec(stop) laid
-// out for c.batch_cap sources; device solver states s0 .. s0+nrhs-1 are used;
-// res receives nrhs results.  x0 (optional; FP32 with FP64 reliable updates
-// only, ignored by the other tiers): a batch of even-site starting guesses of
-// storage tier x0_prec (TSM_F32 or TSM_F64); the first iterate's residual is
-// then the true normal residual of b - D x0, computed as in a reliable update,
-// and the stopping rule stays relative to ||Dhat^dag bhat||.
-int solve_batch(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EOField s, SolveResult* res,
-                const PField* x0 = nullptr, int x0_prec = -1);
+// Storage tier of the sources and solutions of the solves inside the loop
+// estimators: as solution_prec, except that the FP16 tier (whose iterates x
+// and r are FP16 already) keeps its noise source, Schur source and solution in
+// FP16 as well, so that its source preparation, odd reconstruction and
+// contraction move 16-bit fields through the link-sharing stencil.
+int loop_solution_prec(const tm_stop& stop);
 
-// Allocate the solver workspace of a tier for c.batch_cap sources in advance.
-int reserve_solver(Ctx& c, const tm_stop& stop);
+// Solve D_tm s_r = b_r for nrhs independent sources at once.  b and s are
+// batches of nrhs contiguous even/odd fields of tier sol_prec (-1:
+// solution_prec(stop); otherwise solution_prec(stop) or, for the FP16 tier,
+// TSM_F16) laid out for c.batch_cap sources; device solver states s0 ..
+// s0+nrhs-1 are used; res receives nrhs results.  x0 (optional; FP32 with FP64
+// reliable updates only, ignored by the other tiers): a batch of even-site
+// starting guesses of storage tier x0_prec (TSM_F16, TSM_F32 or TSM_F64); the
+// first iterate's residual is then the true normal residual of b - D x0,
+// computed as in a reliable update, and the stopping rule stays relative to
+// ||Dhat^dag bhat||.
+int solve_batch(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EOField s, SolveResult* res,
+                const PField* x0 = nullptr, int x0_prec = -1, int sol_prec = -1);
+
+// Allocate the solver workspace of a tier for c.batch_cap sources in advance
+// (source / solution storage sol_prec as in solve_batch).
+int reserve_solver(Ctx& c, const tm_stop& stop, int sol_prec = -1);
 
 // ||b - D_tm s|| / ||b|| in FP64 (fields of tier prec).
 int true_residual(Ctx& c, int prec, EOField b, EOField s, double* out);
