@@ -146,6 +146,15 @@ inline Twist twist_Ainv(double kappa, double m) {
   const double d = 1.0 + 4.0 * kappa * kappa * m * m;
   return Twist{{1.0 / d, 1.0 / d}, {-2.0 * kappa * m / d, 2.0 * kappa * m / d}};
 }
+// the product of two twists (they commute: both are diagonal)
+inline Twist twist_mul(const Twist& a, const Twist& b) {
+  Twist t;
+  for (int q = 0; q < 2; ++q) {
+    t.re[q] = a.re[q] * b.re[q] - a.im[q] * b.im[q];
+    t.im[q] = a.re[q] * b.im[q] + a.im[q] * b.re[q];
+  }
+  return t;
+}
 
 // ---- launch helpers (instantiated per storage type in ops_*.cu).  Batched
 // helpers take nrhs right-hand sides stored as contiguous parity fields (the

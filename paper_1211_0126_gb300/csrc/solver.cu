@@ -23,6 +23,7 @@
 // depend on the others, so a batched solve gives the same bits as a
 // single-source one.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <vector>
 
@@ -201,22 +202,26 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
   CGState* st = c.states + s0;
   const int pS = S::id, pA = SA::id, pP = SP::id;
   const int nb = c.batch_cap;
+  // DIRECT: r and x share the solution's storage tier, so D-hat^dag bhat is
+  // written straight into r and x accumulates in the even half of s (no copies)
+  constexpr bool DIRECT = !REL && std::is_same<SA, SP>::value;
   PField tmp_o, bhat, w0, t0, r0;
   TSM_TRY(c.field("cg_tmp_o", pP, &tmp_o, nb));
-  TSM_TRY(c.field("cg_bhat", pP, &bhat, nb));
   TSM_TRY(c.field("cg_w0", pP, &w0, nb));
   TSM_TRY(c.field("cg_t0", pP, &t0, nb));
-  TSM_TRY(c.field("cg_r0", pP, &r0, nb));
-  // bhat_e = A^-1 (b_e + kappa H_eo A^-1 b_o)
+  // bhat_e = A^-1 (b_e + kappa H_eo A^-1 b_o).  Only the reliable updates use
+  // bhat itself; otherwise the hop writes w0 = A(-mu)^-1 bhat at once (the two
+  // site-local factors multiply to the real 1 / (1 + 4 kappa^2 mu^2))
   TSM_TRY(launch_twist<SP>(c, twist_Ainv(k, mu), b.o, tmp_o, nullptr, nullptr, nrhs));
+  if constexpr (REL) TSM_TRY(c.field("cg_bhat", pP, &bhat, nb));
   {
     HopArgs<SP> h = hop_args<SP>(c, 0);
     h.in = tmp_o.as<SP>();
     h.center = b.e.as<SP>();
     h.ac = 1.0;
     h.ah = k;
-    h.to = twist_Ainv(k, mu);
-    h.out = bhat.as<SP>();
+    h.to = REL ? twist_Ainv(k, mu) : twist_mul(twist_Ainv(k, -mu), twist_Ainv(k, mu));
+    h.out = REL ? bhat.as<SP>() : w0.as<SP>();
     TSM_TRY(launch_hop<SP>(c, h, 0, HOP_CENTER, -1, nrhs));
   }
   // r0 = Dhat^dag bhat, <r0, r0> initialises the states
@@ -225,8 +230,34 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
                                                          delta * delta);
   c.launches++;
   TSM_TRY(check_launch(c, "state_init_kernel"));
-  TSM_TRY(launch_twist<SP>(c, twist_Ainv(k, -mu), bhat, w0, nullptr, nullptr, nrhs));
-  {
+  // r0 is written straight into r when the tiers allow it
+  constexpr bool R0_IN_R = DIRECT || REL;
+  if constexpr (R0_IN_R) TSM_TRY(c.field("cg_r", pA, &r0, nb));
+  else TSM_TRY(c.field("cg_r0", pP, &r0, nb));
+  if constexpr (REL) {
+    // A(-mu)^-1 bhat in FP64, rounded once to FP32, then Dhat^dag in FP32: the
+    // mixed form of the normal residual of every reliable update (x = 0 here)
+    PField u32, t32;
+    TSM_TRY(c.field("rel_u32", TSM_F32, &u32, nb));
+    TSM_TRY(c.field("rel_t32", TSM_F32, &t32, nb));
+    TSM_TRY(launch_twist<SP>(c, twist_Ainv(k, -mu), bhat, w0, nullptr, nullptr, nrhs));
+    TSM_TRY((launch_convert<SP, F32>(c, w0, u32, nullptr, nrhs)));
+    HopArgs<F32> h = hop_args<F32>(c, 1);
+    h.in = u32.as<F32>();
+    h.out = t32.as<F32>();
+    h.to = twist_Ainv(k, -mu);
+    TSM_TRY(launch_hop<F32>(c, h, 1, 0, -1, nrhs));
+    h = hop_args<F32>(c, 0);
+    h.in = t32.as<F32>();
+    h.center = u32.as<F32>();
+    h.tc = twist_A(k, -mu);
+    h.ac = 1.0;
+    h.ah = -k2;
+    h.out = r0.as<F32>();
+    h.st = st;
+    h.post = POST_INIT;
+    TSM_TRY(launch_hop<F32>(c, h, 1, HOP_CENTER | HOP_NORM, -1, nrhs));
+  } else {
     HopArgs<SP> h = hop_args<SP>(c, 1);
     h.in = w0.as<SP>();
     h.out = t0.as<SP>();
@@ -248,9 +279,14 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
   TSM_TRY(c.field("cg_t", pS, &t, nb));
   TSM_TRY(c.field("cg_w", pS, &w, nb));
   TSM_TRY(c.field("cg_r", pA, &r, nb));
-  TSM_TRY(c.field("cg_x", pA, &x, nb));
-  TSM_TRY((launch_convert<SP, SA>(c, r0, r, nullptr, nrhs)));
-  TSM_TRY((launch_convert<SP, S>(c, r0, p, nullptr, nrhs)));
+  if constexpr (DIRECT) x = s.e;
+  else TSM_TRY(c.field("cg_x", pA, &x, nb));
+  if constexpr (R0_IN_R) {
+    TSM_TRY((launch_convert<SA, S>(c, r, p, nullptr, nrhs)));
+  } else {
+    TSM_TRY((launch_convert<SP, SA>(c, r0, r, nullptr, nrhs)));
+    TSM_TRY((launch_convert<SP, S>(c, r0, p, nullptr, nrhs)));
+  }
   TSM_TRY((launch_convert<SA, SA>(c, PField{}, x, nullptr, nrhs)));
   if constexpr (REL) {
     TSM_TRY(c.field("cg_x64", TSM_F64, &x64, nb));
@@ -388,7 +424,7 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
   // solution: even part from CG, odd part reconstructed
   if constexpr (REL) {
     TSM_TRY((launch_convert<F64, SP>(c, x64, s.e, nullptr, nrhs)));
-  } else {
+  } else if constexpr (!DIRECT) {
     TSM_TRY((launch_convert<SA, SP>(c, x, s.e, nullptr, nrhs)));
   }
   {
