@@ -87,6 +87,9 @@ def parse():
     ap.add_argument("--fft-only", action="store_true",
                     help="only run two all-momenta TSM estimates of 64 LP sources (FP16, batch 32) at 24^3x48 (a "
                          "small case for ncu captures of the FFT projection kernels)")
+    ap.add_argument("--contract-only", action="store_true",
+                    help="only run one LP-only TSM estimate of 4 sources (FP16 solves, batch 4) at 24^3x48 with "
+                         "16 Gamma x 7 momenta (a small case for ncu captures of the contraction kernel)")
     ap.add_argument("--dslash-only", default=None,
                     help="comma list of tiers (f64,f32,f16,bf16): only run 3 standalone H_eo launches per tier "
                          "at 24^3x48 (a small case for ncu captures of the hop kernel)")
@@ -144,6 +147,24 @@ def run_lp_only():
     torch.cuda.synchronize()
     print(json.dumps({"lp_only": {"lattice": list(dims), "batch": 32, "iters_mean": float(np.mean(iters)),
                                   "ms": (time.perf_counter() - t0) * 1e3}}), flush=True)
+    ctx.close()
+
+
+def run_contract_only():
+    import torch
+    from paper_1211_0126_gb300 import build, tsm
+    from paper_1211_0126_gb300 import synthetic as S
+    if not os.path.exists(tsm.LIB_PATH):
+        build.build()
+    ctx = tsm.Context(0, torch.cuda.current_stream().cuda_stream)
+    ctx.load_gauge(S.gauge_field(DIMS, EPS, GAUGE_SEED), DIMS, KAPPA, MU)
+    hp = tsm.stop(HP_TOL, HP_MAXIT, tsm.TSM_F32, reliable=True, reliable_delta=RELIABLE_DELTA)
+    lp = tsm.stop(LP_TOL, LP_MAXIT, tsm.TSM_F16)
+    t0 = time.perf_counter()
+    ctx.loops(5, 4, 0, 4, hp, lp, list(range(N_GAMMA)), S.default_momenta(N_Q), batch=4, verify=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"contract_only": {"lattice": list(DIMS), "lp_sources": 4, "n_gamma": N_GAMMA, "n_q": N_Q,
+                                        "ms": (time.perf_counter() - t0) * 1e3}}), flush=True)
     ctx.close()
 
 
@@ -1239,6 +1260,8 @@ def main():
         run_lp_only()
     elif args.fft_only:
         run_fft_only()
+    elif args.contract_only:
+        run_contract_only()
     elif args.dslash_only:
         run_dslash_only(args.dslash_only)
     elif args.workload == "three-lattice":

@@ -317,9 +317,10 @@ int tsm_loops_graph(tsm_ctx** ctxs, const tsm_params* params, int n, double** lo
 int tsm_tune_batch(tsm_ctx* ctx, const tm_stop* stop, int* best, double* times_ms);
 
 /* Autotuner of the whole multi-RHS launch shape: the batch width as above
- * and, for the 16-bit tiers, the sources per block of their link-sharing
- * stencil (blocks of 32 sites x 2, 4 or 8 sources, one warp per source; the
- * block's links are widened once and shared).  Times one batched solve of
+ * and, for the 16-bit tiers and FP32, the sources per block of their
+ * link-sharing stencil (blocks of 32 sites x 2, 4 or 8 sources, one warp per
+ * source; the block's links are widened once and shared; FP32 uses it for its
+ * hops without a reduction).  Times one batched solve of
  * scratch noise sources per (width, block shape) pair and keeps the pair with
  * the lowest time per source: *best_batch, *best_tile (may be NULL; 1 for
  * tiers without that stencil).  The block shape is then used by every later
@@ -332,8 +333,8 @@ int tsm_tune_batch(tsm_ctx* ctx, const tm_stop* stop, int* best, double* times_m
 int tsm_tune(tsm_ctx* ctx, const tm_stop* stop, int* best_batch, int* best_tile, double* times_ms);
 
 /* Set the sources per block (2, 4 or 8) of the link-sharing stencil of tier
- * prec (TSM_F16 or TSM_BF16) for this context's later solves, as tsm_tune
- * does; 4 by default.  TSM_ERR_ARG for other tiers or values. */
+ * prec (TSM_F16, TSM_BF16 or TSM_F32) for this context's later solves, as
+ * tsm_tune does; 4 by default.  TSM_ERR_ARG for other tiers or values. */
 int tsm_set_tile(tsm_ctx* ctx, int prec, int tile_sources);
 
 

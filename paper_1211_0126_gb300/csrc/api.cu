@@ -976,9 +976,9 @@ int tsm_tune(tsm_ctx* h, const tm_stop* stop, int* best_batch, int* best_tile, d
            stop->prec, stop->reliable, stop->rel_tol, stop->max_iter);
   const int cand[4] = {8, 16, 32, 64};
   const int tiles[3] = {2, 4, 8};
-  // the 16-bit tiers' link-sharing stencil has a block shape to choose; the
-  // other tiers run one thread per (source, site)
-  const bool tiled = stop->prec == TSM_F16 || stop->prec == TSM_BF16;
+  // the link-sharing stencil (16-bit tiers; FP32 for its hops without a
+  // reduction) has a block shape to choose; FP64 runs one thread per (source, site)
+  const bool tiled = stop->prec == TSM_F16 || stop->prec == TSM_BF16 || stop->prec == TSM_F32;
   const int ntile = tiled ? 3 : 1;
   auto ib = c.tuned_batch.find(key);
   auto it = c.tuned_rpb.find(key);
@@ -1047,7 +1047,8 @@ int tsm_tune(tsm_ctx* h, const tm_stop* stop, int* best_batch, int* best_tile, d
 
 int tsm_set_tile(tsm_ctx* h, int prec, int tile_sources) {
   if (h == nullptr) return bad(TSM_ERR_ARG, "null context");
-  if (prec != TSM_F16 && prec != TSM_BF16) return bad(TSM_ERR_ARG, "only the 16-bit tiers have a block shape");
+  if (prec != TSM_F16 && prec != TSM_BF16 && prec != TSM_F32)
+    return bad(TSM_ERR_ARG, "the FP64 tier has no link-sharing block shape");
   if (tile_sources != 2 && tile_sources != 4 && tile_sources != 8)
     return bad(TSM_ERR_ARG, "sources per block must be 2, 4 or 8");
   h->c.tile_rpb[prec] = tile_sources;

@@ -475,6 +475,23 @@ __device__ __forceinline__ double block_sum(V v, double* sh) {
   return s;  // valid in thread 0
 }
 
+// p[first] + p[first + step] + ... (indices below n) added in increasing
+// index order, with eight loads in flight at a time: the same sum, bit for
+// bit, as the plain loop, without one L2 round trip per term
+__device__ __forceinline__ double strided_sum_ordered(const double* p, int first, int n, int step) {
+  double acc = 0.0;
+  int b = first;
+  for (; b + 7 * step < n; b += 8 * step) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldcg(p + b + u * step);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc += v[u];
+  }
+  for (; b < n; b += step) acc += __ldcg(p + b);
+  return acc;
+}
+
 // Called by all threads of every block of right-hand side `rhs`.  Returns
 // true in the last block of that RHS, in which thread 0 holds its total.
 template <int NT, class V>
@@ -494,8 +511,7 @@ __device__ __forceinline__ bool grid_sum(V v, RedSlot slot, int rhs, double* tot
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
-  double acc = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += NT) acc += __ldcg(partials + b);
+  const double acc = strided_sum_ordered(partials, threadIdx.x, nblocks, NT);
   // fixed-order tree over the threads' strided partial sums
   double tot = block_sum<NT>(acc, sh);
   if (threadIdx.x == 0) {

@@ -243,10 +243,9 @@ int launch_contract(Ctx& c, const ContractPlan& plan, const NoiseSpec& ns, uint3
       launch(args, dim3(nbx, T, 2));
       c.launches++;
       TSM_TRY(check_launch(c, "contract_kernel"));
-      const int nred = nout * T;
-      const unsigned rblocks = (unsigned)(((size_t)nred * 32 + 127) / 128);   // a warp per output
-      contract_reduce_kernel<<<rblocks, 128, 0, c.stream>>>(static_cast<double2*>(part), T, nbx, plan.ng, nq,
-                                                            plan.n_q, q0, dst);
+      const dim3 rgrid((unsigned)((nout + 31) / 32), (unsigned)T), rblock(32, CT_RED_WARPS);
+      contract_reduce_kernel<<<rgrid, rblock, 0, c.stream>>>(static_cast<double2*>(part), T, nbx, plan.ng, nq,
+                                                             plan.n_q, q0, dst);
       c.launches++;
       TSM_TRY(check_launch(c, "contract_reduce_kernel"));
       tl.done();
@@ -302,7 +301,11 @@ template int launch_contract<float, F16, F16>(Ctx&, const ContractPlan&, const N
                                               const EOField*, double2*, const EOField*, const EOField*);
 
 int apply_wilson(Ctx& c, int prec, EOField in, EOField out) {
-  return dispatch_prec(prec, [&](auto tag) -> int {
+  // one field: the one-thread-per-site stencil (link tiles pay only when
+  // several sources share them)
+  const bool per_site = c.hop_per_site;
+  c.hop_per_site = true;
+  const int rc = dispatch_prec(prec, [&](auto tag) -> int {
     using S = decltype(tag);
     // both parities: links, neighbour field, centre field, output
     TimedLaunch tl(c, PB_WILSON, (double)c.g.V * (link_site_bytes(S::id) + 3.0 * spinor_site_bytes(S::id)), true);
@@ -329,6 +332,8 @@ int apply_wilson(Ctx& c, int prec, EOField in, EOField out) {
     tl.done();
     return (int)TSM_OK;
   });
+  c.hop_per_site = per_site;
+  return rc;
 }
 
 int reserve_contract(Ctx& c) {

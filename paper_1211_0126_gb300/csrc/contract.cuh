@@ -547,28 +547,46 @@ __global__ void __launch_bounds__(ContractNT<R>::value) deriv_contract_kernel(co
 }
 
 // sum the block partials of one timeslice in fixed order into the output
-// layout [g][q][t] (momenta q0 .. q0+nq-1 of nq_total)
-// one warp per output k = t * (ng * nq) + (q * ng + g): lane l adds the
-// block partials l, l + 32, ... of both parities, then a fixed shuffle tree
-static __global__ void contract_reduce_kernel(const double2* __restrict__ partial, int T, int nbx, int ng, int nq,
-                                       int nq_total, int q0, double2* __restrict__ out) {
-  const int k = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  const int nout = ng * nq;
-  if (k >= nout * T) return;   // the same for the whole warp
-  const int t = k / nout, gq = k % nout;
+// layout [g][q][t] (momenta q0 .. q0+nq-1 of nq_total).  A block per
+// (timeslice, 32 consecutive outputs k = q * ng + g): lane = output, so every
+// load of a warp is one contiguous run; warp w adds the partial rows w, w + 8,
+// ... (row = parity * nbx + block) in increasing order with four loads in
+// flight, then warp 0 adds the eight warp sums in warp order.
+constexpr int CT_RED_WARPS = 8;
+static __global__ void __launch_bounds__(32 * CT_RED_WARPS)
+contract_reduce_kernel(const double2* __restrict__ partial, int T, int nbx, int ng, int nq, int nq_total, int q0,
+                       double2* __restrict__ out) {
+  __shared__ double2 sh[CT_RED_WARPS][32];
+  const int nout = ng * nq, t = blockIdx.y, rows = 2 * nbx;
+  const int gq = blockIdx.x * 32 + threadIdx.x, w = threadIdx.y;
   double re = 0.0, im = 0.0;
-  for (int i = lane; i < 2 * nbx; i += 32) {
-    const int par = i / nbx, b = i % nbx;
-    const double2 v = partial[((size_t)(t * 2 + par) * nbx + b) * nout + gq];
-    re += v.x;
-    im += v.y;
-  }
+  if (gq < nout) {
+    const double2* col = partial + (size_t)t * rows * nout + gq;
+    int i = w;
+    for (; i + 3 * CT_RED_WARPS < rows; i += 4 * CT_RED_WARPS) {
+      double2 v[4];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    re += __shfl_down_sync(0xffffffffu, re, o);
-    im += __shfl_down_sync(0xffffffffu, im, o);
+      for (int u = 0; u < 4; ++u) v[u] = col[(size_t)(i + u * CT_RED_WARPS) * nout];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        re += v[u].x;
+        im += v[u].y;
+      }
+    }
+    for (; i < rows; i += CT_RED_WARPS) {
+      const double2 v = col[(size_t)i * nout];
+      re += v.x;
+      im += v.y;
+    }
   }
-  if (lane == 0) {
+  sh[w][threadIdx.x] = make_double2(re, im);
+  __syncthreads();
+  if (w == 0 && gq < nout) {
+#pragma unroll
+    for (int u = 1; u < CT_RED_WARPS; ++u) {
+      re += sh[u][threadIdx.x].x;
+      im += sh[u][threadIdx.x].y;
+    }
     const int gi = gq % ng, q = gq / ng;
     out[((size_t)gi * nq_total + q0 + q) * T + t] = make_double2(re, im);
   }

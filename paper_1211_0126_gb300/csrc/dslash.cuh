@@ -528,11 +528,7 @@ __device__ __forceinline__ void tile_grid_sum(float part, int rhs, RedSlot slot,
     if (r < 0) continue;
     __threadfence();
     const double* partials = slot.partials + (size_t)r * slot.stride;
-    for (int vl = tid; vl < LT_VLANES; vl += nthr) {
-      double acc = 0.0;
-      for (int b = vl; b < (int)gridDim.y; b += LT_VLANES) acc += __ldcg(partials + b);
-      vsum[vl] = acc;
-    }
+    for (int vl = tid; vl < LT_VLANES; vl += nthr) vsum[vl] = strided_sum_ordered(partials, vl, (int)gridDim.y, LT_VLANES);
     __syncthreads();
     if (w == 0) {
       double acc = 0.0;

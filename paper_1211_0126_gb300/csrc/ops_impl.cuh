@@ -42,11 +42,15 @@ int launch_hop(Ctx& c, const HopArgs<S>& a0, int dag, int mode, int prof_kind, i
   TimedLaunch tl(c, 4 * S::id + kind, bytes);
   // 16-bit tiers: link-sharing blocks of LT_SITES sites x up to RPB sources
   // (RPB = c.tile_rpb, 2, 4 or 8 from the autotuner; every solve, whatever its
-  // batch width, so that a source's iterates do not depend on its batch);
-  // others, and single-source operator applications outside the solvers
-  // (c.hop_per_site): one thread per (source, site), blocks of HOP_NT sites
+  // batch width, so that a source's iterates do not depend on its batch); the
+  // FP32 tier the same for the hops without a reduction (its reducing hop K2
+  // measured slower in tiles; per-site arithmetic, and so every result, is the
+  // same in both kernels); FP64, and single-source operator applications
+  // outside the solvers (c.hop_per_site): one thread per (source, site),
+  // blocks of HOP_NT sites
   constexpr bool TILE16 = S::id == F16::id || S::id == BF16::id;
-  const bool tile = TILE16 && !(c.hop_per_site && nrhs == 1);
+  constexpr bool TILE32 = S::id == F32::id;
+  const bool tile = (TILE16 || (TILE32 && !(mode & HOP_NORM))) && !(c.hop_per_site && nrhs == 1);
   const int RPB = c.tile_rpb[S::id];
   const int rpb = nrhs < RPB ? nrhs : RPB;
   const dim3 grid = tile ? dim3((nrhs + rpb - 1) / rpb, blocks_for(a.g.Vh, LT_SITES)) : dim3(nrhs, nb);
@@ -54,7 +58,7 @@ int launch_hop(Ctx& c, const HopArgs<S>& a0, int dag, int mode, int prof_kind, i
 #define TSM_HOP_CASE(D, M)                                                                        \
   if (dag == (D) && mode == (M)) {                                                                \
     if (tile) {                                                                                   \
-      if constexpr (TILE16) {                                                                     \
+      if constexpr (TILE16 || (TILE32 && !((M) & HOP_NORM))) {                                    \
         if (RPB == 2) hop_tile_kernel<S, (D), (M), 2><<<grid, block, 0, c.stream>>>(a, nrhs);     \
         else if (RPB == 8) hop_tile_kernel<S, (D), (M), 8><<<grid, block, 0, c.stream>>>(a, nrhs); \
         else hop_tile_kernel<S, (D), (M), 4><<<grid, block, 0, c.stream>>>(a, nrhs);              \

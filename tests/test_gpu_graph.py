@@ -121,8 +121,11 @@ def test_tuned_launch_shape_bit_identical(libtsm, prec):
             got = tuned.loops(5, 4, 3, 29, hp, lp, GAM, MOMS, per_source=True, batch=b, verify=False)
             for k in ("loops", "err", "per_corr", "per_lp"):
                 assert np.array_equal(got[k], want[k]), (b, k)
-        # a shape forced on each of the three block widths gives the same bits too
+        # a shape forced on each of the three block widths gives the same bits
+        # too, for the LP tier and for the FP32 iterations of the HP solves
         for t in (2, 8):
             tsm.tsm_set_tile(tuned.h, prec, t)
+            tsm.tsm_set_tile(tuned.h, tsm.TSM_F32, t)
             got = tuned.loops(5, 4, 3, 29, hp, lp, GAM, MOMS, per_source=True, batch=32, verify=False)
             assert np.array_equal(got["per_lp"], want["per_lp"]), t
+            assert np.array_equal(got["per_corr"], want["per_corr"]), t
