@@ -333,13 +333,14 @@ struct NoiseSpec {
   uint32_t k0, k1;   // seed low / high word
   int kind;          // 4 = Z4, 2 = Z2
   double amp;        // 1/sqrt(2) for Z4 (host-computed), 1 for Z2
+  float famp;        // amp rounded once on the host (FP32 kernels: no conversion on the FP64 pipe)
 };
 
 // eta_source at full-lattice site `lex`, component a = 3*spin + colour
 template <class R>
 __device__ __forceinline__ void noise_site(const NoiseSpec& n, uint32_t lex, uint32_t source, cx<R> v[12]) {
   const uint32_t w = philox_word0(lex, source, 0u, 0u, n.k0, n.k1);
-  const R amp = (R)n.amp;
+  const R amp = sizeof(R) == 4 ? (R)n.famp : (R)n.amp;
 #pragma unroll
   for (int a = 0; a < 12; ++a) {
     const R re = ((w >> (2 * a)) & 1u) ? -amp : amp;

@@ -358,6 +358,7 @@ NoiseSpec make_noise(uint64_t seed, int kind) {
   n.k1 = (uint32_t)(seed >> 32);
   n.kind = kind;
   n.amp = (kind == 4) ? 1.0 / std::sqrt(2.0) : 1.0;
+  n.famp = (float)n.amp;
   return n;
 }
 

@@ -138,7 +138,8 @@ template <class R> struct ContractNT { static constexpr int value = 128; };
 template <> struct ContractNT<double> { static constexpr int value = 64; };
 
 // Shared memory of a contraction block of NT sites, reused across phases:
-//   stage   Gs[NT][CT_GS] complex (the 16 traces of each site) | Ws[NT][ncp] (weights)
+//   stage   Gs[NT][CT_GS] complex (the 16 traces of each site) | Ws[ncp][NT + 1] (weights,
+//           channel-major: a warp's stores of one channel hit 32 banks)
 //   reduce  red[NT][CT_RS] (each thread's tile) | chan[16][CT_CHS] complex (channel sums)
 constexpr int CT_GS = 17;            // complex row stride of Gs (16 + 1: no bank conflicts across sites)
 constexpr int CT_RS = 36;            // row stride of red (32 + 4, rows stay 16-byte aligned)
@@ -146,7 +147,7 @@ constexpr int CT_CHS = CT_MAXCH + 1;
 template <class R, int NT>
 struct CtSmem {
   static constexpr size_t gs = (size_t)NT * CT_GS * 2 * sizeof(R);
-  static constexpr size_t stage = gs + (size_t)NT * CT_MAXCH * sizeof(R);
+  static constexpr size_t stage = gs + (size_t)(NT + 1) * CT_MAXCH * sizeof(R);
   static constexpr size_t red = (size_t)NT * CT_RS * sizeof(R);
   static constexpr size_t reduce = red + (size_t)CT_MAXG * CT_CHS * 2 * sizeof(R);
   static constexpr size_t bytes = stage > reduce ? stage : reduce;
@@ -158,7 +159,7 @@ template <class R, int NT, class SA, class SB>
 __device__ __forceinline__ void ct_stage(const ContractArgs<SA, SB>& a, unsigned char* smem, bool valid,
                                          const cx<R> (&S)[4][4], const int c[4]) {
   R* gs = reinterpret_cast<R*>(smem) + (size_t)threadIdx.x * CT_GS * 2;
-  R* ws = reinterpret_cast<R*>(smem + CtSmem<R, NT>::gs) + (size_t)threadIdx.x * a.mom.ncp;
+  R* ws = reinterpret_cast<R*>(smem + CtSmem<R, NT>::gs) + threadIdx.x;   // channel ch at ws[ch * (NT + 1)]
   if (valid) {
     cx<R> G[16];
     chiral_traces(S, G);
@@ -170,28 +171,27 @@ __device__ __forceinline__ void ct_stage(const ContractArgs<SA, SB>& a, unsigned
     for (int k = 0; k < a.mom.ncls; ++k) {
       const cx<R> e = phase_at<R>(a, a.mom.rep[k], c);
       const int ch = a.mom.ch[k];
-      ws[ch] = e.re;
-      if (a.mom.nz[k]) ws[ch + 1] = e.im;
+      ws[ch * (NT + 1)] = e.re;
+      if (a.mom.nz[k]) ws[(ch + 1) * (NT + 1)] = e.im;
     }
-    for (int ch = a.mom.nch; ch < a.mom.ncp; ++ch) ws[ch] = (R)0;
+    for (int ch = a.mom.nch; ch < a.mom.ncp; ++ch) ws[ch * (NT + 1)] = (R)0;
   } else {
 #pragma unroll
     for (int k = 0; k < 32; ++k) gs[k] = (R)0;
-    for (int ch = 0; ch < a.mom.ncp; ++ch) ws[ch] = (R)0;
+    for (int ch = 0; ch < a.mom.ncp; ++ch) ws[ch * (NT + 1)] = (R)0;
   }
 }
 
 template <class R> struct Vec4;
 template <> struct Vec4<float> {
-  static __device__ __forceinline__ void load(const float* p, float w[4]) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+  static __device__ __forceinline__ void store(float* p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
   }
 };
 template <> struct Vec4<double> {
-  static __device__ __forceinline__ void load(const double* p, double w[4]) {
-    const double2 v0 = reinterpret_cast<const double2*>(p)[0], v1 = reinterpret_cast<const double2*>(p)[1];
-    w[0] = v0.x; w[1] = v0.y; w[2] = v1.x; w[3] = v1.y;
+  static __device__ __forceinline__ void store(double* p, double a, double b, double c, double d) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+    reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
   }
 };
 template <class R> struct Vec2;
@@ -243,7 +243,8 @@ __device__ __forceinline__ void ct_reduce(const ContractArgs<SA, SB>& a, unsigne
 #pragma unroll
       for (int r = 0; r < 4; ++r) gv[r] = Vec2<R>::load(grow + go[r]);
       R w[4];
-      Vec4<R>::load(Ws + (size_t)s * ncp + 4 * ct, w);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) w[u] = Ws[(4 * ct + u) * (NT + 1) + s];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -257,14 +258,12 @@ __device__ __forceinline__ void ct_reduce(const ContractArgs<SA, SB>& a, unsigne
   R* red = reinterpret_cast<R*>(smem);
   R* chan = reinterpret_cast<R*>(smem + CtSmem<R, NT>::red);   // [16][CT_CHS] complex
   if (active) {
-    R* row = red + (size_t)tid * CT_RS;
+    R* row = red + (size_t)tid * CT_RS;   // 16-byte vector stores: no bank conflicts
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        row[(r * 4 + u) * 2] = acc[r][u][0];
-        row[(r * 4 + u) * 2 + 1] = acc[r][u][1];
-      }
+      for (int u = 0; u < 4; u += 2)
+        Vec4<R>::store(row + (r * 4 + u) * 2, acc[r][u][0], acc[r][u][1], acc[r][u + 1][0], acc[r][u + 1][1]);
   }
   __syncthreads();
   for (int x = tid; x < types * 32; x += NT) {
