@@ -50,7 +50,9 @@ int launch_hop(Ctx& c, const HopArgs<S>& a0, int dag, int mode, int prof_kind, i
   // blocks of HOP_NT sites
   constexpr bool TILE16 = S::id == F16::id || S::id == BF16::id;
   constexpr bool TILE32 = S::id == F32::id;
-  const bool tile = (TILE16 || (TILE32 && !(mode & HOP_NORM))) && !(c.hop_per_site && nrhs == 1);
+  // (FP32: only with several sources to share the links; a single field runs
+  // faster one thread per site, with the same bits)
+  const bool tile = TILE16 ? !(c.hop_per_site && nrhs == 1) : (TILE32 && !(mode & HOP_NORM) && nrhs >= 2);
   const int RPB = c.tile_rpb[S::id];
   const int rpb = nrhs < RPB ? nrhs : RPB;
   const dim3 grid = tile ? dim3((nrhs + rpb - 1) / rpb, blocks_for(a.g.Vh, LT_SITES)) : dim3(nrhs, nb);
