@@ -507,6 +507,12 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def tune_table(tsm, times):
+    """the autotuner's ms per source: width -> block shape (sources x registers) -> ms"""
+    return {"w%d" % w: {"t%dr%d" % shape: float(times[i, j]) for j, shape in enumerate(tsm.TILE_SHAPES)}
+            for i, w in enumerate((8, 16, 32, 64))}
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("dslash.cuh", "common.cuh"):
@@ -565,11 +571,9 @@ def run_ours(args):
     # launch shape: autotuned (untimed, before the warm-up) unless a batch width is given
     tune = None
     if args.batch is None:
-        best, tile, ttimes = tsm.tsm_tune(ctx.h, lp_stop)
+        best, tile, regs, ttimes = tsm.tsm_tune(ctx.h, lp_stop)
         args.batch = best
-        tune = {"batch": best, "tile_sources": tile,
-                "ms_per_source": {"w%d" % w: {"t%d" % t: float(ttimes[i, j]) for j, t in enumerate((2, 4, 8))}
-                                  for i, w in enumerate((8, 16, 32, 64))}}
+        tune = {"batch": best, "tile_sources": tile, "max_regs": regs, "ms_per_source": tune_table(tsm, ttimes)}
     E = N_GAMMA * N_Q * DIMS[3]
     shape = (N_GAMMA, N_Q, DIMS[3])
     d_loops = torch.zeros(shape, dtype=torch.complex128, device=dev)
@@ -939,13 +943,11 @@ def run_three_lattice(args):
     for k, dims in enumerate(lattices):
         ctx = tsm.Context(0)
         ctx.load_gauge(S.gauge_field(dims, EPS, 100 + k), dims, KAPPA, MU)
-        best, tile, times = tsm.tsm_tune(ctx.h, lp)
+        best, tile, regs, times = tsm.tsm_tune(ctx.h, lp)
         ctxs.append(ctx)
         widths.append(best)
-        tune["x".join(map(str, dims))] = {"batch": best, "tile_sources": tile,
-                                          "ms_per_source": {"w%d" % w: {"t%d" % t: float(times[i, j])
-                                                                        for j, t in enumerate((2, 4, 8))}
-                                                            for i, w in enumerate((8, 16, 32, 64))}}
+        tune["x".join(map(str, dims))] = {"batch": best, "tile_sources": tile, "max_regs": regs,
+                                          "ms_per_source": tune_table(tsm, times)}
     outs = [torch.zeros((len(gam), len(moms), d[3]), dtype=torch.complex128, device="cuda") for d in lattices]
 
     def plist(seed):

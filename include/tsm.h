@@ -317,25 +317,29 @@ int tsm_loops_graph(tsm_ctx** ctxs, const tsm_params* params, int n, double** lo
 int tsm_tune_batch(tsm_ctx* ctx, const tm_stop* stop, int* best, double* times_ms);
 
 /* Autotuner of the whole multi-RHS launch shape: the batch width as above
- * and, for the 16-bit tiers and FP32, the sources per block of their
- * link-sharing stencil (blocks of 32 sites x 2, 4 or 8 sources, one warp per
- * source; the block's links are widened once and shared; FP32 uses it for its
- * hops without a reduction).  Times one batched solve of
- * scratch noise sources per (width, block shape) pair and keeps the pair with
- * the lowest time per source: *best_batch, *best_tile (may be NULL; 1 for
- * tiers without that stencil).  The block shape is then used by every later
- * solve of that tier on this context; the results do not depend on it (per-site
+ * and, for the 16-bit tiers and FP32, the block shape of their link-sharing
+ * stencil (blocks of 32 sites x 2, 4 or 8 sources, one warp per source; the
+ * block's links are widened once and shared; FP32 uses it for its hops
+ * without a reduction), the 4-source blocks compiled for either 80 or 96
+ * registers per thread (768 or 640 resident threads per SM).  Times one
+ * batched solve of scratch noise sources per (width, block shape) pair and
+ * keeps the pair with the lowest time per source: *best_batch, *best_tile
+ * (may be NULL; 1 for tiers without that stencil), *best_regs (may be NULL;
+ * 0 for tiers without it).  The block shape is then used by every later solve
+ * of that tier on this context; the results do not depend on it (per-site
  * arithmetic and reduction order are independent of the block shape).  Cached
- * per context, lattice and stopping rule.  times_ms (may be NULL): 12 entries,
+ * per context, lattice and stopping rule.  times_ms (may be NULL): 16 entries,
  * [width k][shape q] = ms per source for widths {8, 16, 32, 64} and shapes
- * {2, 4, 8} (0 where a shape does not apply).  tsm_tune_batch runs the same
- * search and reports, per width, the best time over the shapes. */
-int tsm_tune(tsm_ctx* ctx, const tm_stop* stop, int* best_batch, int* best_tile, double* times_ms);
+ * {2 sources / 80 registers, 4 / 80, 8 / 80, 4 / 96} (0 where a shape does not
+ * apply).  tsm_tune_batch runs the same search and reports, per width, the best
+ * time over the shapes. */
+int tsm_tune(tsm_ctx* ctx, const tm_stop* stop, int* best_batch, int* best_tile, int* best_regs, double* times_ms);
 
-/* Set the sources per block (2, 4 or 8) of the link-sharing stencil of tier
- * prec (TSM_F16, TSM_BF16 or TSM_F32) for this context's later solves, as
- * tsm_tune does; 4 by default.  TSM_ERR_ARG for other tiers or values. */
-int tsm_set_tile(tsm_ctx* ctx, int prec, int tile_sources);
+/* Set the block shape of the link-sharing stencil of tier prec (TSM_F16,
+ * TSM_BF16 or TSM_F32) for this context's later solves, as tsm_tune does:
+ * tile_sources 2, 4 or 8 sources per block, max_regs 80 (or 96 with 4
+ * sources); 4 and 80 by default.  TSM_ERR_ARG for other tiers or values. */
+int tsm_set_tile(tsm_ctx* ctx, int prec, int tile_sources, int max_regs);
 
 
 /* Tensor-core GEMM of the learned preconditioner's channel mixing (the dense

@@ -965,7 +965,7 @@ int tsm_combine(tsm_ctx* h, const double* per_corr, int n_hp, const double* per_
   return TSM_OK;
 }
 
-int tsm_tune(tsm_ctx* h, const tm_stop* stop, int* best_batch, int* best_tile, double* times_ms) {
+int tsm_tune(tsm_ctx* h, const tm_stop* stop, int* best_batch, int* best_tile, int* best_regs, double* times_ms) {
   if (h == nullptr || best_batch == nullptr) return bad(TSM_ERR_ARG, "null argument");
   TSM_TRY(check_stop(stop));
   Ctx& c = h->c;
@@ -975,17 +975,25 @@ int tsm_tune(tsm_ctx* h, const tm_stop* stop, int* best_batch, int* best_tile, d
   snprintf(key, sizeof(key), "%dx%dx%dx%d/p%d/r%d/t%g/m%d", c.lat.L[0], c.lat.L[1], c.lat.L[2], c.lat.L[3],
            stop->prec, stop->reliable, stop->rel_tol, stop->max_iter);
   const int cand[4] = {8, 16, 32, 64};
-  const int tiles[3] = {2, 4, 8};
+  // block shapes of the link-sharing stencil: sources per block x register budget
+  constexpr int kShapes = 4;
+  const int tiles[kShapes] = {2, 4, 8, 4};
+  const int regs[kShapes] = {80, 80, 80, 96};
   // the link-sharing stencil (16-bit tiers; FP32 for its hops without a
   // reduction) has a block shape to choose; FP64 runs one thread per (source, site)
   const bool tiled = stop->prec == TSM_F16 || stop->prec == TSM_BF16 || stop->prec == TSM_F32;
-  const int ntile = tiled ? 3 : 1;
+  const int ntile = tiled ? kShapes : 1;
   auto ib = c.tuned_batch.find(key);
   auto it = c.tuned_rpb.find(key);
   if (ib != c.tuned_batch.end() && it != c.tuned_rpb.end() && times_ms == nullptr) {
+    const int q = it->second;
     *best_batch = ib->second;
-    if (best_tile) *best_tile = it->second;
-    if (tiled) c.tile_rpb[stop->prec] = it->second;
+    if (best_tile) *best_tile = tiled ? tiles[q] : 1;
+    if (best_regs) *best_regs = tiled ? regs[q] : 0;
+    if (tiled) {
+      c.tile_rpb[stop->prec] = tiles[q];
+      c.tile_regs[stop->prec] = regs[q];
+    }
     return TSM_OK;
   }
   const int sp = loop_solution_prec(*stop);   // the solves of the loop estimators
@@ -1000,8 +1008,8 @@ int tsm_tune(tsm_ctx* h, const tm_stop* stop, int* best_batch, int* best_tile, d
   TSM_CUDA(cudaEventCreate(&e1));
   std::vector<SolveResult> res(cand[3]);
   double best_t = 1e300;
-  int best_w = cand[0], best_r = tiled ? c.tile_rpb[stop->prec] : 1;
-  const int saved_rpb = tiled ? c.tile_rpb[stop->prec] : 0;
+  int best_w = cand[0], best_q = 1;
+  const int saved_rpb = tiled ? c.tile_rpb[stop->prec] : 0, saved_regs = tiled ? c.tile_regs[stop->prec] : 0;
   int rc = TSM_OK;
   for (int k = 0; k < 4 && rc == TSM_OK; ++k) {
     const int w = cand[k];
@@ -1011,7 +1019,10 @@ int tsm_tune(tsm_ctx* h, const tm_stop* stop, int* best_batch, int* best_tile, d
       return launch_noise<S>(c, 1, ns, 0, fb.o, w);
     });
     for (int q = 0; q < ntile && rc == TSM_OK; ++q) {
-      if (tiled) c.tile_rpb[stop->prec] = tiles[q];
+      if (tiled) {
+        c.tile_rpb[stop->prec] = tiles[q];
+        c.tile_regs[stop->prec] = regs[q];
+      }
       // one untimed solve to settle caches and clocks, then one timed
       rc = solve_batch(c, *stop, 0, w, fb, fs, res.data(), nullptr, -1, sp);
       if (rc != TSM_OK) break;
@@ -1022,50 +1033,61 @@ int tsm_tune(tsm_ctx* h, const tm_stop* stop, int* best_batch, int* best_tile, d
       float ms = 0.f;
       if (rc == TSM_OK) cudaEventElapsedTime(&ms, e0, e1);
       const double per = ms / w;
-      if (times_ms) times_ms[3 * k + q] = per;
+      if (times_ms) times_ms[kShapes * k + q] = per;
       if (per < best_t) {
         best_t = per;
         best_w = w;
-        best_r = tiled ? tiles[q] : 1;
+        best_q = q;
       }
     }
-    if (times_ms && !tiled) times_ms[3 * k + 1] = times_ms[3 * k + 2] = 0.0;
+    if (times_ms && !tiled)
+      for (int q = 1; q < kShapes; ++q) times_ms[kShapes * k + q] = 0.0;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != TSM_OK) {
-    if (tiled) c.tile_rpb[stop->prec] = saved_rpb;
+    if (tiled) {
+      c.tile_rpb[stop->prec] = saved_rpb;
+      c.tile_regs[stop->prec] = saved_regs;
+    }
     return rc;
   }
   c.tuned_batch[key] = best_w;
-  c.tuned_rpb[key] = best_r;
-  if (tiled) c.tile_rpb[stop->prec] = best_r;
+  c.tuned_rpb[key] = best_q;
+  if (tiled) {
+    c.tile_rpb[stop->prec] = tiles[best_q];
+    c.tile_regs[stop->prec] = regs[best_q];
+  }
   *best_batch = best_w;
-  if (best_tile) *best_tile = best_r;
+  if (best_tile) *best_tile = tiled ? tiles[best_q] : 1;
+  if (best_regs) *best_regs = tiled ? regs[best_q] : 0;
   return TSM_OK;
 }
 
-int tsm_set_tile(tsm_ctx* h, int prec, int tile_sources) {
+int tsm_set_tile(tsm_ctx* h, int prec, int tile_sources, int max_regs) {
   if (h == nullptr) return bad(TSM_ERR_ARG, "null context");
   if (prec != TSM_F16 && prec != TSM_BF16 && prec != TSM_F32)
     return bad(TSM_ERR_ARG, "the FP64 tier has no link-sharing block shape");
   if (tile_sources != 2 && tile_sources != 4 && tile_sources != 8)
     return bad(TSM_ERR_ARG, "sources per block must be 2, 4 or 8");
+  if (max_regs != 80 && !(max_regs == 96 && tile_sources == 4))
+    return bad(TSM_ERR_ARG, "register budget must be 80, or 96 with 4 sources per block");
   h->c.tile_rpb[prec] = tile_sources;
+  h->c.tile_regs[prec] = max_regs;
   return TSM_OK;
 }
 
 int tsm_tune_batch(tsm_ctx* h, const tm_stop* stop, int* best, double* times_ms) {
   if (best == nullptr) return bad(TSM_ERR_ARG, "null argument");
-  double t[12];
-  int tile = 0;
-  TSM_TRY(tsm_tune(h, stop, best, &tile, times_ms ? t : nullptr));
+  double t[16];
+  int tile = 0, regs = 0;
+  TSM_TRY(tsm_tune(h, stop, best, &tile, &regs, times_ms ? t : nullptr));
   if (times_ms) {
     // per width: the best over the block shapes
     for (int k = 0; k < 4; ++k) {
       double m = 1e300;
-      for (int q = 0; q < 3; ++q)
-        if (t[3 * k + q] > 0.0 && t[3 * k + q] < m) m = t[3 * k + q];
+      for (int q = 0; q < 4; ++q)
+        if (t[4 * k + q] > 0.0 && t[4 * k + q] < m) m = t[4 * k + q];
       times_ms[k] = m;
     }
   }

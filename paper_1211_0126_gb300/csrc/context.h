@@ -91,10 +91,12 @@ struct Ctx {
   int next_guard = 0;
   std::vector<std::pair<int, int>> cap_lp, cap_hp;   // (first state, count) of captured solves
   std::map<std::string, int> tuned_batch;            // autotuner cache: lattice + tier -> batch width
-  std::map<std::string, int> tuned_rpb;              // autotuner cache: lattice + tier -> sources per tile
-  // sources per link-sharing block of the 16-bit stencil, per tier id (2, 4 or
-  // 8; the autotuner sets it, the results do not depend on it)
+  std::map<std::string, int> tuned_rpb;              // autotuner cache: lattice + tier -> block shape index
+  // sources per link-sharing block of the 16-bit and FP32 stencils, per tier id
+  // (2, 4 or 8), and the register budget of the 4-source blocks (80 or 96); the
+  // autotuner sets them, the results do not depend on them
   int tile_rpb[4] = {LT_RHS, LT_RHS, LT_RHS, LT_RHS};
+  int tile_regs[4] = {LT_REGS, LT_REGS, LT_REGS, LT_REGS};   // register budget of the 4-source tiles
   // instrumentation
   bool profile = false;
   struct EvRec {

@@ -442,9 +442,12 @@ __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) cg_update_kern
 constexpr int LT_SITES = 32;
 constexpr int LT_RHS = 4;   // default right-hand sides per block
 
-// resident blocks per SM the tile kernels are compiled for: 768 threads, the
-// register budget (80) of the per-site stencil at six blocks of 128
-template <int RPB> struct TileMinBlocks { static constexpr int value = 24 / RPB; };
+// resident blocks per SM the tile kernels are compiled for: 768 threads at
+// the default register budget of 80 per thread (the per-site stencil's budget
+// at six blocks of 128), or 640 threads at 96 registers (REGS = 96: fewer
+// spills, fewer resident warps; the autotuner chooses)
+constexpr int LT_REGS = 80;   // default register budget of the tile kernels
+template <int RPB, int REGS> struct TileMinBlocks { static constexpr int value = (REGS == 96 ? 20 : 24) / RPB; };
 
 struct LinkTile {
   float4 v[8][5][LT_SITES];   // [hop 2 mu + backward][pair of complex][site]: rows 0..2, then a zero
@@ -552,9 +555,9 @@ __device__ __forceinline__ int tile_rhs(const int* active, int nrhs) {
   return active != nullptr ? active[k] : k;
 }
 
-template <class S, int DAG, int MODE, int RPB>
-__global__ void __launch_bounds__(LT_SITES * RPB, TileMinBlocks<RPB>::value) hop_tile_kernel(const HopArgs<S> a,
-                                                                                            int nrhs) {
+template <class S, int DAG, int MODE, int RPB, int REGS>
+__global__ void __launch_bounds__(LT_SITES * RPB, (TileMinBlocks<RPB, REGS>::value))
+    hop_tile_kernel(const HopArgs<S> a, int nrhs) {
   __shared__ LinkTile tile;
   using R = typename S::real;
   int rhs = tile_rhs(a.active, nrhs);

@@ -41,7 +41,8 @@ int launch_hop(Ctx& c, const HopArgs<S>& a0, int dag, int mode, int prof_kind, i
       (lb + nrhs * sb * (2 + ((mode & HOP_CENTER) ? 1 : 0) + ((mode & HOP_BASE) ? 1 : 0)));
   TimedLaunch tl(c, 4 * S::id + kind, bytes);
   // 16-bit tiers: link-sharing blocks of LT_SITES sites x up to RPB sources
-  // (RPB = c.tile_rpb, 2, 4 or 8 from the autotuner; every solve, whatever its
+  // (RPB = c.tile_rpb, 2, 4 or 8, and for 4 a register budget of 80 or 96,
+  // from the autotuner; every solve, whatever its
   // batch width, so that a source's iterates do not depend on its batch); the
   // FP32 tier the same for the hops without a reduction (its reducing hop K2
   // measured slower in tiles; per-site arithmetic, and so every result, is the
@@ -54,6 +55,7 @@ int launch_hop(Ctx& c, const HopArgs<S>& a0, int dag, int mode, int prof_kind, i
   // faster one thread per site, with the same bits)
   const bool tile = TILE16 ? !(c.hop_per_site && nrhs == 1) : (TILE32 && !(mode & HOP_NORM) && nrhs >= 2);
   const int RPB = c.tile_rpb[S::id];
+  const bool wide = RPB == 4 && c.tile_regs[S::id] == 96;   // 96-register variant (4 sources only)
   const int rpb = nrhs < RPB ? nrhs : RPB;
   const dim3 grid = tile ? dim3((nrhs + rpb - 1) / rpb, blocks_for(a.g.Vh, LT_SITES)) : dim3(nrhs, nb);
   const dim3 block = tile ? dim3(LT_SITES, rpb) : dim3(HOP_NT);
@@ -61,9 +63,10 @@ int launch_hop(Ctx& c, const HopArgs<S>& a0, int dag, int mode, int prof_kind, i
   if (dag == (D) && mode == (M)) {                                                                \
     if (tile) {                                                                                   \
       if constexpr (TILE16 || (TILE32 && !((M) & HOP_NORM))) {                                    \
-        if (RPB == 2) hop_tile_kernel<S, (D), (M), 2><<<grid, block, 0, c.stream>>>(a, nrhs);     \
-        else if (RPB == 8) hop_tile_kernel<S, (D), (M), 8><<<grid, block, 0, c.stream>>>(a, nrhs); \
-        else hop_tile_kernel<S, (D), (M), 4><<<grid, block, 0, c.stream>>>(a, nrhs);              \
+        if (RPB == 2) hop_tile_kernel<S, (D), (M), 2, 80><<<grid, block, 0, c.stream>>>(a, nrhs); \
+        else if (RPB == 8) hop_tile_kernel<S, (D), (M), 8, 80><<<grid, block, 0, c.stream>>>(a, nrhs); \
+        else if (wide) hop_tile_kernel<S, (D), (M), 4, 96><<<grid, block, 0, c.stream>>>(a, nrhs); \
+        else hop_tile_kernel<S, (D), (M), 4, 80><<<grid, block, 0, c.stream>>>(a, nrhs);          \
       }                                                                                           \
     } else {                                                                                      \
       hop_kernel<S, (D), (M)><<<grid, block, 0, c.stream>>>(a);                                   \

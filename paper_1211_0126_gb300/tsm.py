@@ -87,8 +87,8 @@ _SIGS = {
                                        ctypes.POINTER(TsmLoopStats)]),
     "tsm_tune_batch": (ctypes.c_int, [_P, ctypes.POINTER(TmStop), ctypes.POINTER(ctypes.c_int), _P]),
     "tsm_tune": (ctypes.c_int, [_P, ctypes.POINTER(TmStop), ctypes.POINTER(ctypes.c_int),
-                                ctypes.POINTER(ctypes.c_int), _P]),
-    "tsm_set_tile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _P]),
+    "tsm_set_tile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "tsm_umma_gemm": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "tsm_umma_inject_timeout": (ctypes.c_int, [ctypes.c_int]),
     "tsm_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -407,20 +407,26 @@ def tsm_tune_batch(h, stp):
     return best.value, times
 
 
+# block shapes the autotuner tries: (sources per block, registers per thread)
+TILE_SHAPES = ((2, 80), (4, 80), (8, 80), (4, 96))
+
+
 def tsm_tune(h, stp):
     """Autotuned launch shape for the loaded lattice and tier: returns (best
-    batch width, best sources per link-sharing block, per-source ms [4][3] for
-    widths 8, 16, 32, 64 x block shapes 2, 4, 8)."""
+    batch width, best sources per link-sharing block, its register budget,
+    per-source ms [4][4] for widths 8, 16, 32, 64 x the block shapes of
+    TILE_SHAPES)."""
     best = ctypes.c_int(0)
     tile = ctypes.c_int(0)
-    times = np.zeros(12)
-    _check(library().tsm_tune(h, ctypes.byref(stp), ctypes.byref(best), ctypes.byref(tile),
+    regs = ctypes.c_int(0)
+    times = np.zeros(16)
+    _check(library().tsm_tune(h, ctypes.byref(stp), ctypes.byref(best), ctypes.byref(tile), ctypes.byref(regs),
                               ctypes.c_void_p(times.ctypes.data)), "tsm_tune")
-    return best.value, tile.value, times.reshape(4, 3)
+    return best.value, tile.value, regs.value, times.reshape(4, 4)
 
 
-def tsm_set_tile(h, prec, tile_sources):
-    return _check(library().tsm_set_tile(h, int(prec), int(tile_sources)), "tsm_set_tile")
+def tsm_set_tile(h, prec, tile_sources, max_regs=80):
+    return _check(library().tsm_set_tile(h, int(prec), int(tile_sources), int(max_regs)), "tsm_set_tile")
 
 
 def tsm_umma_gemm(A, B, C, beta=0, stream=None):

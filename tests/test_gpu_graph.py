@@ -102,30 +102,32 @@ def test_autotuner_and_config_sizes_graph_matches_eager(libtsm):
 
 @pytest.mark.parametrize("prec", [tsm.TSM_F16, tsm.TSM_BF16])
 def test_tuned_launch_shape_bit_identical(libtsm, prec):
-    """tsm_tune picks the batch width and the sources per link-sharing block
-    (2, 4 or 8) of the 16-bit stencil; whatever it picks, the TSM results are
-    bit-identical to the default shape (batch 32, 4 sources per block): the
-    per-site arithmetic and every reduction order are independent of both."""
+    """tsm_tune picks the batch width and the block shape of the link-sharing
+    stencil (2, 4 or 8 sources per block; 80 or 96 registers per thread for 4);
+    whatever it picks, the TSM results are bit-identical to the default shape
+    (batch 32, 4 sources per block, 80 registers): the per-site arithmetic and
+    every reduction order are independent of both."""
     dims = (8, 8, 8, 16)
     hp = tsm.stop(1e-10, 3000, tsm.TSM_F32, reliable=True, reliable_delta=1e-3)
     lp = tsm.stop(5e-3, 60, prec)
     with tsm.Context(0) as ref, tsm.Context(0) as tuned:
         for c in (ref, tuned):
             c.load_gauge(S.gauge_field(dims, 0.25, 71), dims, KAPPA, MU)
-        best, tile, times = tsm.tsm_tune(tuned.h, lp)
-        print("tuned: batch %d, %d sources per block; ms per source:\n%s" % (best, tile, times))
-        assert best in (8, 16, 32, 64) and tile in (2, 4, 8)
-        assert times.min() > 0 and times[[8, 16, 32, 64].index(best), [2, 4, 8].index(tile)] == times.min()
+        best, tile, regs, times = tsm.tsm_tune(tuned.h, lp)
+        print("tuned: batch %d, %d sources per block, %d registers; ms per source:\n%s" % (best, tile, regs, times))
+        assert best in (8, 16, 32, 64) and (tile, regs) in tsm.TILE_SHAPES
+        assert times.min() > 0
+        assert times[[8, 16, 32, 64].index(best), tsm.TILE_SHAPES.index((tile, regs))] == times.min()
         want = ref.loops(5, 4, 3, 29, hp, lp, GAM, MOMS, per_source=True, batch=32, verify=False)
         for b in (best, 32, 7):   # the tuned block shape with several batch widths
             got = tuned.loops(5, 4, 3, 29, hp, lp, GAM, MOMS, per_source=True, batch=b, verify=False)
             for k in ("loops", "err", "per_corr", "per_lp"):
                 assert np.array_equal(got[k], want[k]), (b, k)
-        # a shape forced on each of the three block widths gives the same bits
+        # each of the other block shapes, forced, gives the same bits
         # too, for the LP tier and for the FP32 iterations of the HP solves
-        for t in (2, 8):
-            tsm.tsm_set_tile(tuned.h, prec, t)
-            tsm.tsm_set_tile(tuned.h, tsm.TSM_F32, t)
+        for t, r in ((2, 80), (8, 80), (4, 96)):
+            tsm.tsm_set_tile(tuned.h, prec, t, r)
+            tsm.tsm_set_tile(tuned.h, tsm.TSM_F32, t, r)
             got = tuned.loops(5, 4, 3, 29, hp, lp, GAM, MOMS, per_source=True, batch=32, verify=False)
             assert np.array_equal(got["per_lp"], want["per_lp"]), t
             assert np.array_equal(got["per_corr"], want["per_corr"]), t
