@@ -374,15 +374,21 @@ struct CGUpdArgs {
 };
 
 // epilogue of one even site of one right-hand side: acc = (H^dag)_eo t on
-// entry; v = A(-mu) w - kappa^2 acc, r -= alpha v, x += alpha p; returns <r, r>
+// entry; v = A(-mu) w - kappa^2 acc, r -= alpha v, x += alpha p; returns <r, r>.
+// w, p, r and x are read at index li of chunk stride ls from ws, ps, rs, xs
+// (the fields themselves, or their copies in shared memory); r and x are
+// written to the fields.
 template <class S, class SA>
 __device__ __forceinline__ typename SA::real cg_update_epilogue(const CGUpdArgs<S, SA>& a, const CGState* st,
-                                                                size_t off, size_t offa, int ih,
-                                                                cx<typename S::real> acc[12]) {
+                                                                size_t offa, int ih, cx<typename S::real> acc[12],
+                                                                const typename S::schunk* ws,
+                                                                const typename S::schunk* ps,
+                                                                const typename SA::schunk* rs,
+                                                                const typename SA::schunk* xs, int ls, int li) {
   using R = typename S::real;
   using RA = typename SA::real;
   cx<R> v[12];
-  load_spinor<S>(a.w + off, a.sstride, ih, v);
+  load_spinor<S>(ws, ls, li, v);
   constexpr bool FP32 = sizeof(R) == 4;
   if constexpr (FP32) apply_twist(a.ftw, v);
   else apply_twist(a.tw, v);
@@ -391,9 +397,9 @@ __device__ __forceinline__ typename SA::real cg_update_epilogue(const CGUpdArgs<
   for (int k = 0; k < 12; ++k) acc[k] = v[k] - k2 * acc[k];
   const RA alpha = sizeof(RA) == 4 ? (RA)st->alpha_f : (RA)st->alpha;
   cx<RA> rv[12], xv[12];
-  load_spinor<SA>(a.r + offa, a.sstride, ih, rv);
-  load_spinor<SA>(a.x + offa, a.sstride, ih, xv);
-  load_spinor<S>(a.p + off, a.sstride, ih, v);
+  load_spinor<SA>(rs, ls, li, rv);
+  load_spinor<SA>(xs, ls, li, xv);
+  load_spinor<S>(ps, ls, li, v);
   RA s = 0;
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
@@ -406,9 +412,28 @@ __device__ __forceinline__ typename SA::real cg_update_epilogue(const CGUpdArgs<
   return s;
 }
 
+// The FP16 tier (S = SA = F16): the four site-local streams of the epilogue
+// (w, p, r, x: twelve 16-byte chunks per thread) are copied into shared
+// memory with cp.async when the thread starts, so that their latency hides
+// behind the hop instead of following it.
+template <class S, class SA> struct UpdPrefetch {
+  static constexpr bool value = S::id == F16::id && SA::id == F16::id;
+};
+
+__device__ __forceinline__ void copy16_async(void* smem_dst, const void* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void copy16_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 template <class S, class SA>
 __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) cg_update_kernel(const CGUpdArgs<S, SA> a) {
   using R = typename S::real;
+  constexpr bool PF = UpdPrefetch<S, SA>::value;
+  constexpr int NCH = PF ? 3 : 1;   // 16-byte chunks per 16-bit spinor
+  __shared__ uint4 pf[PF ? 4 * NCH : 1][PF ? HOP_NT : 1];
   const int rhs = rhs_slot(a.active);
   CGState* st = a.st + rhs;
   if (st->done) return;
@@ -416,11 +441,28 @@ __global__ void __launch_bounds__(HOP_NT, HopMinBlocks<S>::value) cg_update_kern
   const int ih = blockIdx.y * HOP_NT + threadIdx.x;
   typename SA::real part = 0;
   if (ih < a.g.Vh) {
+    if constexpr (PF) {
+      const uint4* src[4] = {reinterpret_cast<const uint4*>(a.w + off), reinterpret_cast<const uint4*>(a.p + off),
+                             reinterpret_cast<const uint4*>(a.r + offa), reinterpret_cast<const uint4*>(a.x + offa)};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) copy16_async(&pf[q * NCH + ch][threadIdx.x], src[q] + ch * a.sstride + ih);
+    }
     int c[4];
     site_coords(a.g, 0, ih, c);
     cx<R> acc[12];
     hop_site<S, 1>(a.g, ih, c, a.Ue, a.Uo, a.lstride, a.t + off, a.sstride, acc);
-    part = cg_update_epilogue<S, SA>(a, st, off, offa, ih, acc);
+    if constexpr (PF) {
+      copy16_wait_all();   // this thread's own copies: no block barrier needed
+      part = cg_update_epilogue<S, SA>(a, st, offa, ih, acc, reinterpret_cast<const typename S::schunk*>(pf[0]),
+                                       reinterpret_cast<const typename S::schunk*>(pf[NCH]),
+                                       reinterpret_cast<const typename SA::schunk*>(pf[2 * NCH]),
+                                       reinterpret_cast<const typename SA::schunk*>(pf[3 * NCH]), HOP_NT, threadIdx.x);
+    } else {
+      part = cg_update_epilogue<S, SA>(a, st, offa, ih, acc, a.w + off, a.p + off, a.r + offa, a.x + offa, a.sstride,
+                                       ih);
+    }
   }
   double total;
   if (grid_sum<HOP_NT>(part, a.red, rhs, &total) && threadIdx.x == 0) post_action(st, POST_RR, total);
