@@ -491,6 +491,10 @@ constexpr int LT_RHS = 4;   // default right-hand sides per block
 constexpr int LT_REGS = 80;   // default register budget of the tile kernels
 template <int RPB, int REGS> struct TileMinBlocks { static constexpr int value = (REGS == 96 ? 20 : 24) / RPB; };
 
+// groups of LT_SITES sites a link-tile block walks: 4 for the hops with a
+// norm (fewer block partials and grid-sum steps), 1 otherwise
+template <int MODE> struct LtGroups { static constexpr int value = (MODE & HOP_NORM) ? 4 : 1; };
+
 struct LinkTile {
   float4 v[8][5][LT_SITES];   // [hop 2 mu + backward][pair of complex][site]: rows 0..2, then a zero
 };
@@ -605,17 +609,23 @@ __global__ void __launch_bounds__(LT_SITES * RPB, (TileMinBlocks<RPB, REGS>::val
   int rhs = tile_rhs(a.active, nrhs);
   if (rhs >= 0 && a.skip != nullptr && (a.skip_rel ? !a.skip[rhs].need_rel : a.skip[rhs].done)) rhs = -1;
   if (!__syncthreads_or(rhs >= 0)) return;   // every right-hand side of the block is idle
-  const int ih = blockIdx.y * LT_SITES + threadIdx.x;
-  int c[4] = {0, 0, 0, 0};
-  if (ih < a.g.Vh) site_coords(a.g, a.p_out, ih, c);
-  stage_tile<S>(a.g, ih, c, a.Uout, a.Uin, a.lstride, tile);
-  __syncthreads();
+  // a reducing block walks LT_GROUPS<MODE> consecutive groups of 32 sites, so
+  // that its grid-sum step (fence, ticket, barrier) is paid once per group run
   R part = 0;
-  if (rhs >= 0 && ih < a.g.Vh) {
-    const size_t off = rhs_offset<S>(rhs, a.sstride);
-    cx<R> acc[12];
-    hop_site_with<S, DAG>(a.g, c, a.in + off, a.sstride, TileLinks{tile, (int)threadIdx.x}, acc);
-    part = hop_epilogue<S, MODE>(a, off, ih, acc);
+#pragma unroll 1
+  for (int grp = 0; grp < LtGroups<MODE>::value; ++grp) {
+    const int ih = (blockIdx.y * LtGroups<MODE>::value + grp) * LT_SITES + threadIdx.x;
+    int c[4] = {0, 0, 0, 0};
+    if (ih < a.g.Vh) site_coords(a.g, a.p_out, ih, c);
+    if (grp > 0) __syncthreads();   // the previous group's links are consumed
+    stage_tile<S>(a.g, ih, c, a.Uout, a.Uin, a.lstride, tile);
+    __syncthreads();
+    if (rhs >= 0 && ih < a.g.Vh) {
+      const size_t off = rhs_offset<S>(rhs, a.sstride);
+      cx<R> acc[12];
+      hop_site_with<S, DAG>(a.g, c, a.in + off, a.sstride, TileLinks{tile, (int)threadIdx.x}, acc);
+      part += hop_epilogue<S, MODE>(a, off, ih, acc);
+    }
   }
   if constexpr (MODE & HOP_NORM) tile_grid_sum<RPB>(part, rhs, a.red, a.st, a.post);
 }
