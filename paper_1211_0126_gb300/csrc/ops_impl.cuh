@@ -57,7 +57,7 @@ int launch_hop(Ctx& c, const HopArgs<S>& a0, int dag, int mode, int prof_kind, i
   const int RPB = c.tile_rpb[S::id];
   const bool wide = RPB == 4 && c.tile_regs[S::id] == 96;   // 96-register variant (4 sources only)
   const int rpb = nrhs < RPB ? nrhs : RPB;
-  const int tile_sites = LT_SITES * ((mode & HOP_NORM) ? LtGroups<HOP_NORM>::value : 1);
+  const int tile_sites = LT_SITES * ((mode & HOP_NORM) ? LtGroups<HOP_NORM>::value : LtGroups<0>::value);
   const dim3 grid = tile ? dim3((nrhs + rpb - 1) / rpb, blocks_for(a.g.Vh, tile_sites)) : dim3(nrhs, nb);
   const dim3 block = tile ? dim3(LT_SITES, rpb) : dim3(HOP_NT);
 #define TSM_HOP_CASE(D, M)                                                                        \
