@@ -102,7 +102,7 @@ int launch_cg_update(Ctx& c, const CGUpdArgs<S, SA>& a0, int nrhs) {
   TimedLaunch tl(c, 4 * S::id + PK_HOP_UPDATE, (double)a.g.Vh * (lb + nrhs * (3 * sb + 4 * sa)));
   // one thread per (source, site) for every tier: the update is memory-bound,
   // and link sharing measured slower here (534 against 511 us per launch)
-  cg_update_kernel<S, SA><<<dim3(nrhs, nb), HOP_NT, 0, c.stream>>>(a);
+  cg_update_kernel<S, SA><<<dim3(nrhs, blocks_for(a.g.Vh, HOP_NT * UpdGroups<S, SA>::value)), HOP_NT, 0, c.stream>>>(a);
   tl.done();
   c.launches++;
   return check_launch(c, "cg_update_kernel");
