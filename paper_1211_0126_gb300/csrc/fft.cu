@@ -294,8 +294,9 @@ struct ZSink {
   int first;             // mode 2: first source of the batch (assign instead of add)
   double2* mean;         // mode 1
   double* m2;
-  float2* bsum;          // mode 2: sum of x over the batch
-  float* bsq;            // mode 2: sum of |x|^2 over the batch
+  float2* bsum;          // mode 2: sum of d = x - K over the batch
+  float* bsq;            // mode 2: sum of |d|^2 over the batch
+  float2* bshift;        // mode 2: K, the batch's first value of the entry
 };
 
 // z transform of a band of W columns c0 .. c0 + W - 1 (flattened (y, x)) of
@@ -329,16 +330,18 @@ __global__ void __launch_bounds__(FFT_Z_NT) fft_z_kernel(int P, int Lz, FftAxis 
     if (sink.mode == 0) {
       st2(dens + idx, v);
     } else if (sink.mode == 2) {
-      float2 sm = make_float2((float)v.re, (float)v.im);
-      float sq = sm.x * sm.x + sm.y * sm.y;
-      if (!sink.first) {
+      const float2 x = make_float2((float)v.re, (float)v.im);
+      if (sink.first) {   // K = x: d = 0
+        sink.bshift[idx] = x;
+        sink.bsum[idx] = make_float2(0.f, 0.f);
+        sink.bsq[idx] = 0.f;
+      } else {
+        const float2 k = sink.bshift[idx];
+        const float dr = x.x - k.x, di = x.y - k.y;
         const float2 o = sink.bsum[idx];
-        sm.x += o.x;
-        sm.y += o.y;
-        sq += sink.bsq[idx];
+        sink.bsum[idx] = make_float2(o.x + dr, o.y + di);
+        sink.bsq[idx] = sink.bsq[idx] + (dr * dr + di * di);
       }
-      sink.bsum[idx] = sm;
-      sink.bsq[idx] = sq;
     } else {
       // Welford: mean += d / k, m2 += |d|^2 (k - 1) / k with d = x - mean
       const double xr = (double)v.re, xi = (double)v.im;
@@ -355,18 +358,21 @@ __global__ void __launch_bounds__(FFT_Z_NT) fft_z_kernel(int P, int Lz, FftAxis 
   }
 }
 
-// Merge a batch of nb sources (FP32 sums of x and |x|^2) into the running FP64
-// moments of the na sources before it (Chan, Golub & LeVeque's pairwise
-// update): with the batch mean b = S / nb and M2_b = Q - nb |b|^2,
-// mean += (b - mean) nb / n, m2 += M2_b + |b - mean|^2 na nb / n, n = na + nb.
-__global__ void fft_merge_kernel(const float2* __restrict__ bsum, const float* __restrict__ bsq, int na, int nb,
-                                 double2* __restrict__ mean, double* __restrict__ m2, long long E) {
+// Merge a batch of nb sources (FP32 sums S of d = x - K and Q of |d|^2) into
+// the running FP64 moments of the na sources before it (Chan, Golub &
+// LeVeque's pairwise update): with the batch mean b = K + S / nb and
+// M2_b = Q - |S|^2 / nb, mean += (b - mean) nb / n,
+// m2 += M2_b + |b - mean|^2 na nb / n, n = na + nb.
+__global__ void fft_merge_kernel(const float2* __restrict__ bsum, const float* __restrict__ bsq,
+                                 const float2* __restrict__ bshift, int na, int nb, double2* __restrict__ mean,
+                                 double* __restrict__ m2, long long E) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   const double inv_nb = 1.0 / (double)nb;   // uniform: one division per thread
-  const float2 S = bsum[e];
-  const double br = (double)S.x * inv_nb, bi = (double)S.y * inv_nb;
-  const double m2b = fmax((double)bsq[e] - (br * br + bi * bi) * nb, 0.0);
+  const float2 S = bsum[e], K = bshift[e];
+  const double sr = (double)S.x * inv_nb, si = (double)S.y * inv_nb;
+  const double br = (double)K.x + sr, bi = (double)K.y + si;
+  const double m2b = fmax((double)bsq[e] - (sr * sr + si * si) * nb, 0.0);
   if (na == 0) {
     mean[e] = make_double2(br, bi);
     m2[e] = m2b;
@@ -532,6 +538,8 @@ int FftProjector::init(Ctx& c, int ng_, bool dbl) {
       bsum[s] = static_cast<float2*>(p);
       TSM_TRY(c.buffer(s ? "fft_bsq_lp" : "fft_bsq_corr", (size_t)E * sizeof(float), &p));
       bsq[s] = static_cast<float*>(p);
+      TSM_TRY(c.buffer(s ? "fft_bshift_lp" : "fft_bshift_corr", (size_t)E * sizeof(float2), &p));
+      bshift[s] = static_cast<float2*>(p);
     }
     TSM_TRY(c.buffer(s ? "fft_mean_lp" : "fft_mean_corr", (size_t)E * sizeof(double2), &p));
     mean[s] = static_cast<double2*>(p);
@@ -586,8 +594,8 @@ int FftProjector::z_pass(Ctx& c, const void* sink_ptr) {
 
 int FftProjector::merge(Ctx& c, int set) {
   if (nb[set] == 0) return TSM_OK;
-  fft_merge_kernel<<<(unsigned)((E + 255) / 256), 256, 0, c.stream>>>(bsum[set], bsq[set], nmerged[set], nb[set],
-                                                                       mean[set], m2[set], E);
+  fft_merge_kernel<<<(unsigned)((E + 255) / 256), 256, 0, c.stream>>>(bsum[set], bsq[set], bshift[set], nmerged[set],
+                                                                       nb[set], mean[set], m2[set], E);
   c.launches++;
   nmerged[set] += nb[set];
   nb[set] = 0;
@@ -609,13 +617,14 @@ int FftProjector::accumulate(Ctx& c, const GammaTab& gam, const NoiseSpec& ns, u
   // algorithmic bytes: the fields read, the partly transformed densities
   // written and read once, then per entry either the FP64 running mean (16 B)
   // and sum of squares (8 B) read and written, or the FP32 batch sums (12 B)
-  // written (and read after the batch's first source), plus the batch merge
+  // and shift (8 B) written by the batch's first source, the sums read and
+  // written and the shift read by the others, plus the batch merge
   const double csz = sizeof(cx<R>);
   const bool batched = sizeof(R) == 4;
   double per_entry = 2.0 * csz;
   if (!batched) per_entry += k > 1 ? 48.0 : 24.0;
-  else per_entry += nb[set] > 0 ? 24.0 : 12.0;
-  if (batched && nb[set] + 1 == kFftBatch) per_entry += 12.0 + (nmerged[set] > 0 ? 48.0 : 24.0);
+  else per_entry += nb[set] > 0 ? 32.0 : 20.0;
+  if (batched && nb[set] + 1 == kFftBatch) per_entry += 20.0 + (nmerged[set] > 0 ? 48.0 : 24.0);
   TimedLaunch tl(c, PB_FFT,
                  (double)c.g.V * (spinor_site_bytes(SA::id) + (b ? spinor_site_bytes(SB::id) : 0.0)) +
                      (double)E * per_entry,
@@ -631,6 +640,7 @@ int FftProjector::accumulate(Ctx& c, const GammaTab& gam, const NoiseSpec& ns, u
     sink.first = nb[set] == 0;
     sink.bsum = bsum[set];
     sink.bsq = bsq[set];
+    sink.bshift = bshift[set];
     TSM_TRY(z_pass<R>(c, &sink));
     if (++nb[set] == kFftBatch) TSM_TRY(merge(c, set));
   } else {

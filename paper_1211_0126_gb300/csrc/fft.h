@@ -40,11 +40,14 @@ struct FftProjector {
   void* dens = nullptr;                         // per-source densities / transforms [n_gamma][T][Lz][Ly][Lx]
   double2* mean[2] = {nullptr, nullptr};        // running means: [0] HP-set corrections, [1] LP set
   double* m2[2] = {nullptr, nullptr};           // running sums of squared deviations
-  // FP32 tier: per-entry sums of x and |x|^2 over the current batch of up to
-  // kFftBatch sources of a set, merged into the FP64 moments once per batch
+  // FP32 tier: per-entry sums of d = x - K and |d|^2 over the current batch
+  // of up to kFftBatch sources of a set, K = the batch's first value of the
+  // entry (shifted sums: no cancellation when |mean| >> spread), merged into
+  // the FP64 moments once per batch
   static constexpr int kFftBatch = 32;
   float2* bsum[2] = {nullptr, nullptr};
   float* bsq[2] = {nullptr, nullptr};
+  float2* bshift[2] = {nullptr, nullptr};
   int nb[2] = {0, 0};                           // sources in the current batch
   int nmerged[2] = {0, 0};                      // sources already in the FP64 moments
   double2* twd = nullptr;                       // twiddles e^{+2 pi i m / L}: x, y, z tables (FP64)

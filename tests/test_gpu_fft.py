@@ -11,7 +11,8 @@
   order) equals, at sampled momenta, the TSM with those momenta projected
   by direct phase sums: estimate to 1e-10, error to 1e-8 in FP64 (two-pass
   versus running variance); 1e-5 and 1e-4 in the mixed tier, whose FP32
-  batch sums over 32 sources are merged into FP64 moments.
+  batch sums over 32 sources (of each value minus the batch's first one)
+  are merged into FP64 moments.
 """
 import numpy as np
 import pytest
