@@ -415,6 +415,25 @@ static int cg_solve(Ctx& c, const tm_stop& stop, int s0, int nrhs, EOField b, EO
     const int* dact = nullptr;
     TSM_TRY(upload_list(c, 0, act, &dact));
     int m = chunk;
+    // after the first chunk: about as many iterations as the slowest listed
+    // source still needs at its convergence rate so far (rr falls by rr / rr0
+    // in iter iterations), so that a straggler or two do not drag a chunk of
+    // empty iterations behind them; the device still decides every stop
+    if (launched > 0 && stop.rel_tol > 0.0) {
+      const double goal = stop.rel_tol * stop.rel_tol;   // rr / rr0 at the stopping rule
+      int need = 1;
+      for (int i : act) {
+        const CGState& q = hs[i];
+        const double drop = q.rr0 > 0.0 ? q.rr / q.rr0 : 1.0;
+        if (q.iter <= 0 || !(drop > 0.0) || !(drop < 1.0)) {
+          need = chunk;
+          break;
+        }
+        const double est = q.iter * std::log(goal / drop) / std::log(drop);
+        if (est > need) need = est < chunk ? (int)std::ceil(est) : chunk;
+      }
+      m = need;
+    }
     if (min_left < m) m = min_left;
     if (m < 1) m = 1;
     launched += m;
