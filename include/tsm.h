@@ -82,7 +82,11 @@ typedef enum {
  *            FP32 arithmetic.  TSM_F16 keeps the CG residual and iterate in
  *            FP16 as well (relative precision 2^-11, below the truncation of
  *            an LP solve); TSM_BF16 keeps them in FP32.  Sources and solutions
- *            are exchanged in FP32 for both. */
+ *            are exchanged in FP32 for both through tm_solve_batch; inside
+ *            tsm_loops / tsm_loops_graph the TSM_F16 tier also keeps its noise
+ *            source, Schur source and solution in FP16 (the solution is FP16
+ *            already as the CG iterate; the source's rounding is part of the LP
+ *            map, which both source sets share). */
 typedef enum { TSM_F64 = 0, TSM_F32 = 1, TSM_BF16 = 2, TSM_F16 = 3 } tsm_prec;
 
 typedef struct {
