@@ -859,6 +859,7 @@ int tsm_loops_graph(tsm_ctx** ctxs, const tsm_params* params, int n, double** lo
     c.capturing = true;
     c.next_state = 0;
     c.next_guard = 0;
+    c.guard_body_launches.clear();
     c.cap_lp.clear();
     c.cap_hp.clear();
     if (cudaStreamWaitEvent(c.stream, evs[n], 0) != cudaSuccess) rc = TSM_ERR_CUDA;
@@ -915,6 +916,16 @@ int tsm_loops_graph(tsm_ctx** ctxs, const tsm_params* params, int n, double** lo
           cudaMemcpy(c.h_states, c.states, used * sizeof(CGState), cudaMemcpyDeviceToHost) != cudaSuccess) {
         rc = TSM_ERR_CUDA;
         break;
+      }
+      // launch count: every while-loop body ran as many rounds as its guard counted
+      if (c.next_guard > 0) {
+        std::vector<int> rounds(c.next_guard);
+        if (cudaMemcpy(rounds.data(), c.d_guard, c.next_guard * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+          rc = TSM_ERR_CUDA;
+          break;
+        }
+        for (int k = 0; k < c.next_guard && k < (int)c.guard_body_launches.size(); ++k)
+          if (rounds[k] > 1) c.launches += (long long)c.guard_body_launches[k] * (rounds[k] - 1);
       }
       for (auto& r : c.cap_lp)
         for (int k = 0; k < r.second; ++k) {

@@ -89,6 +89,7 @@ struct Ctx {
   size_t red_branch_cap = 0;
   int next_state = 0;
   int next_guard = 0;
+  std::vector<int> guard_body_launches;   // kernels in the body of each captured while-loop
   std::vector<std::pair<int, int>> cap_lp, cap_hp;   // (first state, count) of captured solves
   std::map<std::string, int> tuned_batch;            // autotuner cache: lattice + tier -> batch width
   std::map<std::string, int> tuned_rpb;              // autotuner cache: lattice + tier -> block shape index

@@ -175,12 +175,15 @@ static int capture_while(Ctx& c, CGState* st, int n, int max_iter, Body&& body) 
   TSM_CUDA(cudaStreamBeginCaptureToGraph(c.body_stream, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   cudaStream_t outer = c.stream;
   c.stream = c.body_stream;
+  const long long launches0 = c.launches;
   int rc = body();
   if (rc == TSM_OK) {
     while_cond_kernel<<<1, 32, 0, c.stream>>>(st, n, h, guard, max_iter + 8);
     c.launches++;
     rc = check_launch(c, "while_cond_kernel");
   }
+  // the body is counted once here; the graph's caller adds the rounds it ran
+  c.guard_body_launches.push_back((int)(c.launches - launches0));
   c.stream = outer;
   cudaGraph_t captured = nullptr;
   const cudaError_t e = cudaStreamEndCapture(c.body_stream, &captured);
